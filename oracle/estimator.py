@@ -1,0 +1,261 @@
+"""Oracle for the MLMC / OF-MLMC estimator (test infrastructure).
+
+Plain numpy in FP64, following Section 2.4 of the paper:
+  - classical MLMC telescoping estimator, Eq. (mlmc), and its MSE, Eq. (mlmc-err);
+  - OF-MLMC control-variate coefficients from the tridiagonal system,
+    Eq. (alpha-matvec), which minimises the cost-weighted variance of
+    Eq. (cv-mlmc-var);
+  - the OF-MLMC estimator, Eq. (ocv-mlmc), and its MSE, Eq. (ocv-mlmc-err);
+  - optimal sample numbers for a tolerance, Eq. (M-tol), or a budget,
+    Eq. (M-budget), with the keep-computed-samples re-optimisation of step 7;
+  - warm-up sample numbers, Eq. (warmup);
+  - the MC-equivalent cost, Eq. (speedup).
+
+Input convention: ``pairs[l]`` is an (M_l, 2) array; column 0 holds q_l and
+column 1 holds q_{l-1} evaluated on the same random input (column 1 unused
+for l = 0).  W[l] is the cost of one sample at l = 0 and of one pair
+(levels l and l-1) for l > 0.
+
+Readings of points the paper leaves open:
+  - sigma^2_l is the unbiased sample variance pooled over every computed
+    q_l (fine members of pair l and coarse members of pair l+1);
+    sigma^2_{l,l-1} is the unbiased sample covariance of pair l;
+  - sigma~^2_l is the unbiased sample variance of alpha_l q_l - alpha_{l-1} q_{l-1}
+    over pair l (of alpha_0 q_0 for l = 0);
+  - the tolerance constraint is eps_OF <= tau, i.e. sum sigma~^2_l/M_l <= tau^2;
+  - the MC-equivalent sample number is ceil((sigma_L/eps)^2) (the printed
+    formula omits the square).
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+
+def _var(x: np.ndarray) -> float:
+    x = np.asarray(x, dtype=np.float64)
+    m = x.size
+    if m < 2:
+        return float("nan")
+    mu = x.sum() / m
+    return float(((x - mu) ** 2).sum() / (m - 1))
+
+
+def _cov(x: np.ndarray, y: np.ndarray) -> float:
+    m = x.size
+    if m < 2:
+        return float("nan")
+    return float(((x - x.sum() / m) * (y - y.sum() / m)).sum() / (m - 1))
+
+
+def indicators(pairs: Sequence[np.ndarray]):
+    """(sigma2[0..L], cov[0..L]) with cov[0] = 0 (Step 3)."""
+    L = len(pairs) - 1
+    sigma2 = np.zeros(L + 1)
+    cov = np.zeros(L + 1)
+    for l in range(L + 1):
+        members = [pairs[l][:, 0]]
+        if l < L:
+            members.append(pairs[l + 1][:, 1])
+        sigma2[l] = _var(np.concatenate(members))
+        if l > 0:
+            cov[l] = _cov(pairs[l][:, 0], pairs[l][:, 1])
+    return sigma2, cov
+
+
+def alpha_matrix(sigma2: np.ndarray, cov: np.ndarray, W: np.ndarray):
+    """Matrix and right-hand side of Eq. (alpha-matvec) for alpha_0..alpha_{L-1}."""
+    L = len(sigma2) - 1
+    A = np.zeros((L, L))
+    rhs = np.zeros(L)
+    for l in range(L):
+        A[l, l] = sigma2[l] * (W[l + 1] + W[l])
+        if l > 0:
+            A[l, l - 1] = -cov[l] * W[l]
+        if l + 1 < L:
+            A[l, l + 1] = -cov[l + 1] * W[l + 1]
+    rhs[L - 1] = cov[L] * W[L]
+    return A, rhs
+
+
+def alpha_optimal(sigma2, cov, W) -> np.ndarray:
+    """alpha[0..L] with alpha_L = 1 (Step 4)."""
+    L = len(sigma2) - 1
+    alpha = np.ones(L + 1)
+    if L > 0:
+        A, rhs = alpha_matrix(np.asarray(sigma2), np.asarray(cov), np.asarray(W, dtype=np.float64))
+        alpha[:L] = np.linalg.solve(A, rhs)
+    return alpha
+
+
+def cost_functional(alpha, sigma2, cov, W) -> float:
+    """C[q_L^*] of Eq. (cv-mlmc-var) for given coefficients (alpha_L = 1)."""
+    L = len(sigma2) - 1
+    C = alpha[0] ** 2 * sigma2[0] * W[0]
+    for l in range(1, L + 1):
+        C += (alpha[l] ** 2 * sigma2[l] + alpha[l - 1] ** 2 * sigma2[l - 1]
+              - 2.0 * alpha[l] * alpha[l - 1] * cov[l]) * W[l]
+    return float(C)
+
+
+def sigma_tilde2(pairs, alpha) -> np.ndarray:
+    """Variances of the alpha-weighted level differences (Step 5)."""
+    L = len(pairs) - 1
+    out = np.zeros(L + 1)
+    out[0] = _var(alpha[0] * pairs[0][:, 0])
+    for l in range(1, L + 1):
+        out[l] = _var(alpha[l] * pairs[l][:, 0] - alpha[l - 1] * pairs[l][:, 1])
+    return out
+
+
+def ofmlmc_mean(pairs, alpha) -> float:
+    """Eq. (ocv-mlmc)."""
+    L = len(pairs) - 1
+    e = alpha[0] * pairs[0][:, 0].sum() / pairs[0].shape[0]
+    for l in range(1, L + 1):
+        d = alpha[l] * pairs[l][:, 0] - alpha[l - 1] * pairs[l][:, 1]
+        e += d.sum() / pairs[l].shape[0]
+    return float(e)
+
+
+def mlmc_mean(pairs) -> float:
+    """Eq. (mlmc): the alpha = 1 special case."""
+    return ofmlmc_mean(pairs, np.ones(len(pairs)))
+
+
+def eps2(sig_t2, M) -> float:
+    """Eq. (ocv-mlmc-err): sum sigma~^2_l / M_l."""
+    return float(sum(s / m for s, m in zip(sig_t2, M)))
+
+
+def estimate(pairs, W):
+    """Steps 3-5 and the estimator of step 6: a dict of everything the paper names."""
+    sigma2, cov = indicators(pairs)
+    alpha = alpha_optimal(sigma2, cov, W)
+    st2 = sigma_tilde2(pairs, alpha)
+    M = [p.shape[0] for p in pairs]
+    return dict(alpha=alpha, sigma2=sigma2, cov=cov, sigma_tilde2=st2,
+                mean=ofmlmc_mean(pairs, alpha), eps2=eps2(st2, M), M=M)
+
+
+def optimal_M(sig_t2, W, target: float, mode: str) -> np.ndarray:
+    """Eq. (M-tol) (mode 'tol', target = tau) or Eq. (M-budget) (mode 'budget', target = B)."""
+    s = np.asarray(sig_t2, dtype=np.float64)
+    W = np.asarray(W, dtype=np.float64)
+    total = float(np.sum(np.sqrt(s * W)))
+    if mode == "tol":
+        raw = (1.0 / target ** 2) * np.sqrt(s / W) * total
+    elif mode == "budget":
+        raw = target * np.sqrt(s / W) / total
+    else:
+        raise ValueError(mode)
+    return np.array([math.ceil(x) for x in raw], dtype=np.int64)
+
+
+def optimal_M_keep(sig_t2, W, M_done, target: float, mode: str) -> np.ndarray:
+    """Step 7 with the keep-samples remark.
+
+    Levels whose optimum falls below the samples already computed keep them;
+    their share (sigma~^2_l/M_l of tau^2, or M_l W_l of the budget) is taken
+    off the target and the remaining levels are re-optimised, until no
+    optimum falls below what is computed.
+    """
+    s = np.asarray(sig_t2, dtype=np.float64)
+    W = np.asarray(W, dtype=np.float64)
+    M_done = np.asarray(M_done, dtype=np.int64)
+    n = len(s)
+    fixed = np.zeros(n, dtype=bool)
+    while True:
+        free = ~fixed
+        if mode == "tol":
+            rem = target ** 2 - float(np.sum(s[fixed] / M_done[fixed]))
+            if rem <= 0.0:
+                raise ValueError("tolerance already consumed by the kept levels")
+            Mf = optimal_M(s[free], W[free], math.sqrt(rem), "tol")
+        else:
+            rem = target - float(np.sum(M_done[fixed] * W[fixed]))
+            if rem <= 0.0:
+                raise ValueError("budget already consumed by the kept levels")
+            Mf = optimal_M(s[free], W[free], rem, "budget")
+        M = M_done.copy()
+        M[free] = Mf
+        newly = free & (M < M_done)
+        if not newly.any():
+            M[fixed] = M_done[fixed]
+            return M
+        fixed |= newly
+
+
+def warmup_M(W) -> np.ndarray:
+    """Eq. (warmup): M_l = ceil(W_L/W_l / 2^(L-l))."""
+    W = np.asarray(W, dtype=np.float64)
+    L = len(W) - 1
+    return np.array([math.ceil(W[L] / W[l] / 2.0 ** (L - l)) for l in range(L + 1)],
+                    dtype=np.int64)
+
+
+def mc_equivalent(sigma2_L: float, eps: float, W_finest_sample: float):
+    """Eq. (speedup) with the squared ratio: (M_MC, W_MC)."""
+    M = math.ceil(sigma2_L / eps ** 2)
+    return M, M * W_finest_sample
+
+
+def total_work(M, W) -> float:
+    return float(np.sum(np.asarray(M, dtype=np.float64) * np.asarray(W, dtype=np.float64)))
+
+
+def adaptive(draw, W, tau: float, max_iter: int = 10, mode: str = "tol",
+             budget: Optional[float] = None, min_samples: int = 2):
+    """Steps 1-8 of the adaptive OF-MLMC algorithm.
+
+    ``draw(l, m)`` returns m new pairs for level l (an (m, 2) array).  Returns
+    the final estimate dict plus the per-iteration sample numbers.  Reading:
+    without the optional Bayesian fit of step 3, a sample variance needs two
+    samples, so every level starts with at least ``min_samples``.
+    """
+    L = len(W) - 1
+    M_target = np.maximum(warmup_M(W), min_samples)                # step 1
+    pairs: List[np.ndarray] = [np.zeros((0, 2)) for _ in range(L + 1)]
+    history = []
+    est = None
+    for it in range(max_iter):
+        for l in range(L + 1):                                       # step 2
+            need = int(M_target[l]) - pairs[l].shape[0]
+            if need > 0:
+                pairs[l] = np.concatenate([pairs[l], draw(l, need)])
+        history.append([p.shape[0] for p in pairs])
+        est = estimate(pairs, W)                                     # steps 3-5
+        spent = total_work([p.shape[0] for p in pairs], W)
+        if math.sqrt(est["eps2"]) <= tau or (mode == "budget" and spent >= budget):
+            break                                                    # step 6
+        M_done = np.array([p.shape[0] for p in pairs])
+        target = tau if mode == "tol" else budget
+        M_target = optimal_M_keep(est["sigma_tilde2"], W, M_done, target, mode)  # step 7
+    est = dict(est)
+    est["history"] = history
+    return est
+
+
+def surrogate_cv(D_top: np.ndarray, s_paired: np.ndarray, s_extra: np.ndarray):
+    """Extra control variate for the top-level term of the estimator.
+
+    D_top[i] = q_L^i - alpha_{L-1} q_{L-1}^i on the M finest-pair inputs,
+    s_paired[i] the surrogate on the same inputs, s_extra the surrogate on N
+    independent extra inputs.  The corrected estimate of E[D_top] is
+        mean(D) + beta (mean(s_extra) - mean(s_paired)),
+    unbiased for any fixed beta; the variance-minimising coefficient is
+        beta = Cov(D, s) / (V[s] (1 + M/N)),
+    giving variance (V[D] - Cov(D, s)^2 / (V[s] (1 + M/N))) / M.
+    (Not in the paper: a standard control variate with an estimated mean.)
+    """
+    M = D_top.size
+    N = s_extra.size
+    vs = _var(s_paired)
+    c = _cov(D_top, s_paired)
+    beta = c / (vs * (1.0 + M / N)) if vs > 0 else 0.0
+    corr = beta * (s_extra.sum() / N - s_paired.sum() / M)
+    var = (_var(D_top) - c * c / (vs * (1.0 + M / N))) / M if vs > 0 else _var(D_top) / M
+    return dict(beta=beta, correction=float(corr), var=float(var),
+                mean=float(D_top.sum() / M + corr))

@@ -1,0 +1,163 @@
+"""Pins of the estimator oracle: closed forms, special cases, brute force,
+the paper's printed numbers, and a toy hierarchy with known moments."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize
+
+import workloads as Wk
+from oracle import estimator as E
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "ofmlmc_paper_numbers.json")))
+
+
+def toy_moments(L, a, b, mu=1.0, c=0.5):
+    """Closed forms for q_l = mu + c 2^-l + (1 + a 2^-l) Z + b 2^-l Y."""
+    s = lambda l: 1.0 + a * 2.0 ** (-l)
+    mean = [mu + c * 2.0 ** (-l) for l in range(L + 1)]
+    var = [s(l) ** 2 + b ** 2 * 4.0 ** (-l) for l in range(L + 1)]
+    cov = [0.0] + [s(l) * s(l - 1) for l in range(1, L + 1)]
+    return np.array(mean), np.array(var), np.array(cov)
+
+
+def test_two_level_closed_form():
+    """L = 1: alpha_0 = W_1/(W_1 + W_0) Cov/V[q_0], Eq. (alpha-opt-works)."""
+    s2 = np.array([2.0, 3.0])
+    cov = np.array([0.0, 1.7])
+    W = np.array([1.0, 17.0])
+    a = E.alpha_optimal(s2, cov, W)
+    assert a[1] == 1.0
+    assert abs(a[0] - 17.0 / 18.0 * 1.7 / 2.0) < 1e-15
+
+
+def test_alpha_minimises_cost_brute_force():
+    rng = np.random.default_rng(0)
+    for L in (2, 3, 4):
+        s2 = rng.uniform(0.5, 2.0, L + 1)
+        cov = np.concatenate([[0.0], rng.uniform(0.2, 0.9, L) * np.sqrt(s2[1:] * s2[:-1])])
+        W = 16.0 ** np.arange(L + 1)
+        a = E.alpha_optimal(s2, cov, W)
+        f = lambda x: E.cost_functional(np.append(x, 1.0), s2, cov, W)
+        res = minimize(f, np.ones(L), method="Nelder-Mead",
+                       options=dict(xatol=1e-10, fatol=1e-12, maxiter=20000, maxfev=40000))
+        assert np.allclose(a[:L], res.x, rtol=1e-4, atol=1e-6)
+        assert f(a[:L]) <= f(np.ones(L)) + 1e-12
+        assert f(a[:L]) <= res.fun * (1 + 1e-12)
+        for _ in range(200):   # no nearby point does better
+            d = rng.normal(size=L) * 10.0 ** rng.uniform(-6, -1)
+            assert f(a[:L] + d) >= f(a[:L]) * (1 - 1e-14)
+
+
+def test_alpha_one_reduces_to_classical_mlmc():
+    pairs = Wk.toy_levels(50, 3, 0.3, 0.4, seed=1)
+    assert abs(E.ofmlmc_mean(pairs, np.ones(4)) - E.mlmc_mean(pairs)) == 0.0
+    manual = pairs[0][:, 0].mean() + sum((p[:, 0] - p[:, 1]).mean() for p in pairs[1:])
+    assert abs(E.mlmc_mean(pairs) - manual) < 1e-14
+
+
+def test_indicators_converge_to_closed_forms():
+    L, a, b = 3, 0.5, 0.8
+    pairs = Wk.toy_levels(200000, L, a, b, seed=2)
+    _, var, cov = toy_moments(L, a, b)
+    s2, c = E.indicators(pairs)
+    assert np.allclose(s2, var, rtol=0.01)
+    assert np.allclose(c[1:], cov[1:], rtol=0.01)
+    W = 16.0 ** np.arange(L + 1)
+    assert np.allclose(E.alpha_optimal(s2, c, W), E.alpha_optimal(var, cov, W), rtol=0.02)
+
+
+def test_estimator_unbiased_and_error_estimate_matches_rmse():
+    L, a, b = 2, 0.5, 1.0
+    mean, var, cov = toy_moments(L, a, b)
+    W = np.array([1.0, 17.0, 272.0])
+    alpha = E.alpha_optimal(var, cov, W)    # fixed coefficients: exactly unbiased
+    M = [400, 60, 12]
+    R = 600
+    ests, e2 = [], []
+    for r in range(R):
+        pairs = Wk.toy_levels(M, L, a, b, seed=1000 + r)
+        ests.append(E.ofmlmc_mean(pairs, alpha))
+        e2.append(E.eps2(E.sigma_tilde2(pairs, alpha), M))
+    ests = np.array(ests)
+    mse = np.mean((ests - mean[L]) ** 2)
+    # closed-form variance of the estimator with these coefficients
+    st2 = [alpha[0] ** 2 * var[0]] + [alpha[l] ** 2 * var[l] + alpha[l - 1] ** 2 * var[l - 1]
+                                      - 2 * alpha[l] * alpha[l - 1] * cov[l] for l in range(1, L + 1)]
+    v_exact = sum(s / m for s, m in zip(st2, M))
+    assert abs(ests.mean() - mean[L]) < 4 * math.sqrt(v_exact / R)
+    assert abs(mse / v_exact - 1) < 0.15
+    assert abs(np.mean(e2) / v_exact - 1) < 0.05
+
+
+def test_optimal_M_tol_and_budget():
+    st2 = np.array([1.0, 0.2, 0.04, 0.01])
+    W = 16.0 ** np.arange(4)
+    tau = 0.01
+    M = E.optimal_M(st2, W, tau, "tol")
+    assert E.eps2(st2, M) <= tau ** 2
+    # one fewer sample on every level violates the tolerance only through rounding slack
+    raw = (1 / tau ** 2) * np.sqrt(st2 / W) * np.sum(np.sqrt(st2 * W))
+    assert abs(np.sum(st2 / raw) - tau ** 2) < 1e-12 * tau ** 2
+    B = 1e6
+    Mb = E.optimal_M(st2, W, B, "budget")
+    assert E.total_work(Mb, W) >= B * (1 - 1e-12)
+    assert E.total_work(Mb - 1, W) < B
+    # Lagrange optimality: M_l proportional to sqrt(sigma~^2_l / W_l)
+    r = raw / np.sqrt(st2 / W)
+    assert np.allclose(r, r[0])
+
+
+def test_keep_samples_reoptimisation():
+    st2 = np.array([1.0, 0.2, 0.04, 0.01])
+    W = 16.0 ** np.arange(4)
+    tau = 0.01
+    M_done = np.array([200000, 10, 1, 1])   # level 0 is over-sampled already (optimum 123889)
+    M = E.optimal_M_keep(st2, W, M_done, tau, "tol")
+    assert np.all(M >= M_done)
+    assert M[0] == 200000
+    assert E.eps2(st2, M) <= tau ** 2 * (1 + 1e-12)
+    plain = E.optimal_M(st2, W, tau, "tol")
+    assert np.all(M[1:] <= plain[1:])      # the kept samples relax the other levels
+
+
+def test_warmup_sequence_printed_in_paper():
+    W = 16.0 ** np.arange(4)
+    M = E.warmup_M(W)
+    assert list(M) == GOLD["warmup_L3_W_16pow"]["M_l0_to_lL"]
+    assert E.total_work(M, W) <= 2 * W[-1]
+
+
+def test_work_model_reproduces_budget_ratio_of_table():
+    """Pair costs W_l = (16^l + 16^(l-1)) w: the printed OF-MLMC sample numbers
+    cost ~8 finest solves, as the text states."""
+    M = GOLD["table"]["OF-MLMC"]["M"]
+    W = np.array([1.0] + [16.0 ** l + 16.0 ** (l - 1) for l in range(1, 4)])
+    ratio = E.total_work(M, W) / 16.0 ** 3
+    assert abs(ratio - GOLD["budget_over_finest_solve"]["value"]) < 0.1
+
+
+def test_mc_equivalent_squared_ratio():
+    M, Wmc = E.mc_equivalent(4.0, 0.1, 3.0)
+    assert M == 400 and Wmc == 1200.0
+
+
+def test_adaptive_loop_reaches_tolerance_on_toy():
+    L, a, b = 3, 0.4, 0.6
+    mean, _, _ = toy_moments(L, a, b)
+    W = np.array([1.0] + [16.0 ** l + 16.0 ** (l - 1) for l in range(1, L + 1)])
+    rng_seed = [10]
+
+    def draw(l, m):
+        rng_seed[0] += 1
+        Ms = [0] * (L + 1)
+        Ms[l] = m
+        return Wk.toy_levels(Ms, L, a, b, seed=rng_seed[0])[l]
+
+    est = E.adaptive(draw, W, tau=0.02)
+    assert math.sqrt(est["eps2"]) <= 0.02
+    assert len(est["history"]) <= 4
+    assert abs(est["mean"] - mean[L]) < 5 * 0.02
+    assert est["history"][0] == list(np.maximum(E.warmup_M(W), 2))

@@ -1,0 +1,409 @@
+"""Pins of the oracle solver against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: textbook
+formulas, exact solutions, invariants, or brute force.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import cloud
+from oracle import solver as S
+from riemann_exact import Side, sample
+
+GAM = (6.12, 1.4)
+PC = (34.3, 0.0)
+
+
+def rel(a, b):
+    return np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300)
+
+
+# ---------------------------------------------------------------- closure (Section 2.1)
+
+@pytest.mark.parametrize("a2,gamma,pc", [(0.0, GAM[0], PC[0]), (1.0, GAM[1], PC[1])])
+def test_pure_phase_limit_is_stiffened_gas(a2, gamma, pc):
+    """alpha2 = 0 / 1: p = (g - 1) rho e - g pc with rho e = E - rho|u|^2/2."""
+    g = S.make_grid(4, gamma=GAM, pc_nd=PC)
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        rho = rng.uniform(0.5, 2.0)
+        u = rng.normal(size=3) * 0.3
+        rhoe = rng.uniform(1.0, 50.0) + gamma * pc / (gamma - 1)
+        E = rhoe + 0.5 * rho * u @ u
+        q = np.array([rho * (1 - a2), rho * a2, *(rho * u), E, a2]).reshape(7, 1)
+        w = S.cons_to_prim(g, q).ravel()
+        p_text = (gamma - 1.0) * rhoe - gamma * pc
+        assert abs(w[5] - p_text) <= 1e-12 * abs(rhoe * gamma)
+        assert np.allclose(w[2:5], u, rtol=1e-14, atol=1e-15)
+
+
+def test_prim_cons_round_trip():
+    g = S.make_grid(8, gamma=GAM, pc_nd=PC)
+    Wp = W.smooth_periodic_primitives(8, seed=3).reshape(7, -1)
+    Q = S.prim_to_cons(g, Wp)
+    assert rel(S.cons_to_prim(g, Q), Wp) < 1e-12
+
+
+def test_max_speed_uniform_state_is_textbook():
+    """Uniform pure-liquid state: max speed = max|u_d| + sqrt(g (p + pc)/rho)."""
+    n = 4
+    g = S.make_grid(n, gamma=GAM, pc_nd=PC)
+    Wp = np.zeros((7, n ** 3))
+    Wp[0] = 1.0
+    Wp[1] = 0.0
+    Wp[2], Wp[3], Wp[4] = 0.1, -0.7, 0.2
+    Wp[5] = 1.0
+    Q = S.prim_to_cons(g, Wp)
+    c = math.sqrt(GAM[0] * (1.0 + PC[0]) / 1.0)
+    assert abs(S.max_speed(g, Q) - (0.7 + c)) < 1e-12 * c
+
+
+# ---------------------------------------------------------------- WENO5 (Jiang & Shu)
+
+def test_weno5_exact_on_quadratics():
+    """Cell averages of a quadratic give exact face values for any nonlinear weights."""
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        a, b, c = rng.normal(size=3) * np.array([1.0, 3.0, 10.0])
+        avg = lambda i: a + b * i + c * (i * i + 1.0 / 12.0)   # average over [i-1/2, i+1/2]
+        exact_r = a + b * 0.5 + c * 0.25                        # f(+1/2)
+        exact_l = a - b * 0.5 + c * 0.25                        # f(-1/2)
+        v = [avg(i) for i in (-2, -1, 0, 1, 2)]
+        scale = abs(a) + abs(b) + abs(c)
+        assert abs(S.weno5(*v) - exact_r) < 1e-12 * scale
+        assert abs(S.weno5(*v[::-1]) - exact_l) < 1e-12 * scale
+
+
+def test_weno5_fifth_order_on_smooth_data():
+    def err(n):
+        h = 1.0 / n
+        x = (np.arange(-2, n + 3) + 0.5) * h
+        avg = (np.cos(2 * np.pi * (x - 0.5 * h)) - np.cos(2 * np.pi * (x + 0.5 * h))) / (2 * np.pi * h)
+        e = 0.0
+        for i in range(2, n + 2):
+            val = S.weno5(*avg[i - 2:i + 3], eps=1e-40)
+            e = max(e, abs(val - np.sin(2 * np.pi * (x[i] + 0.5 * h))))
+        return e
+    e1, e2 = err(40), err(80)
+    assert math.log2(e1 / e2) > 4.5
+
+
+# ---------------------------------------------------------------- HLLC
+
+def _flux_text(w, d, gamma, pc):
+    """Physical flux of the five-equation system from textbook formulas."""
+    a2 = w[6]
+    rho = w[0] + w[1]
+    G = (1 - a2) / (gamma[0] - 1) + a2 / (gamma[1] - 1)
+    Pi = (1 - a2) * gamma[0] * pc[0] / (gamma[0] - 1) + a2 * gamma[1] * pc[1] / (gamma[1] - 1)
+    u = np.array(w[2:5])
+    p = w[5]
+    E = G * p + Pi + 0.5 * rho * u @ u
+    un = u[d]
+    F = np.array([w[0] * un, w[1] * un, rho * u[0] * un, rho * u[1] * un, rho * u[2] * un,
+                  (E + p) * un, a2 * un])
+    F[2 + d] += p
+    return F
+
+
+def _random_state(rng, a2=None):
+    a2 = rng.uniform(0.01, 0.99) if a2 is None else a2
+    return np.array([(1 - a2) * rng.uniform(0.8, 1.2), a2 * rng.uniform(0.004, 0.006),
+                     *rng.normal(size=3) * 0.5, rng.uniform(0.5, 2.0), a2])
+
+
+def test_hllc_consistency():
+    g = S.make_grid(4, gamma=GAM, pc_nd=PC)
+    rng = np.random.default_rng(11)
+    for _ in range(30):
+        w = _random_state(rng)
+        for d in range(3):
+            F, uf = S.hllc(g, w, w, d)
+            Ft = _flux_text(w, d, GAM, PC)
+            assert np.allclose(F, Ft, rtol=1e-12, atol=1e-12 * np.max(np.abs(Ft)))
+            assert abs(uf - w[2 + d]) < 1e-12
+
+
+def test_hllc_isolated_contact_is_exact():
+    """Equal p and u, different composition: flux is the upwind physical flux."""
+    g = S.make_grid(4, gamma=GAM, pc_nd=PC)
+    rng = np.random.default_rng(12)
+    for un in (0.3, -0.4, 0.0):
+        wl = _random_state(rng, 0.1)
+        wr = _random_state(rng, 0.9)
+        wl[2:5] = wr[2:5] = [un, 0.1, -0.2]
+        wl[5] = wr[5] = 1.3
+        F, uf = S.hllc(g, wl, wr, 0)
+        up = wl if un >= 0 else wr
+        Ft = _flux_text(up, 0, GAM, PC)
+        assert np.allclose(F[:6], Ft[:6], rtol=1e-12, atol=1e-12)
+        assert abs(uf - un) < 1e-13
+        assert abs(F[6] - up[6] * un) < 1e-13
+
+
+def test_hllc_mirror_symmetry():
+    g = S.make_grid(4, gamma=GAM, pc_nd=PC)
+    rng = np.random.default_rng(13)
+    for _ in range(30):
+        wl, wr = _random_state(rng), _random_state(rng)
+        F, uf = S.hllc(g, wl, wr, 1)
+        ml, mr = wr.copy(), wl.copy()
+        ml[3] *= -1
+        mr[3] *= -1
+        Fm, ufm = S.hllc(g, ml, mr, 1)
+        sign = np.ones(7)
+        sign[[0, 1, 2, 4, 5, 6]] = -1.0   # mass, tangential momenta, energy, alpha2 flip
+        sign[3] = 1.0                      # normal momentum flux is even
+        assert np.allclose(Fm, sign * F, rtol=1e-11, atol=1e-12)
+        assert abs(ufm + uf) < 1e-12
+
+
+# ---------------------------------------------------------------- low-storage RK3
+
+def _butcher():
+    A, B = S.rk_coefficients()
+    a21 = B[0]
+    a31, a32 = B[0] + B[1] * A[1], B[1]
+    b = np.array([B[0] + B[1] * A[1] + B[2] * A[2] * A[1], B[1] + B[2] * A[2], B[2]])
+    c = np.array([0.0, a21, a31 + a32])
+    return A, B, b, c, a32
+
+
+def test_rk3_order_conditions():
+    A, B, b, c, a32 = _butcher()
+    assert A[0] == 0.0
+    assert abs(b.sum() - 1) < 1e-8
+    assert abs(b @ c - 0.5) < 1e-8
+    assert abs(b @ (c * c) - 1.0 / 3.0) < 1e-8
+    assert abs(b[2] * a32 * c[1] - 1.0 / 6.0) < 1e-8
+
+
+def test_rk3_linear_amplification():
+    A, B = S.rk_coefficients()
+    for z in (-0.3, 0.1 + 0.5j, -1.0 + 1.0j):
+        y, dy = 1.0, 0.0
+        for s in range(3):
+            dy = A[s] * dy + z * y
+            y = y + B[s] * dy
+        assert abs(y - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-8
+
+
+# ---------------------------------------------------------------- full scheme
+
+def _riemann_run(nx, left, right, gam, pc, t_end, x0=0.5, eps=1e-8):
+    g = S.make_grid(nx, 1, 1, gamma=gam, pc_nd=pc, bc=0, h=1.0 / nx)
+    x = (np.arange(nx) + 0.5) / nx
+    L = x < x0
+    Wp = np.zeros((7, nx))
+    a2 = np.where(L, eps, 1 - eps)
+    Wp[0] = np.where(L, (1 - a2) * left[0], (1 - a2) * left[0])
+    Wp[1] = np.where(L, a2 * right[0], a2 * right[0])
+    Wp[2] = np.where(L, left[1], right[1])
+    Wp[5] = np.where(L, left[2], right[2])
+    Wp[6] = a2
+    Q = S.prim_to_cons(g, Wp)
+    Q, n = S.advance(g, Q.reshape(7, 1, 1, nx), t_end)
+    Wn = S.cons_to_prim(g, Q.reshape(7, -1))
+    er, eu, ep, _ = sample(Side(*left, gam[0], pc[0]), Side(*right, gam[1], pc[1]), (x - x0) / t_end)
+    rho = Wn[0] + Wn[1]
+    return (np.mean(np.abs(rho - er)) / np.mean(er), np.mean(np.abs(Wn[5] - ep)) / np.mean(np.abs(ep)),
+            np.mean(np.abs(Wn[2] - eu)) / max(np.mean(np.abs(eu)), 1e-300))
+
+
+def test_riemann_sod_single_gas_converges():
+    """Ideal gas on both sides (both phases gamma 1.4, pc 0): Sod's problem."""
+    e100 = _riemann_run(100, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), (1.4, 1.4), (0.0, 0.0), 0.2)
+    e200 = _riemann_run(200, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), (1.4, 1.4), (0.0, 0.0), 0.2)
+    for a, b in zip(e100, e200):
+        assert b < 0.65 * a
+    assert max(e200) < 0.025
+
+
+def test_riemann_water_air_converges():
+    """Water at 1e9 Pa against air at 1e5 Pa (ratio 1e4), densities 1000 / 50 kg/m^3."""
+    args = ((1.0, 0.0, 100.0), (0.05, 0.0, 0.01), GAM, PC, 0.008)
+    e100 = _riemann_run(100, *args)
+    e200 = _riemann_run(200, *args)
+    for a, b in zip(e100, e200):
+        assert b < 0.75 * a
+    assert e200[0] < 0.02 and e200[1] < 0.03 and e200[2] < 0.15
+
+
+def test_mixture_expansion_follows_phase_isentropes():
+    """Pins K of Eq. (var_K): in smooth flow each phase of the Kapila model is
+    isentropic, rho_k = rho_k0 ((p + pc_k)/(p0 + pc_k))^(1/g_k).  Without the
+    K div(u) source the gas density would follow the mixture density instead
+    (a few per cent off for this expansion)."""
+    nx = 200
+    g = S.make_grid(nx, 1, 1, gamma=GAM, pc_nd=PC, bc=0, h=1.0 / nx)
+    x = (np.arange(nx) + 0.5) / nx
+    a2, r1, r2, p0 = 0.3, 1.0, 0.005, 1.0
+    Wp = np.zeros((7, nx))
+    Wp[0], Wp[1], Wp[5], Wp[6] = (1 - a2) * r1, a2 * r2, p0, a2
+    Wp[2] = np.where(x < 0.5, -0.02, 0.02)
+    Q, _ = S.advance(g, S.prim_to_cons(g, Wp).reshape(7, 1, 1, nx), 0.1)
+    Wn = S.cons_to_prim(g, Q.reshape(7, -1))
+    p, a = Wn[5], Wn[6]
+    assert p.min() < 0.97 * p0       # a real expansion happened
+    rho2 = Wn[1] / a
+    rho1 = Wn[0] / (1 - a)
+    iso2 = r2 * ((p + PC[1]) / (p0 + PC[1])) ** (1 / GAM[1])
+    iso1 = r1 * ((p + PC[0]) / (p0 + PC[0])) ** (1 / GAM[0])
+    assert np.max(np.abs(rho2 / iso2 - 1)) < 1e-3
+    assert np.max(np.abs(rho1 / iso1 - 1)) < 1e-4
+
+
+def test_interface_advection_keeps_p_and_u_uniform():
+    """Uniform p and u with an alpha2 / density step stays at uniform p and u.
+
+    The step carries the initial condition's one-cell tanh smoothing; a bare
+    step on a bubble only ~5 cells wide drives WENO5 into overshoots that make
+    the liquid partial density negative (a known limit of the scheme).
+    """
+    n = 16
+    g = S.make_grid(n, gamma=GAM, pc_nd=PC, bc=1)
+    x = (np.arange(n) + 0.5) / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    d = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+    a2 = np.clip(0.5 * (1 - np.tanh((d - 0.3) * n)), 1e-6, 1 - 1e-6)
+    Wp = np.zeros((7, n, n, n))
+    Wp[0] = (1 - a2) * 1.0
+    Wp[1] = a2 * 0.005
+    Wp[2], Wp[3], Wp[4] = 0.5, -0.25, 0.125
+    Wp[5] = 1.0
+    Wp[6] = a2
+    Q = S.prim_to_cons(g, Wp.reshape(7, -1)).reshape(7, n, n, n)
+    dt = 0.3 * g.h / S.max_speed(g, Q)
+    for _ in range(10):
+        Q = S.rk3_step(g, Q, dt)
+    Wn = S.cons_to_prim(g, Q.reshape(7, -1))
+    assert np.max(np.abs(Wn[5] - 1.0)) < 1e-12
+    assert np.max(np.abs(Wn[2] - 0.5)) < 1e-12
+    assert np.max(np.abs(Wn[3] + 0.25)) < 1e-12
+    assert np.max(np.abs(Wn[4] - 0.125)) < 1e-12
+    assert np.max(np.abs(Wn[6] - a2.ravel())) > 1e-3   # the interface did move
+
+
+def test_conservation_on_periodic_box():
+    n = 8
+    g = S.make_grid(n, gamma=GAM, pc_nd=PC, bc=1)
+    Q = S.prim_to_cons(g, W.smooth_periodic_primitives(n, seed=5).reshape(7, -1)).reshape(7, n, n, n)
+    t0 = S.totals(g, Q)
+    dt = 0.3 * g.h / S.max_speed(g, Q)
+    for _ in range(4):
+        Q = S.rk3_step(g, Q, dt)
+    t1 = S.totals(g, Q)
+    scale = np.array([1.0, 0.005, 1.0, 1.0, 1.0, 40.0])
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * scale)
+    assert np.max(np.abs(S.rhs(g, Q)[:6])) > 1e-3   # the fields are not static
+
+
+def test_centred_bubble_keeps_cube_symmetry():
+    n = 12
+    sp = W.SolverParams()
+    b = np.array([[0.05, 0.05, 0.05, 0.02]])
+    Q = S.init_cloud(sp, n, b)
+    g = S.grid_from_params(sp, n)
+    dt = 0.3 * g.h / S.max_speed(g, Q)
+    for _ in range(3):
+        Q = S.rk3_step(g, Q, dt)
+    # transpose x <-> y swaps the x and y momenta
+    T = Q.transpose(0, 1, 3, 2).copy()
+    T[[2, 3]] = T[[3, 2]]
+    assert rel(T, Q) < 1e-12
+    # mirror x -> -x flips the x momentum
+    M = Q[:, :, :, ::-1].copy()
+    M[2] *= -1
+    assert np.max(np.abs(M - Q)) < 1e-12 * np.max(np.abs(Q))
+    assert np.max(np.abs(Q[2])) > 1e-6
+
+
+# ---------------------------------------------------------------- reductions and QoIs
+
+def test_reductions_brute_force():
+    n = 6
+    g = S.make_grid(n, gamma=GAM, pc_nd=PC, bc=1)
+    Wp = W.smooth_periodic_primitives(n, seed=9, amp=0.3).reshape(7, -1)
+    Q = S.prim_to_cons(g, Wp)
+    a2 = Wp[6]
+    G = (1 - a2) / (GAM[0] - 1) + a2 / (GAM[1] - 1)
+    Pi = (1 - a2) * GAM[0] * PC[0] / (GAM[0] - 1) + a2 * GAM[1] * PC[1] / (GAM[1] - 1)
+    c = np.sqrt(((G + 1) * Wp[5] + Pi) / (G * (Wp[0] + Wp[1])))
+    smax = np.max(np.maximum(np.maximum(np.abs(Wp[2]), np.abs(Wp[3])), np.abs(Wp[4])) + c)
+    assert abs(S.max_speed(g, Q) - smax) < 1e-12 * smax
+    vol = (1.0 / n) ** 3
+    assert np.allclose(S.totals(g, Q), Q[:6].sum(axis=1) * vol, rtol=1e-13)
+
+
+def test_centre_sensor_has_eight_cells_on_even_grids():
+    for n in (16, 32, 64):
+        g = S.make_grid(n)
+        s = np.array([0.5, 0.5, 0.5, 0.005])
+        assert S._lib().orc_sensor_cell_count(g, S._p(s)) == 8
+
+
+def test_solve_time_loop_and_qois():
+    w = W.tiny(16, 4)
+    b = cloud.sample_cloud(w.cloud, W.BASE_SEED, 3)
+    q, hist, Q = S.solve(w.solver, 16, b)
+    assert q["status"] == 0
+    assert q["t_final"] == w.solver.t_end
+    g = S.grid_from_params(w.solver, 16)
+    # the peak is at least the final max pressure, and the history ends at the final sensor value
+    Wn = S.cons_to_prim(g, Q.reshape(7, -1))
+    assert q["p_peak"] >= Wn[5].max() * w.solver.p_liq * (1 - 1e-15)
+    k = q["peak_index"]
+    assert q["p_peak_xyz"][0] == ((k % 16) + 0.5) / 16 * w.solver.domain_L
+    centre = Wn[5].reshape(16, 16, 16)[7:9, 7:9, 7:9].mean() * w.solver.p_liq
+    assert abs(hist[0, -1] - centre) < 1e-9 * centre
+    # number of steps ~ t_end / dt at CFL 0.3 (the IC at rest has c = 1469.8 m/s in water)
+    assert 25 <= q["n_steps"] <= 40
+
+
+# ---------------------------------------------------------------- initial condition and sampler
+
+def test_initial_condition_far_and_inside():
+    sp = W.SolverParams()
+    n = 16
+    b = np.array([[0.05, 0.05, 0.05, 0.03]])
+    Q = S.init_cloud(sp, n, b)
+    g = S.grid_from_params(sp, n)
+    Wn = S.cons_to_prim(g, Q.reshape(7, -1)).reshape(7, n, n, n)
+    # corner cell: liquid (alpha2 clamped at 1e-6), p = p_liq + (p_gas - p_liq) H
+    Hc = 0.5 * (1 - math.tanh((math.sqrt(3) * (0.5 - 0.5 / n) - 0.3) * n))
+    assert abs(Wn[6, 0, 0, 0] - 1e-6) < 1e-18
+    assert abs(Wn[5, 0, 0, 0] - (1.0 + (2.34e3 / 1e7 - 1.0) * Hc)) < 1e-12
+    assert abs(Wn[0, 0, 0, 0] - (1 - 1e-6)) < 1e-15
+    # centre cells: gas at p_gas (H = 1/2 (1 - tanh(-r/h)) ~ 1)
+    H = 0.5 * (1 - math.tanh((math.sqrt(3) * 0.5 / n - 0.3) * n))
+    assert abs(Wn[5, 8, 8, 8] - (1.0 + (2.34e3 / 1e7 - 1.0) * H)) < 1e-12
+    assert np.all(Wn[2:5] == 0.0)
+
+
+def test_sampler_distributions():
+    cp = W.cloud_uniform(200)
+    b = cloud.sample_cloud(cp, W.BASE_SEED, 0)
+    c = 0.5 * cp.domain_L
+    r = np.sqrt(((b[:, :3] - c) ** 2).sum(1))
+    assert np.all(r <= cp.cloud_radius * (1 + 1e-15))
+    assert np.all((b[:, 3] >= cp.r_min) & (b[:, 3] <= cp.r_max))
+    # uniform in a ball: E[(r/R)^3] = 1/2
+    assert abs(np.mean((r / cp.cloud_radius) ** 3) - 0.5) < 0.07
+    lp = W.cloud_paper500()
+    b5 = cloud.sample_cloud(lp, 1, 2)
+    assert b5.shape == (500, 4)
+    assert np.all((b5[:, 3] >= 0.8e-3) & (b5[:, 3] <= 1.2e-3))
+    # same (seed, id) -> same cloud; another id -> another cloud
+    assert np.array_equal(cloud.sample_cloud(cp, 5, 7), cloud.sample_cloud(cp, 5, 7))
+    assert not np.array_equal(cloud.sample_cloud(cp, 5, 7), cloud.sample_cloud(cp, 5, 8))
+
+
+def test_splitmix64_reference_values():
+    """SplitMix64 from seed 0 (Steele, Lea & Flood): first outputs of the published generator."""
+    g = cloud.SplitMix64(0, 0)
+    assert g.next_u64() == 0xE220A8397B1DCDAF
+    assert g.next_u64() == 0x6E789E6AA1B965F4
+    assert g.next_u64() == 0x06C45D188009454F
