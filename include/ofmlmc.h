@@ -1,0 +1,237 @@
+/*
+ * ofmlmc.h - C ABI of the GB300 library for optimal-fidelity multi-level
+ * Monte Carlo (OF-MLMC) of cloud cavitation collapse.
+ *
+ * Method: Sukys, Rasthofer, Wermelinger, Hadjidoukas, Koumoutsakos,
+ * "Optimal fidelity multi-level Monte Carlo for quantification of uncertainty
+ * in simulations of cloud cavitation collapse" (2017).
+ *
+ * Conventions
+ *   - Units at this interface are SI (m, Pa, s, kg/m^3).  Internally the
+ *     solver is non-dimensional (length L, density 1000 kg/m^3, pressure
+ *     p_liq, velocity sqrt(p_liq/1000)).
+ *   - Host arrays are owned by the caller.  Device memory is either a
+ *     caller-provided workspace (borrowed for the lifetime of the object it
+ *     was given to) or allocated by the library when the workspace pointer is
+ *     NULL (freed by the matching destroy call).
+ *   - Every int-returning call returns OFM_OK (0) or a negative OFM_E* code;
+ *     ofm_last_error() gives a message for the calling thread.
+ *   - One handle per thread; calls on the same handle must not overlap.
+ *   - `stream` arguments are cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Calls order their device work after the work already
+ *     queued on that stream.
+ */
+#ifndef OFMLMC_H
+#define OFMLMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    OFM_OK = 0,
+    OFM_EINVAL = -1,   /* bad argument (sizes, NULL pointers, unsupported grid) */
+    OFM_ENOMEM = -2,   /* workspace too small or device allocation failed */
+    OFM_ECUDA = -3,    /* a CUDA runtime call failed */
+    OFM_ENUMERIC = -4, /* the call completed but some sample's status is non-zero */
+    OFM_ETIMEOUT = -5  /* a bounded device-side wait expired */
+};
+
+enum { OFM_FP64 = 0, OFM_FP32 = 1 };                      /* stencil storage/arithmetic */
+enum { OFM_BC_TRANSMISSIVE = 0, OFM_BC_PERIODIC = 1 };    /* ghost cells */
+enum { OFM_RADII_UNIFORM = 0, OFM_RADII_LOGNORMAL = 1 };  /* cloud radius law */
+enum { OFM_MODE_TOL = 0, OFM_MODE_BUDGET = 1 };           /* sample-number optimisation */
+
+/* Per-sample status bits (fault-tolerant MLMC, Section 2.5): a sample with a
+ * non-zero status is excluded from estimators. */
+enum {
+    OFM_ST_NONFINITE = 1, /* NaN/Inf in the state or pressure */
+    OFM_ST_NEGATIVE = 2,  /* mixture density or squared sound speed <= 0 */
+    OFM_ST_MAXSTEPS = 4   /* step limit reached before t_end */
+};
+
+#define OFM_MAX_SENSORS 8
+#define OFM_MAX_GROUPS 8
+#define OFM_MAX_LEVELS 16
+
+/* One spherical bubble; centre and radius in metres. */
+typedef struct {
+    double x, y, z, r;
+} ofm_bubble;
+
+/* Random cloud geometry (Section 3.1): n_bubbles centres uniform in a ball of
+ * radius cloud_radius around the domain centre; radii uniform in
+ * [r_min, r_max] or log-normal(ln_mu, ln_sigma) truncated to [r_min, r_max].
+ * Overlapping bubbles are allowed. */
+typedef struct {
+    int n_bubbles;
+    int radius_law;      /* OFM_RADII_* */
+    double cloud_radius; /* m */
+    double r_min, r_max; /* m */
+    double ln_mu, ln_sigma;
+    double domain_L;     /* m, the domain is [0, L]^3 */
+} ofm_cloud_params;
+
+/* Flow solver configuration (Sections 2.1-2.2, 3.1). */
+typedef struct {
+    double gamma[2];  /* stiffened-gas gamma: [0] liquid, [1] gas */
+    double pc[2];     /* stiffened-gas p_c [Pa] */
+    double rho0[2];   /* initial phase densities [kg/m^3] */
+    double p_gas;     /* initial bubble pressure [Pa] */
+    double p_liq;     /* initial liquid pressure [Pa] (also the pressure unit) */
+    double cfl;       /* Courant number (0.3 in the paper) */
+    double t_end;     /* end time [s] */
+    double weno_eps;  /* WENO5 epsilon (non-dimensional) */
+    double domain_L;  /* m */
+    int precision;    /* OFM_FP64 or OFM_FP32 (FP32 stencil, FP64 reductions) */
+    int bc;           /* OFM_BC_* */
+    int max_steps;    /* per-sample step limit */
+    int n_sensors;    /* <= OFM_MAX_SENSORS */
+    double sensors[OFM_MAX_SENSORS][4]; /* centre (x, y, z) and radius [m], Eq. (sensor) */
+    int n_out_times;  /* sensor history samples on t_k = k t_end/(n_out_times-1) */
+} ofm_solver_config;
+
+/* Per-sample quantities of interest (Section 3.2). */
+typedef struct {
+    double p_peak;          /* max over time (t = 0 and every step) of max over cells of p [Pa] */
+    double p_peak_xyz[3];   /* cell centre of the first maximiser (x fastest) [m] */
+    double p_peak_t;        /* time of p_peak [s] */
+    double p_peak_dist;     /* distance of p_peak_xyz from the domain centre [m] */
+    int64_t peak_index;     /* linear cell index of the maximiser */
+    double sensor_peak[OFM_MAX_SENSORS]; /* max over time of each sensor [Pa] */
+    double totals0[6];      /* sum over cells of Q_0..Q_5 times h^3 at t = 0 (non-dimensional) */
+    double totals_end[6];   /* the same at the final time */
+    double t_final;         /* [s] */
+    int n_steps;
+    int status;             /* OFM_ST_* bits */
+} ofm_qoi;
+
+/* One group of samples on one grid. */
+typedef struct {
+    int N;                       /* cells per axis: a multiple of 8, 8 <= N <= 512 */
+    int n_samples;
+    const uint64_t* sample_ids;  /* host [n_samples]; cloud of sample i = (seed, sample_ids[i]) */
+    uint64_t seed;
+    const ofm_bubble* bubbles;   /* host [n_samples * n_bubbles] or NULL: sample the clouds */
+    ofm_qoi* qoi_out;            /* host [n_samples], written by ofm_batch_qoi / ofm_solve_batch */
+    double* sensor_hist;         /* host [n_samples][n_sensors][n_out_times] [Pa], or NULL */
+} ofm_group;
+
+typedef struct ofm_solver ofm_solver;
+typedef struct ofm_batch ofm_batch;
+
+/* Thread-local message for the last failing call ("" if none). */
+const char* ofm_last_error(void);
+
+/* Version string of the library build. */
+const char* ofm_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Cloud sampler (Section 3.1).  SplitMix64 seeded with
+ * seed ^ (sample_id * 0x9E3779B97F4A7C15); uniform doubles from the top 53
+ * bits; centres by rejection from the cube [-R, R]^3 (x, y, z per try); then
+ * the radius (uniform, or Box-Muller log-normal redrawn until in range).
+ * Writes params->n_bubbles bubbles to `out` (host).  Pure host computation.
+ * ------------------------------------------------------------------------- */
+int ofm_sample_cloud(const ofm_cloud_params* params, uint64_t seed, uint64_t sample_id,
+                     ofm_bubble* out);
+
+/* ---------------------------------------------------------------------------
+ * Solver handle.  Validates and copies the configuration (non-dimensionalised
+ * once).  Allocates no device memory.
+ * ------------------------------------------------------------------------- */
+int ofm_solver_create(ofm_solver** out, const ofm_solver_config* config);
+void ofm_solver_destroy(ofm_solver* solver);
+
+/* Device bytes a batch of these groups needs (states Q, Q', dQ per sample in
+ * the configured precision, per-tile partial reductions, per-sample records). */
+int ofm_batch_workspace_bytes(const ofm_solver* solver, const ofm_cloud_params* cloud,
+                              const ofm_group* groups, int n_groups, size_t* bytes);
+
+/* ---------------------------------------------------------------------------
+ * Batched solves of uneven levels (Sections 2.2-2.3 per sample; every group's
+ * samples advance together, each with its own CFL time step, in one set of
+ * kernel launches per stage).
+ *
+ * ofm_batch_create: lays out the workspace (device, >= the bytes above; NULL =
+ *   allocate), samples or copies the clouds on the host and uploads them.
+ * ofm_batch_init:   initial condition, t = 0 reductions and first time step.
+ * ofm_batch_run:    advances every unfinished sample by up to max_steps steps
+ *   (CUDA-graph-captured chunks); *n_active receives the number of samples
+ *   that have not reached t_end (0 when all are done).  Synchronises with the
+ *   batch's internal stream once per chunk.
+ * ofm_batch_qoi:    copies the QoI records (and sensor histories if the group
+ *   has a sensor_hist buffer) to the groups' host arrays; returns OFM_ENUMERIC
+ *   if any sample's status is non-zero.
+ * ofm_batch_copy_state / ofm_batch_set_state: read / overwrite the current
+ *   state Q[7][N][N][N] (x fastest, non-dimensional, storage precision) of one
+ *   sample; `host_buf` is a host pointer of exactly 7 N^3 elements.  Setting a
+ *   state after ofm_batch_init recomputes the sample's t = 0 reductions, so a
+ *   caller can start from any state (e.g. to inject a corrupted sample).
+ * ------------------------------------------------------------------------- */
+int ofm_batch_create(ofm_batch** out, ofm_solver* solver, const ofm_cloud_params* cloud,
+                     const ofm_group* groups, int n_groups, void* workspace, size_t workspace_bytes,
+                     void* stream);
+int ofm_batch_init(ofm_batch* batch);
+int ofm_batch_run(ofm_batch* batch, int max_steps, int* n_active);
+int ofm_batch_qoi(ofm_batch* batch);
+int ofm_batch_copy_state(ofm_batch* batch, int group, int sample, void* host_buf, size_t bytes);
+int ofm_batch_set_state(ofm_batch* batch, int group, int sample, const void* host_buf, size_t bytes);
+/* Cell-steps (cells x completed RK3 steps, summed over samples) so far. */
+int ofm_batch_cell_steps(ofm_batch* batch, double* cell_steps);
+/* Number of kernels this batch has launched so far (graph replays count
+ * every kernel node). */
+int ofm_batch_kernel_launches(ofm_batch* batch, int64_t* launches);
+void ofm_batch_destroy(ofm_batch* batch);
+
+/* One call for the whole path: create, init, run to t_end, copy QoIs, destroy. */
+int ofm_solve_batch(ofm_solver* solver, const ofm_cloud_params* cloud, const ofm_group* groups,
+                    int n_groups, void* workspace, size_t workspace_bytes, void* stream);
+
+/* A single level: ofm_solve_batch with one group. */
+int ofm_solve_level(ofm_solver* solver, const ofm_cloud_params* cloud, int N, int n,
+                    const uint64_t* sample_ids, uint64_t seed, ofm_qoi* out, double* sensor_hist,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * OF-MLMC estimator (Section 2.4), host FP64.
+ *
+ * q[l] points to M[l] rows of (q_l, q_{l-1}) pairs on shared inputs
+ * (row-major, 2 doubles per row; the second column is ignored for l = 0).
+ * W[l] = cost of one sample (l = 0) or one pair (l > 0).
+ * Outputs (arrays of L+1):
+ *   alpha        coefficients of Eq. (alpha-matvec), alpha[L] = 1;
+ *   sigma2       sample variance of q_l pooled over pair l's fine and pair
+ *                l+1's coarse members; cov[l] = sample Cov[q_l, q_{l-1}] of pair l;
+ *   sigma_tilde2 sample variance of alpha_l q_l - alpha_{l-1} q_{l-1} (Step 5);
+ *   mean         Eq. (ocv-mlmc); eps2 = sum sigma_tilde2/M, Eq. (ocv-mlmc-err).
+ * All variances use the M-1 denominator; every level needs M >= 2.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double alpha[OFM_MAX_LEVELS];
+    double sigma2[OFM_MAX_LEVELS];
+    double cov[OFM_MAX_LEVELS];
+    double sigma_tilde2[OFM_MAX_LEVELS];
+    double mean;
+    double eps2;
+} ofm_estimate_out;
+
+int ofm_estimate(int L, const int64_t* M, const double* const* q, const double* W,
+                 ofm_estimate_out* out);
+
+/* Eq. (M-tol) (mode OFM_MODE_TOL, target = tau, constraint eps_OF <= tau) or
+ * Eq. (M-budget) (OFM_MODE_BUDGET, target = budget) with the step-7 rule that
+ * keeps already computed samples (M_done may be NULL = none). */
+int ofm_optimal_samples(int L, const double* sigma_tilde2, const double* W, const int64_t* M_done,
+                        double target, int mode, int64_t* M_out);
+
+/* Eq. (warmup): M_l = ceil(W_L / W_l / 2^(L-l)). */
+int ofm_warmup_samples(int L, const double* W, int64_t* M_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OFMLMC_H */

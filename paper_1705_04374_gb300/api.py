@@ -1,0 +1,235 @@
+"""Python front end of the C ABI: configuration marshalling and a Batch object.
+
+Device memory for a batch's workspace comes from PyTorch (a uint8 CUDA
+tensor); its raw pointer and the current torch stream are passed to the
+library, which does all of the work.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import native as nv
+
+
+def solver_config(sp, precision: str = "fp64") -> nv.ofm_solver_config:
+    c = nv.ofm_solver_config()
+    c.gamma[0], c.gamma[1] = sp.gamma
+    c.pc[0], c.pc[1] = sp.pc
+    c.rho0[0], c.rho0[1] = sp.rho0
+    c.p_gas = sp.p_gas
+    c.p_liq = sp.p_liq
+    c.cfl = sp.cfl
+    c.t_end = sp.t_end
+    c.weno_eps = sp.weno_eps
+    c.domain_L = sp.domain_L
+    c.precision = {"fp64": nv.OFM_FP64, "fp32": nv.OFM_FP32}[precision]
+    c.bc = sp.bc
+    c.max_steps = sp.max_steps
+    c.n_sensors = len(sp.sensors)
+    for i, s in enumerate(sp.sensors):
+        for k in range(4):
+            c.sensors[i][k] = s[k]
+    c.n_out_times = sp.n_out_times
+    return c
+
+
+def cloud_params(cp) -> nv.ofm_cloud_params:
+    c = nv.ofm_cloud_params()
+    c.n_bubbles = cp.n_bubbles
+    c.radius_law = cp.radius_law
+    c.cloud_radius = cp.cloud_radius
+    c.r_min = cp.r_min
+    c.r_max = cp.r_max
+    c.ln_mu = cp.ln_mu
+    c.ln_sigma = cp.ln_sigma
+    c.domain_L = cp.domain_L
+    return c
+
+
+def sample_cloud(cp, seed: int, sample_id: int) -> np.ndarray:
+    out = (nv.ofm_bubble * max(cp.n_bubbles, 1))()
+    p = cloud_params(cp)
+    nv.check(nv.lib().ofm_sample_cloud(C.byref(p), seed, sample_id, out), "ofm_sample_cloud")
+    return np.array([[b.x, b.y, b.z, b.r] for b in out[: cp.n_bubbles]]).reshape(-1, 4)
+
+
+class Solver:
+    def __init__(self, sp, precision: str = "fp64"):
+        self.sp = sp
+        self.precision = precision
+        self.cfg = solver_config(sp, precision)
+        h = C.c_void_p()
+        nv.check(nv.lib().ofm_solver_create(C.byref(h), C.byref(self.cfg)), "ofm_solver_create")
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            nv.lib().ofm_solver_destroy(self.h)
+            self.h = None
+
+
+class Group:
+    """Host-side arrays of one group (kept alive for the C side)."""
+
+    def __init__(self, N: int, sample_ids: Sequence[int], seed: int, n_sensors: int, n_out: int,
+                 bubbles: Optional[np.ndarray] = None, n_bubbles: int = 0):
+        self.N = N
+        self.M = len(sample_ids)
+        self.ids = np.ascontiguousarray(np.asarray(sample_ids, dtype=np.uint64))
+        self.seed = seed
+        self.qoi = (nv.ofm_qoi * self.M)()
+        self.hist = np.zeros((self.M, max(n_sensors, 0), n_out)) if n_sensors and n_out else None
+        self.bub = None
+        if bubbles is not None:
+            b = np.ascontiguousarray(np.asarray(bubbles, dtype=np.float64).reshape(self.M * n_bubbles, 4))
+            self.bub = b
+        self.c = nv.ofm_group()
+        self.c.N = N
+        self.c.n_samples = self.M
+        self.c.sample_ids = self.ids.ctypes.data_as(C.POINTER(C.c_uint64))
+        self.c.seed = seed
+        self.c.bubbles = self.bub.ctypes.data_as(C.POINTER(nv.ofm_bubble)) if self.bub is not None else None
+        self.c.qoi_out = C.cast(self.qoi, C.POINTER(nv.ofm_qoi))
+        self.c.sensor_hist = (self.hist.ctypes.data_as(C.POINTER(C.c_double))
+                              if self.hist is not None else None)
+
+    def qoi_dicts(self, n_sensors: int) -> List[dict]:
+        out = []
+        for q in self.qoi:
+            out.append(dict(p_peak=q.p_peak, peak_index=q.peak_index, p_peak_xyz=np.array(q.p_peak_xyz[:]),
+                            p_peak_t=q.p_peak_t, p_peak_dist=q.p_peak_dist,
+                            sensor_peak=np.array(q.sensor_peak[:n_sensors]),
+                            totals0=np.array(q.totals0[:]), totals_end=np.array(q.totals_end[:]),
+                            t_final=q.t_final, n_steps=q.n_steps, status=q.status))
+        return out
+
+
+def _torch_stream_ptr():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Batch:
+    """One ofm_batch: groups of samples on their grids, device workspace from torch."""
+
+    def __init__(self, solver: Solver, cloud, groups: List[Group], device: str = "cuda"):
+        import torch
+        self.solver = solver
+        self.cloud = cloud
+        self.cp = cloud_params(cloud)
+        self.groups = groups
+        self.garr = (nv.ofm_group * len(groups))(*[g.c for g in groups])
+        nbytes = C.c_size_t()
+        L = nv.lib()
+        nv.check(L.ofm_batch_workspace_bytes(solver.h, C.byref(self.cp), self.garr, len(groups),
+                                             C.byref(nbytes)), "ofm_batch_workspace_bytes")
+        self.ws_bytes = nbytes.value
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
+        base = self.ws.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        h = C.c_void_p()
+        nv.check(L.ofm_batch_create(C.byref(h), solver.h, C.byref(self.cp), self.garr, len(groups),
+                                    C.c_void_p(aligned), self.ws_bytes, _torch_stream_ptr()),
+                 "ofm_batch_create")
+        self.h = h
+
+    def init(self):
+        nv.check(nv.lib().ofm_batch_init(self.h), "ofm_batch_init")
+
+    def run(self, max_steps: int = 1 << 30) -> int:
+        a = C.c_int()
+        nv.check(nv.lib().ofm_batch_run(self.h, max_steps, C.byref(a)), "ofm_batch_run")
+        return a.value
+
+    def qoi(self, allow_bad: bool = False) -> int:
+        rc = nv.lib().ofm_batch_qoi(self.h)
+        if rc == nv.OFM_ENUMERIC and allow_bad:
+            return rc
+        nv.check(rc, "ofm_batch_qoi")
+        return rc
+
+    def _elem(self):
+        return np.float64 if self.solver.precision == "fp64" else np.float32
+
+    def state(self, group: int, sample: int) -> np.ndarray:
+        N = self.groups[group].N
+        buf = np.empty((7, N, N, N), dtype=self._elem())
+        nv.check(nv.lib().ofm_batch_copy_state(self.h, group, sample, buf.ctypes.data_as(C.c_void_p),
+                                               buf.nbytes), "ofm_batch_copy_state")
+        return buf
+
+    def set_state(self, group: int, sample: int, Q: np.ndarray):
+        buf = np.ascontiguousarray(Q, dtype=self._elem())
+        nv.check(nv.lib().ofm_batch_set_state(self.h, group, sample, buf.ctypes.data_as(C.c_void_p),
+                                              buf.nbytes), "ofm_batch_set_state")
+
+    def cell_steps(self) -> float:
+        v = C.c_double()
+        nv.check(nv.lib().ofm_batch_cell_steps(self.h, C.byref(v)), "ofm_batch_cell_steps")
+        return v.value
+
+    def launches(self) -> int:
+        v = C.c_int64()
+        nv.check(nv.lib().ofm_batch_kernel_launches(self.h, C.byref(v)), "ofm_batch_kernel_launches")
+        return v.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            nv.lib().ofm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+def make_group(sp, N: int, ids: Sequence[int], seed: int, bubbles=None, n_bubbles: int = 0) -> Group:
+    return Group(N, ids, seed, len(sp.sensors), sp.n_out_times, bubbles=bubbles, n_bubbles=n_bubbles)
+
+
+def solve_batch_host(solver: Solver, cloud, groups: List[Group], workspace=None) -> int:
+    """ofm_solve_batch with host arrays (library-allocated workspace unless given)."""
+    cp = cloud_params(cloud)
+    garr = (nv.ofm_group * len(groups))(*[g.c for g in groups])
+    ws_ptr = C.c_void_p(0)
+    ws_bytes = 0
+    if workspace is not None:
+        ws_ptr = C.c_void_p(workspace[0])
+        ws_bytes = workspace[1]
+    stream = _torch_stream_ptr()
+    return nv.lib().ofm_solve_batch(solver.h, C.byref(cp), garr, len(groups), ws_ptr, ws_bytes, stream)
+
+
+def estimate(pairs: Sequence[np.ndarray], W: Sequence[float]) -> dict:
+    """ofm_estimate on per-level (M_l, 2) arrays of (q_l, q_{l-1})."""
+    L = len(pairs) - 1
+    arrs = [np.ascontiguousarray(p, dtype=np.float64) for p in pairs]
+    M = (C.c_int64 * (L + 1))(*[a.shape[0] for a in arrs])
+    ptrs = (C.POINTER(C.c_double) * (L + 1))(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs])
+    Wc = (C.c_double * (L + 1))(*W)
+    out = nv.ofm_estimate_out()
+    nv.check(nv.lib().ofm_estimate(L, M, ptrs, Wc, C.byref(out)), "ofm_estimate")
+    n = L + 1
+    return dict(alpha=np.array(out.alpha[:n]), sigma2=np.array(out.sigma2[:n]), cov=np.array(out.cov[:n]),
+                sigma_tilde2=np.array(out.sigma_tilde2[:n]), mean=out.mean, eps2=out.eps2)
+
+
+def optimal_samples(sigma_tilde2, W, target: float, mode: str = "tol", M_done=None) -> np.ndarray:
+    L = len(W) - 1
+    s = (C.c_double * (L + 1))(*sigma_tilde2)
+    Wc = (C.c_double * (L + 1))(*W)
+    Md = (C.c_int64 * (L + 1))(*M_done) if M_done is not None else None
+    out = (C.c_int64 * (L + 1))()
+    m = nv.OFM_MODE_TOL if mode == "tol" else nv.OFM_MODE_BUDGET
+    nv.check(nv.lib().ofm_optimal_samples(L, s, Wc, Md, target, m, out), "ofm_optimal_samples")
+    return np.array(out[:])
+
+
+def warmup_samples(W) -> np.ndarray:
+    L = len(W) - 1
+    Wc = (C.c_double * (L + 1))(*W)
+    out = (C.c_int64 * (L + 1))()
+    nv.check(nv.lib().ofm_warmup_samples(L, Wc, out), "ofm_warmup_samples")
+    return np.array(out[:])

@@ -1,0 +1,64 @@
+"""Build the CUDA library ``libofmlmc.so`` in-tree for sm_103a.
+
+Two translation units compiled in parallel: ``csrc/solver.cu`` (kernels and
+the device-facing C ABI) with nvcc, and ``csrc/host.cpp`` (sampler,
+estimator, errors) with g++ -ffp-contract=off.  The CUDA runtime is linked
+statically so the library has no run-time dependency beyond the driver.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libofmlmc.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC = os.environ.get("NVCC", "nvcc")
+
+SOURCES = {
+    "solver.o": [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                 "-I", INCLUDE, "-c", os.path.join(CSRC, "solver.cu")],
+    "host.o": ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I", INCLUDE,
+               "-c", os.path.join(CSRC, "host.cpp")],
+}
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "ofmlmc.h"), __file__]
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if not force and not _stale():
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    procs = []
+    for obj, cmd in SOURCES.items():
+        out = os.path.join(BUILD, obj)
+        procs.append((obj, subprocess.Popen(cmd + ["-o", out], stdout=subprocess.PIPE,
+                                            stderr=subprocess.STDOUT, text=True)))
+    for obj, p in procs:
+        log, _ = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError(f"compiling {obj} failed:\n{log}")
+        if verbose and log:
+            print(log)
+    link = [NVCC, *ARCH, "-shared", "-o", LIB + ".tmp",
+            os.path.join(BUILD, "solver.o"), os.path.join(BUILD, "host.o")]
+    r = subprocess.run(link, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"linking failed:\n{r.stdout}{r.stderr}")
+    os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True))

@@ -1,0 +1,236 @@
+// Host-side parts of the C ABI: error reporting, the cloud sampler and the
+// OF-MLMC estimator (Section 2.4 of the paper).  All FP64; compiled with
+// -ffp-contract=off so the sampler's arithmetic rounds identically on x86 and
+// Arm hosts.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "ofmlmc.h"
+#include "internal.h"
+
+namespace ofm {
+
+static thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+void clear_error() { g_err[0] = '\0'; }
+
+}  // namespace ofm
+
+using namespace ofm;
+
+extern "C" const char* ofm_last_error(void) { return g_err; }
+
+extern "C" const char* ofm_version(void) { return "ofmlmc-gb300 1.0 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// Cloud sampler.  SplitMix64 (Steele, Lea & Flood 2014): the state advances by
+// the golden-ratio increment and each output is the state passed through two
+// xor-shift-multiply rounds and a final xor-shift.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct SplitMix {
+    uint64_t s;
+    uint64_t next() {
+        s += 0x9E3779B97F4A7C15ull;
+        uint64_t z = s;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double unit() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+};
+
+}  // namespace
+
+extern "C" int ofm_sample_cloud(const ofm_cloud_params* p, uint64_t seed, uint64_t sample_id,
+                                ofm_bubble* out) {
+    if (!p || !out) return fail(OFM_EINVAL, "ofm_sample_cloud: NULL argument");
+    if (p->n_bubbles < 0 || !(p->cloud_radius >= 0.0) || !(p->r_min > 0.0) ||
+        !(p->r_max >= p->r_min))
+        return fail(OFM_EINVAL, "ofm_sample_cloud: bad cloud parameters");
+    SplitMix g{seed ^ (sample_id * 0x9E3779B97F4A7C15ull)};
+    const double R = p->cloud_radius;
+    const double c = 0.5 * p->domain_L;
+    for (int b = 0; b < p->n_bubbles; ++b) {
+        double x, y, z;
+        for (;;) {
+            x = (2.0 * g.unit() - 1.0) * R;
+            y = (2.0 * g.unit() - 1.0) * R;
+            z = (2.0 * g.unit() - 1.0) * R;
+            if (x * x + y * y + z * z <= R * R) break;
+        }
+        double r;
+        if (p->radius_law == OFM_RADII_UNIFORM) {
+            r = p->r_min + g.unit() * (p->r_max - p->r_min);
+        } else {
+            for (int tries = 0;; ++tries) {
+                if (tries > 100000000) return fail(OFM_EINVAL, "ofm_sample_cloud: radius law never hits [r_min, r_max]");
+                double u1 = g.unit();
+                double u2 = g.unit();
+                double n = std::sqrt(-2.0 * std::log(1.0 - u1)) * std::cos(2.0 * M_PI * u2);
+                r = std::exp(p->ln_mu + p->ln_sigma * n);
+                if (p->r_min <= r && r <= p->r_max) break;
+            }
+        }
+        out[b].x = c + x;
+        out[b].y = c + y;
+        out[b].z = c + z;
+        out[b].r = r;
+    }
+    return OFM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Estimator (Section 2.4).
+// ---------------------------------------------------------------------------
+namespace {
+
+double mean_of(const std::vector<double>& x) {
+    double s = 0.0;
+    for (double v : x) s += v;
+    return s / (double)x.size();
+}
+
+double var_of(const std::vector<double>& x) {
+    const double m = mean_of(x);
+    double s = 0.0;
+    for (double v : x) s += (v - m) * (v - m);
+    return s / (double)(x.size() - 1);
+}
+
+double cov_of(const std::vector<double>& x, const std::vector<double>& y) {
+    const double mx = mean_of(x), my = mean_of(y);
+    double s = 0.0;
+    for (size_t i = 0; i < x.size(); ++i) s += (x[i] - mx) * (y[i] - my);
+    return s / (double)(x.size() - 1);
+}
+
+// Thomas algorithm for the symmetric tridiagonal system of Eq. (alpha-matvec):
+// row l: -cov[l] W[l] a_{l-1} + sigma2[l] (W[l] + W[l+1]) a_l - cov[l+1] W[l+1] a_{l+1}
+//        = (l == L-1) ? cov[L] W[L] : 0.
+int solve_alpha(int L, const double* sigma2, const double* cov, const double* W, double* alpha) {
+    alpha[L] = 1.0;
+    if (L == 0) return OFM_OK;
+    std::vector<double> a(L), b(L), c(L), d(L);
+    for (int l = 0; l < L; ++l) {
+        b[l] = sigma2[l] * (W[l + 1] + W[l]);
+        a[l] = l > 0 ? -cov[l] * W[l] : 0.0;
+        c[l] = l + 1 < L ? -cov[l + 1] * W[l + 1] : 0.0;
+        d[l] = l == L - 1 ? cov[L] * W[L] : 0.0;
+    }
+    for (int l = 1; l < L; ++l) {
+        if (b[l - 1] == 0.0) return fail(OFM_ENUMERIC, "ofm_estimate: singular coefficient system");
+        const double m = a[l] / b[l - 1];
+        b[l] -= m * c[l - 1];
+        d[l] -= m * d[l - 1];
+    }
+    if (b[L - 1] == 0.0) return fail(OFM_ENUMERIC, "ofm_estimate: singular coefficient system");
+    alpha[L - 1] = d[L - 1] / b[L - 1];
+    for (int l = L - 2; l >= 0; --l) alpha[l] = (d[l] - c[l] * alpha[l + 1]) / b[l];
+    return OFM_OK;
+}
+
+}  // namespace
+
+extern "C" int ofm_estimate(int L, const int64_t* M, const double* const* q, const double* W,
+                            ofm_estimate_out* out) {
+    if (L < 0 || L >= OFM_MAX_LEVELS || !M || !q || !W || !out)
+        return fail(OFM_EINVAL, "ofm_estimate: bad arguments");
+    for (int l = 0; l <= L; ++l) {
+        if (M[l] < 2 || !q[l]) return fail(OFM_EINVAL, "ofm_estimate: level %d needs >= 2 samples", l);
+        if (!(W[l] > 0.0)) return fail(OFM_EINVAL, "ofm_estimate: W[%d] must be > 0", l);
+    }
+    std::memset(out, 0, sizeof(*out));
+    std::vector<std::vector<double>> fine(L + 1), coarse(L + 1);
+    for (int l = 0; l <= L; ++l) {
+        fine[l].resize(M[l]);
+        coarse[l].resize(M[l]);
+        for (int64_t i = 0; i < M[l]; ++i) {
+            fine[l][i] = q[l][2 * i];
+            coarse[l][i] = q[l][2 * i + 1];
+        }
+    }
+    for (int l = 0; l <= L; ++l) {
+        std::vector<double> pooled = fine[l];
+        if (l < L) pooled.insert(pooled.end(), coarse[l + 1].begin(), coarse[l + 1].end());
+        out->sigma2[l] = var_of(pooled);
+        out->cov[l] = l > 0 ? cov_of(fine[l], coarse[l]) : 0.0;
+    }
+    int rc = solve_alpha(L, out->sigma2, out->cov, W, out->alpha);
+    if (rc != OFM_OK) return rc;
+    double mean = 0.0, eps2 = 0.0;
+    for (int l = 0; l <= L; ++l) {
+        std::vector<double> d(M[l]);
+        for (int64_t i = 0; i < M[l]; ++i)
+            d[i] = l == 0 ? out->alpha[0] * fine[0][i]
+                          : out->alpha[l] * fine[l][i] - out->alpha[l - 1] * coarse[l][i];
+        out->sigma_tilde2[l] = var_of(d);
+        mean += mean_of(d);
+        eps2 += out->sigma_tilde2[l] / (double)M[l];
+    }
+    out->mean = mean;
+    out->eps2 = eps2;
+    return OFM_OK;
+}
+
+extern "C" int ofm_warmup_samples(int L, const double* W, int64_t* M_out) {
+    if (L < 0 || L >= OFM_MAX_LEVELS || !W || !M_out) return fail(OFM_EINVAL, "ofm_warmup_samples: bad arguments");
+    for (int l = 0; l <= L; ++l) {
+        if (!(W[l] > 0.0)) return fail(OFM_EINVAL, "ofm_warmup_samples: W[%d] must be > 0", l);
+        M_out[l] = (int64_t)std::ceil(W[L] / W[l] / std::ldexp(1.0, L - l));
+    }
+    return OFM_OK;
+}
+
+extern "C" int ofm_optimal_samples(int L, const double* st2, const double* W, const int64_t* M_done,
+                                   double target, int mode, int64_t* M_out) {
+    if (L < 0 || L >= OFM_MAX_LEVELS || !st2 || !W || !M_out || !(target > 0.0) ||
+        (mode != OFM_MODE_TOL && mode != OFM_MODE_BUDGET))
+        return fail(OFM_EINVAL, "ofm_optimal_samples: bad arguments");
+    const int n = L + 1;
+    bool fixed[OFM_MAX_LEVELS] = {false};
+    for (;;) {
+        double rem = mode == OFM_MODE_TOL ? target * target : target;
+        double total = 0.0;
+        for (int l = 0; l < n; ++l) {
+            if (fixed[l])
+                rem -= mode == OFM_MODE_TOL ? st2[l] / (double)M_done[l] : (double)M_done[l] * W[l];
+            else
+                total += std::sqrt(st2[l] * W[l]);
+        }
+        if (!(rem > 0.0))
+            return fail(OFM_EINVAL, "ofm_optimal_samples: target already consumed by kept samples");
+        const double t = mode == OFM_MODE_TOL ? std::sqrt(rem) : rem;
+        bool newly = false;
+        for (int l = 0; l < n; ++l) {
+            if (fixed[l]) {
+                M_out[l] = M_done[l];
+                continue;
+            }
+            double raw = mode == OFM_MODE_TOL ? (1.0 / (t * t)) * std::sqrt(st2[l] / W[l]) * total
+                                              : t * std::sqrt(st2[l] / W[l]) / total;
+            M_out[l] = (int64_t)std::ceil(raw);
+            if (M_done && M_out[l] < M_done[l]) {
+                fixed[l] = true;
+                newly = true;
+            }
+        }
+        if (!newly) {
+            for (int l = 0; l < n; ++l)
+                if (fixed[l]) M_out[l] = M_done[l];
+            return OFM_OK;
+        }
+    }
+}

@@ -1,0 +1,315 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP64 path, relative L1 per variable <= 1e-12 after one step and
+relative QoI error <= 1e-9 at t_end, on the same seeded clouds.  FP32 stencil
+path: its QoI errors against the oracle are measured and bounded loosely
+(the FP32 pressure loses about two digits to the cancellation
+E - rho|u|^2/2 - Pi with Pi/p ~ 40 in the liquid).
+"""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import cloud as ocloud
+from oracle import solver as osolver
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1705_04374_gb300 import api  # noqa: E402
+from paper_1705_04374_gb300 import native as nv  # noqa: E402
+
+THREADS = max(1, min(32, os.cpu_count() or 1))
+TOL_STEP_FP64 = 1e-12
+TOL_QOI_FP64 = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    torch.cuda.set_device(0)
+
+
+def rel_l1(a, b):
+    a = a.reshape(7, -1).astype(np.float64)
+    b = b.reshape(7, -1)
+    num = np.abs(a - b).sum(1)
+    den = np.abs(b).sum(1)
+    out = np.where(den > 0, num / np.where(den > 0, den, 1.0), num)
+    return out
+
+
+def oracle_one_step(sp, N, bub):
+    Q0 = osolver.init_cloud(sp, N, bub)
+    g = osolver.grid_from_params(sp, N)
+    dt = sp.cfl * g.h / osolver.max_speed(g, Q0)
+    if dt > sp.t_end / osolver.Units(sp.domain_L, sp.p_liq).t_ref:
+        dt = sp.t_end / osolver.Units(sp.domain_L, sp.p_liq).t_ref
+    return osolver.rk3_step(g, Q0, dt)
+
+
+def gpu_batch(sp, precision, groups_spec, cloud, seed=W.BASE_SEED):
+    s = api.Solver(sp, precision)
+    groups = [api.make_group(sp, N, ids, seed) for (N, ids) in groups_spec]
+    b = api.Batch(s, cloud, groups)
+    return s, groups, b
+
+
+# ----------------------------------------------------------------- one step
+
+@pytest.mark.parametrize("N", [8, 16, 24])
+def test_one_step_fp64_relative_l1(N):
+    w = W.tiny(N, 4)
+    sp = w.solver
+    ids = [0, 5, 9]
+    s, groups, b = gpu_batch(sp, "fp64", [(N, ids)], w.cloud)
+    b.init()
+    b.run(1)
+    for i, sid in enumerate(ids):
+        bub = ocloud.sample_cloud(w.cloud, W.BASE_SEED, sid)
+        ref = oracle_one_step(sp, N, bub)
+        r = rel_l1(b.state(0, i), ref)
+        assert np.all(r <= TOL_STEP_FP64), (sid, r)
+    b.close()
+
+
+def test_one_step_fp64_periodic_smooth_field():
+    N = 16
+    sp = W.with_solver(W.tiny(N), bc=1).solver
+    g = osolver.grid_from_params(sp, N)
+    Wp = W.smooth_periodic_primitives(N, seed=21, amp=0.1)
+    Q0 = osolver.prim_to_cons(g, Wp.reshape(7, -1)).reshape(7, N, N, N)
+    s, groups, b = gpu_batch(sp, "fp64", [(N, [0])], W.cloud_uniform(1))
+    b.init()
+    b.set_state(0, 0, Q0)
+    b.run(1)
+    dt = sp.cfl * g.h / osolver.max_speed(g, Q0)
+    ref = osolver.rk3_step(g, Q0, dt)
+    assert np.all(rel_l1(b.state(0, 0), ref) <= TOL_STEP_FP64)
+    b.close()
+
+
+def test_one_step_fp32_close_to_oracle():
+    N = 16
+    w = W.tiny(N, 4)
+    sp = w.solver
+    s, groups, b = gpu_batch(sp, "fp32", [(N, [0, 1])], w.cloud)
+    b.init()
+    b.run(1)
+    for i in range(2):
+        ref = oracle_one_step(sp, N, ocloud.sample_cloud(w.cloud, W.BASE_SEED, i))
+        r = rel_l1(b.state(0, i), ref)
+        assert np.all(r <= 1e-4), r
+    b.close()
+
+
+# ----------------------------------------------------------------- t_end QoIs
+
+QOI_KEYS = ("p_peak", "p_peak_t", "t_final")
+
+
+def oracle_qois(sp, N, cloud, ids, seed=W.BASE_SEED):
+    def one(sid):
+        q, hist, _ = osolver.solve(sp, N, ocloud.sample_cloud(cloud, seed, sid))
+        return q, hist
+    with ThreadPoolExecutor(THREADS) as ex:
+        return list(ex.map(one, ids))
+
+
+def compare_qoi(qg, hg, qo, ho, tol, n_sens):
+    assert qg["status"] == 0 and qo["status"] == 0
+    assert qg["n_steps"] == qo["n_steps"]
+    for k in QOI_KEYS:
+        assert abs(qg[k] - qo[k]) <= tol * abs(qo[k]), (k, qg[k], qo[k])
+    assert np.all(np.abs(qg["sensor_peak"] - qo["sensor_peak"]) <= tol * np.abs(qo["sensor_peak"]))
+    assert np.allclose(qg["totals_end"], qo["totals_end"], rtol=tol, atol=1e-14)
+    assert np.allclose(qg["totals0"], qo["totals0"], rtol=1e-13, atol=1e-15)
+    if hg is not None and ho.size:
+        assert np.all(np.abs(hg - ho) <= tol * np.abs(ho))
+
+
+def test_two_level_config_fp64_qois_at_t_end():
+    """The two-level FP64 workload: 16 clouds of 4 bubbles on 16^3, 4 on 32^3
+    and their 16^3 partners, all in one uneven batch."""
+    w = W.cfg1()
+    sp = w.solver
+    coarse_ids = list(range(16))
+    fine_ids = list(range(100, 104))
+    s, groups, b = gpu_batch(sp, "fp64", [(16, coarse_ids), (32, fine_ids), (16, fine_ids)], w.cloud)
+    b.init()
+    while b.run(64) > 0:
+        pass
+    b.qoi()
+    ns = len(sp.sensors)
+    for gi, (N, ids) in enumerate([(16, coarse_ids), (32, fine_ids), (16, fine_ids)]):
+        ref = oracle_qois(sp, N, w.cloud, ids)
+        got = groups[gi].qoi_dicts(ns)
+        for i in range(len(ids)):
+            compare_qoi(got[i], groups[gi].hist[i], ref[i][0], ref[i][1], TOL_QOI_FP64, ns)
+            assert got[i]["peak_index"] == ref[i][0]["peak_index"]
+    b.close()
+
+
+def test_fp32_qoi_errors_are_small_and_stated(capsys):
+    w = W.tiny(32, 4, samples=3)
+    sp = w.solver
+    ids = [0, 1, 2]
+    s, groups, b = gpu_batch(sp, "fp32", [(32, ids)], w.cloud)
+    b.init()
+    while b.run(64) > 0:
+        pass
+    b.qoi()
+    got = groups[0].qoi_dicts(len(sp.sensors))
+    ref = oracle_qois(sp, 32, w.cloud, ids)
+    errs = {"p_peak": [], "sensor_peak": [], "hist": []}
+    for i in range(3):
+        qo, ho = ref[i]
+        qg = got[i]
+        assert qg["status"] == 0
+        errs["p_peak"].append(abs(qg["p_peak"] - qo["p_peak"]) / qo["p_peak"])
+        errs["sensor_peak"].append(float(np.max(np.abs(qg["sensor_peak"] - qo["sensor_peak"]) / qo["sensor_peak"])))
+        errs["hist"].append(float(np.max(np.abs(groups[0].hist[i] - ho)) / np.max(np.abs(ho))))
+    with capsys.disabled():
+        print("\nFP32 vs FP64 oracle, relative QoI errors (32^3, 4 bubbles):",
+              {k: f"{max(v):.2e}" for k, v in errs.items()})
+    assert max(errs["p_peak"]) < 1e-3
+    assert max(errs["sensor_peak"]) < 1e-2
+    assert max(errs["hist"]) < 1e-2
+    b.close()
+
+
+# ----------------------------------------------------------------- invariants on the GPU
+
+def test_conservation_periodic_fp64_and_fp32():
+    N = 16
+    sp = W.with_solver(W.tiny(N), bc=1).solver
+    g = osolver.grid_from_params(sp, N)
+    Q0 = osolver.prim_to_cons(g, W.smooth_periodic_primitives(N, seed=4).reshape(7, -1)).reshape(7, N, N, N)
+    for prec, tol in (("fp64", 1e-13), ("fp32", 2e-6)):
+        s, groups, b = gpu_batch(sp, prec, [(N, [0])], W.cloud_uniform(1))
+        b.init()
+        b.set_state(0, 0, Q0)
+        b.run(6)
+        Q = b.state(0, 0).astype(np.float64)
+        t0 = osolver.totals(g, Q0)
+        t1 = osolver.totals(g, Q)
+        scale = np.array([1.0, 0.005, 1.0, 1.0, 1.0, 40.0])
+        assert np.all(np.abs(t1 - t0) <= tol * scale), (prec, t1 - t0)
+        b.close()
+
+
+def test_interface_equilibrium_fp64():
+    N = 16
+    sp = W.with_solver(W.tiny(N), bc=1).solver
+    g = osolver.grid_from_params(sp, N)
+    x = (np.arange(N) + 0.5) / N
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    d = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+    a2 = np.clip(0.5 * (1 - np.tanh((d - 0.3) * N)), 1e-6, 1 - 1e-6)
+    Wp = np.zeros((7, N, N, N))
+    Wp[0], Wp[1], Wp[2], Wp[3], Wp[4], Wp[5], Wp[6] = (1 - a2), a2 * 0.005, 0.5, -0.25, 0.125, 1.0, a2
+    Q0 = osolver.prim_to_cons(g, Wp.reshape(7, -1)).reshape(7, N, N, N)
+    s, groups, b = gpu_batch(sp, "fp64", [(N, [0])], W.cloud_uniform(1))
+    b.init()
+    b.set_state(0, 0, Q0)
+    b.run(10)
+    Wn = osolver.cons_to_prim(g, b.state(0, 0).reshape(7, -1))
+    assert np.max(np.abs(Wn[5] - 1.0)) < 1e-12
+    assert np.max(np.abs(Wn[2] - 0.5)) < 1e-12
+    b.close()
+
+
+def test_uneven_batch_equals_separate_batches_bitwise():
+    w = W.tiny(16, 4)
+    sp = w.solver
+    spec = [(16, [0, 1, 2]), (32, [3, 4]), (8, [5])]
+    s, groups, b = gpu_batch(sp, "fp32", spec, w.cloud)
+    b.init()
+    while b.run(64) > 0:
+        pass
+    b.qoi()
+    together = [g.qoi_dicts(1) for g in groups]
+    b.close()
+    for gi, (N, ids) in enumerate(spec):
+        s2, g2, b2 = gpu_batch(sp, "fp32", [(N, ids)], w.cloud)
+        b2.init()
+        while b2.run(64) > 0:
+            pass
+        b2.qoi()
+        alone = g2[0].qoi_dicts(1)
+        for a, c in zip(together[gi], alone):
+            assert a["p_peak"] == c["p_peak"] and a["n_steps"] == c["n_steps"]
+            assert np.array_equal(a["sensor_peak"], c["sensor_peak"])
+            assert np.array_equal(a["totals_end"], c["totals_end"])
+        b2.close()
+
+
+def test_runs_are_deterministic():
+    w = W.tiny(16, 4)
+    sp = w.solver
+    res = []
+    for _ in range(2):
+        s, groups, b = gpu_batch(sp, "fp32", [(16, [0, 1, 2, 3])], w.cloud)
+        b.init()
+        b.run(5)
+        res.append(np.stack([b.state(0, i) for i in range(4)]))
+        b.close()
+    assert np.array_equal(res[0].view(np.uint32), res[1].view(np.uint32))
+
+
+def test_corrupted_sample_is_excluded_and_reported():
+    """Fault injection on the host: one sample's initial state holds a NaN."""
+    w = W.tiny(16, 4)
+    sp = w.solver
+    s, groups, b = gpu_batch(sp, "fp64", [(16, [0, 1, 2])], w.cloud)
+    b.init()
+    Q = b.state(0, 1).copy()
+    Q[5, 3, 4, 5] = np.nan
+    b.set_state(0, 1, Q)
+    while b.run(64) > 0:
+        pass
+    assert b.qoi(allow_bad=True) == nv.OFM_ENUMERIC
+    q = groups[0].qoi_dicts(1)
+    assert q[1]["status"] & nv.OFM_ST_NONFINITE
+    assert q[1]["n_steps"] == 0
+    assert q[0]["status"] == 0 and q[2]["status"] == 0
+    assert q[0]["t_final"] == pytest.approx(sp.t_end, rel=1e-15)
+    b.close()
+
+
+def test_solve_level_host_api_matches_batch():
+    w = W.tiny(16, 4)
+    sp = w.solver
+    s = api.Solver(sp, "fp64")
+    g = api.make_group(sp, 16, [0, 1], W.BASE_SEED)
+    rc = api.solve_batch_host(s, w.cloud, [g])
+    assert rc == nv.OFM_OK, nv.lib().ofm_last_error()
+    ref = oracle_qois(sp, 16, w.cloud, [0, 1])
+    for i in range(2):
+        compare_qoi(g.qoi_dicts(1)[i], g.hist[i], ref[i][0], ref[i][1], TOL_QOI_FP64, 1)
+
+
+# ----------------------------------------------------------------- full size, sampled
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp64", TOL_STEP_FP64)])
+def test_full_size_ensemble_one_step_sampled(precision, tol):
+    """512 clouds of 20 bubbles on 64^3 (the throughput workload) in the same
+    launch configuration as the benchmark; samples checked one by one."""
+    w = W.cfg2(precision)
+    sp = w.solver
+    M = 512
+    s, groups, b = gpu_batch(sp, precision, [(64, list(range(M)))], w.cloud)
+    b.init()
+    b.run(1)
+    picks = [0, 257, 511]
+    with ThreadPoolExecutor(THREADS) as ex:
+        refs = list(ex.map(lambda i: oracle_one_step(sp, 64, ocloud.sample_cloud(w.cloud, W.BASE_SEED, i)),
+                           picks))
+    for i, ref in zip(picks, refs):
+        r = rel_l1(b.state(0, i), ref)
+        assert np.all(r <= tol), (i, r)
+    b.close()

@@ -1,0 +1,107 @@
+"""CPU tests of the C-ABI library: loads, exports the header's symbols, and its
+host-side parts (sampler, estimator, validation) agree with the oracle.
+No device work is requested here."""
+import ctypes as C
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import cloud as ocloud
+from oracle import estimator as E
+from paper_1705_04374_gb300 import api
+from paper_1705_04374_gb300 import native as nv
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "ofmlmc.h")
+
+
+def header_functions():
+    text = open(HEADER).read()
+    return re.findall(r"^\s*(?:const char\*|int|void)\s+(ofm_\w+)\s*\(", text, re.M)
+
+
+def test_library_exports_every_declared_function():
+    names = header_functions()
+    assert len(names) >= 18
+    L = nv.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(nv.SIGNATURES), "binding and header list different functions"
+
+
+def test_struct_sizes_match_header_layout():
+    assert C.sizeof(nv.ofm_bubble) == 32
+    assert C.sizeof(nv.ofm_qoi) == 8 * (1 + 3 + 1 + 1 + 1 + 8 + 6 + 6 + 1) + 8
+    assert C.sizeof(nv.ofm_estimate_out) == 8 * (4 * 16 + 2)
+
+
+@pytest.mark.parametrize("cp", [W.cloud_uniform(4), W.cloud_uniform(50), W.cloud_paper500()],
+                         ids=["uniform4", "uniform50", "paper500"])
+def test_sampler_bitwise_identical_to_oracle(cp):
+    for sid in (0, 1, 17, 2 ** 40 + 3):
+        a = api.sample_cloud(cp, W.BASE_SEED, sid)
+        b = ocloud.sample_cloud(cp, W.BASE_SEED, sid)
+        assert a.shape == b.shape
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+def test_estimator_matches_oracle():
+    for L, M in ((1, [40, 7]), (3, [300, 50, 9, 3])):
+        pairs = W.toy_levels(M, L, 0.4, 0.7, seed=11)
+        Wc = [1.0] + [16.0 ** l + 16.0 ** (l - 1) for l in range(1, L + 1)]
+        a = api.estimate(pairs, Wc)
+        b = E.estimate(pairs, Wc)
+        for k in ("alpha", "sigma2", "cov", "sigma_tilde2"):
+            assert np.allclose(a[k], b[k], rtol=1e-12, atol=1e-14), k
+        assert abs(a["mean"] - b["mean"]) < 1e-12 * max(1, abs(b["mean"]))
+        assert abs(a["eps2"] - b["eps2"]) < 1e-12 * b["eps2"]
+
+
+def test_optimal_and_warmup_samples_match_oracle():
+    st2 = [1.0, 0.2, 0.04, 0.01]
+    Wc = [1.0, 17.0, 272.0, 4352.0]
+    for tau in (0.05, 0.01, 0.003):
+        assert list(api.optimal_samples(st2, Wc, tau, "tol")) == list(E.optimal_M(st2, Wc, tau, "tol"))
+    for B in (1e4, 3e6):
+        assert list(api.optimal_samples(st2, Wc, B, "budget")) == list(E.optimal_M(st2, Wc, B, "budget"))
+    done = [200000, 10, 1, 1]
+    assert list(api.optimal_samples(st2, Wc, 0.01, "tol", done)) == \
+        list(E.optimal_M_keep(st2, Wc, done, 0.01, "tol"))
+    assert list(api.warmup_samples([16.0 ** l for l in range(4)])) == [512, 64, 8, 1]
+    assert list(api.warmup_samples(Wc)) == list(E.warmup_M(Wc))
+
+
+def test_invalid_arguments_are_rejected_on_the_host():
+    L = nv.lib()
+    cfg = api.solver_config(W.SolverParams(), "fp64")
+    cfg.cfl = -1.0
+    h = C.c_void_p()
+    assert L.ofm_solver_create(C.byref(h), C.byref(cfg)) == nv.OFM_EINVAL
+    assert b"non-physical" in L.ofm_last_error()
+    # estimator needs two samples per level
+    with pytest.raises(nv.OfmError):
+        api.estimate([np.zeros((1, 2)), np.zeros((5, 2))], [1.0, 2.0])
+    # grid sizes must be multiples of the tile edge
+    s = api.Solver(W.SolverParams(), "fp32")
+    g = api.make_group(W.SolverParams(), 20, [0], 1)
+    cp = api.cloud_params(W.cloud_uniform(2))
+    garr = (nv.ofm_group * 1)(g.c)
+    n = C.c_size_t()
+    assert L.ofm_batch_workspace_bytes(s.h, C.byref(cp), garr, 1, C.byref(n)) == nv.OFM_EINVAL
+
+
+def test_workspace_size_accounts_for_three_state_buffers():
+    sp = W.SolverParams()
+    L = nv.lib()
+    for prec, es in (("fp64", 8), ("fp32", 4)):
+        s = api.Solver(sp, prec)
+        g = api.make_group(sp, 64, list(range(3)), 1)
+        cp = api.cloud_params(W.cloud_uniform(20))
+        garr = (nv.ofm_group * 1)(g.c)
+        n = C.c_size_t()
+        nv.check(L.ofm_batch_workspace_bytes(s.h, C.byref(cp), garr, 1, C.byref(n)), "ws")
+        state = 3 * 3 * 7 * 64 ** 3 * es
+        assert state <= n.value < state * 1.05
