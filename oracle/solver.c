@@ -82,16 +82,17 @@ typedef struct {
 /* ------------------------------------------------------------------ */
 static double clamp01(double a) { return a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a); }
 
+/* The bracketed factors are per-run constants. */
 static double mix_gamma(const orc_grid* g, double a2) {
     double a = clamp01(a2);
     FL(4); /* 1 - a, two products by per-run constants, one add */
-    return (1.0 - a) / (g->gamma1 - 1.0) + a / (g->gamma2 - 1.0);
+    return (1.0 - a) * (1.0 / (g->gamma1 - 1.0)) + a * (1.0 / (g->gamma2 - 1.0));
 }
 static double mix_pi(const orc_grid* g, double a2) {
     double a = clamp01(a2);
     FL(3); /* two products by per-run constants, one add (1 - a shared) */
-    return (1.0 - a) * g->gamma1 * g->pc1 / (g->gamma1 - 1.0)
-         + a * g->gamma2 * g->pc2 / (g->gamma2 - 1.0);
+    return (1.0 - a) * (g->gamma1 * g->pc1 / (g->gamma1 - 1.0))
+         + a * (g->gamma2 * g->pc2 / (g->gamma2 - 1.0));
 }
 
 /* Q -> W = (a1r1, a2r2, u, v, w, p, a2) */
@@ -161,9 +162,9 @@ static double sound2(const orc_grid* g, const double* w) {
 /* the five averages given in reverse order.                             */
 /* ------------------------------------------------------------------ */
 double orc_weno5(double a, double b, double c, double d, double e, double eps) {
-    double q0 = (2.0 * a - 7.0 * b + 11.0 * c) / 6.0;
-    double q1 = (-b + 5.0 * c + 2.0 * d) / 6.0;
-    double q2 = (2.0 * c + 5.0 * d - e) / 6.0;
+    double q0 = (2.0 * a - 7.0 * b + 11.0 * c) * (1.0 / 6.0);
+    double q1 = (-b + 5.0 * c + 2.0 * d) * (1.0 / 6.0);
+    double q2 = (2.0 * c + 5.0 * d - e) * (1.0 / 6.0);
     double t, s;
     t = a - 2.0 * b + c;
     s = a - 4.0 * b + 3.0 * c;

@@ -1,7 +1,8 @@
 """Build the CUDA library ``libofmlmc.so`` in-tree for sm_103a.
 
-Two translation units compiled in parallel: ``csrc/solver.cu`` (kernels and
-the device-facing C ABI) with nvcc, and ``csrc/host.cpp`` (sampler,
+Four translation units compiled in parallel: the solver kernels once per
+precision (``kernels_fp64.cu`` without FMA contraction, ``kernels_fp32.cu``),
+the device-facing C ABI (``solver.cu``) with nvcc, and ``host.cpp`` (sampler,
 estimator, errors) with g++ -ffp-contract=off.  The CUDA runtime is linked
 statically so the library has no run-time dependency beyond the driver.
 """
@@ -20,9 +21,12 @@ LIB = os.path.join(HERE, "libofmlmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
+_NV = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 SOURCES = {
-    "solver.o": [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                 "-I", INCLUDE, "-c", os.path.join(CSRC, "solver.cu")],
+    # FP64 kernels round exactly like the FP64 reference: no FMA contraction
+    "kernels_fp64.o": _NV + ["-fmad=false", "-c", os.path.join(CSRC, "kernels_fp64.cu")],
+    "kernels_fp32.o": _NV + ["-c", os.path.join(CSRC, "kernels_fp32.cu")],
+    "solver.o": _NV + ["-c", os.path.join(CSRC, "solver.cu")],
     "host.o": ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I", INCLUDE,
                "-c", os.path.join(CSRC, "host.cpp")],
 }
@@ -51,8 +55,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"compiling {obj} failed:\n{log}")
         if verbose and log:
             print(log)
-    link = [NVCC, *ARCH, "-shared", "-o", LIB + ".tmp",
-            os.path.join(BUILD, "solver.o"), os.path.join(BUILD, "host.o")]
+    link = [NVCC, *ARCH, "-shared", "-o", LIB + ".tmp"] + [os.path.join(BUILD, o) for o in SOURCES]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"linking failed:\n{r.stdout}{r.stderr}")

@@ -1,0 +1,114 @@
+// Types shared by the host API and the per-precision kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "ofmlmc.h"
+
+namespace ofm {
+namespace gpu {
+
+constexpr int TS = 8;                    // tile edge (cells)
+constexpr int HALO = 3;                  // WENO5 needs three cells on each side
+constexpr int BX = TS + 2 * HALO;        // staged box edge (14)
+constexpr int BOX3 = BX * BX * BX;       // staged box cells (2744, corners unused)
+constexpr int NCELL = TS * TS * TS;      // 512 cells per tile
+constexpr int NSLAB = HALO * TS * TS;    // 192 cells per halo slab
+constexpr int NCROSS = NCELL + 6 * NSLAB;  // 1664 staged cells
+constexpr int NFACE = (TS + 1) * TS * TS;  // 576 faces per direction
+constexpr int NT = 192;                  // threads per block: 3 faces each per direction
+constexpr int CELLS_PER_THREAD = (NCELL + NT - 1) / NT;  // 3
+constexpr int CHUNK_STEPS = 8;           // steps per captured graph (even)
+
+static_assert(NFACE % NT == 0, "each thread computes the same number of faces");
+
+template <typename T>
+struct Eos {
+    T g1, g2, pc1, pc2;   // gamma, p_c (non-dimensional)
+    T gi1, gi2;           // 1/(gamma-1)
+    T pi1, pi2;           // gamma p_c/(gamma-1)
+    T eps;                // WENO epsilon
+};
+
+struct Partial {          // per-tile reduction of one state
+    double smax;          // max over cells of max_d(|u_d| + c)
+    double pmax;          // max pressure
+    long long idx;        // first linear index of pmax
+    int status;           // OR of health bits
+    int pad;
+};
+
+struct DevQoi {           // per-sample record, non-dimensional
+    double p_peak;
+    long long peak_index;
+    double p_peak_t;
+    double sensor_peak[OFM_MAX_SENSORS];
+    double totals0[6];
+    double totals_end[6];
+    double t_final;
+    int n_steps;
+    int status;
+};
+
+struct GroupDev {
+    int N, tpd, tps, n_samples, slot0;
+    long long block0;     // first block of this group in the flattened tile grid
+    void* QA;
+    void* QB;
+    void* dQ;
+    Partial* part;
+    const int* sens_cells;
+    int sens_off[OFM_MAX_SENSORS + 1];
+    double h;
+};
+
+struct SampleDev {
+    double* t;
+    double* dt;
+    int* last;
+    int* done;
+    int* nsteps;
+    int* kout;
+    DevQoi* qoi;
+    double* sens_old;     // [slot][OFM_MAX_SENSORS]
+    double* hist;         // [slot][n_sens][n_out]
+    int* n_active;
+    const double* bubbles;  // [slot][nb][4], non-dimensional
+};
+
+template <typename T>
+struct Params {
+    int n_groups;
+    long long total_blocks;
+    GroupDev g[OFM_MAX_GROUPS];
+    SampleDev s;
+    Eos<T> eos;
+    double rkA[3], rkB[3];
+    int bc, nb, n_sens, n_out, max_steps, total_slots;
+    double t_end, cfl, p_gas, p_liq, rho1, rho2;
+};
+
+// Low-storage TVD RK3 (Gottlieb & Shu 1998), Williamson 2N form.
+constexpr double RK_A[3] = {0.0, -2.915492524638791, -0.000000093517376};
+constexpr double RK_B[3] = {0.924574, 0.287713063186749, 0.626538109512740};
+
+
+constexpr size_t smem_bytes(size_t elem) { return elem * (7 * BOX3 + 8 * NFACE); }
+
+// Launch wrappers, instantiated for double in kernels_fp64.cu (compiled
+// without FMA contraction, in the oracle's operation order) and for float in
+// kernels_fp32.cu.  Each returns OFM_OK or OFM_ECUDA and counts its launches.
+template <typename T>
+int set_smem_attrs();
+template <typename T>
+int launch_step(const Params<T>& P, int parity, cudaStream_t st, long long* launches);
+template <typename T>
+int launch_init(const Params<T>& P, cudaStream_t st, bool fill_ic, long long* launches);
+template <typename T>
+int launch_totals(const Params<T>& P, cudaStream_t st, int which, long long* launches);
+
+}  // namespace gpu
+}  // namespace ofm

@@ -1,10 +1,16 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
 Tolerances: FP64 path, relative L1 per variable <= 1e-12 after one step and
-relative QoI error <= 1e-9 at t_end, on the same seeded clouds.  FP32 stencil
-path: its QoI errors against the oracle are measured and bounded loosely
-(the FP32 pressure loses about two digits to the cancellation
-E - rho|u|^2/2 - Pi with Pi/p ~ 40 in the liquid).
+relative QoI error <= 1e-9 at t_end, on the same seeded clouds.
+
+FP32 stencil path: relative L1 <= 1e-3 after one step.  Derivation: a face
+flux carries HLLC star terms of size |s| ~ c ~ 29 (non-dimensional) times
+O(1) states, so FP32 rounding (6e-8) leaves ~2e-6 absolute noise per face,
+while one step from rest gives momenta of only ~dt |grad p| (the L1 mean of
+|grad p| over the box is ~1e-3 of p), i.e. up to ~1e-3 relative in the
+momenta; masses, energy and alpha2 stay near 1e-7.  QoI errors at t_end are
+measured and bounded loosely (the FP32 pressure loses about two digits to
+the cancellation E - rho|u|^2/2 - Pi with Pi/p ~ 40 in the liquid).
 """
 import os
 from concurrent.futures import ThreadPoolExecutor
@@ -25,6 +31,7 @@ from paper_1705_04374_gb300 import native as nv  # noqa: E402
 THREADS = max(1, min(32, os.cpu_count() or 1))
 TOL_STEP_FP64 = 1e-12
 TOL_QOI_FP64 = 1e-9
+TOL_STEP_FP32 = 1e-3
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -103,7 +110,7 @@ def test_one_step_fp32_close_to_oracle():
     for i in range(2):
         ref = oracle_one_step(sp, N, ocloud.sample_cloud(w.cloud, W.BASE_SEED, i))
         r = rel_l1(b.state(0, i), ref)
-        assert np.all(r <= 1e-4), r
+        assert np.all(r <= TOL_STEP_FP32), r
     b.close()
 
 
@@ -295,7 +302,7 @@ def test_solve_level_host_api_matches_batch():
 
 # ----------------------------------------------------------------- full size, sampled
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp64", TOL_STEP_FP64)])
+@pytest.mark.parametrize("precision,tol", [("fp32", TOL_STEP_FP32), ("fp64", TOL_STEP_FP64)])
 def test_full_size_ensemble_one_step_sampled(precision, tol):
     """512 clouds of 20 bubbles on 64^3 (the throughput workload) in the same
     launch configuration as the benchmark; samples checked one by one."""
