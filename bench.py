@@ -1,0 +1,429 @@
+"""Benchmark: cell-updates/s of the batched cloud-collapse ensemble on GB300.
+
+Workload (one "step" = one full pass of the hot path over the batch): 512
+seeded clouds of 20 bubbles on 64^3 grids, sampled on the host, initial
+condition, CFL-stepped low-storage RK3 (WENO5 + HLLC) to t_end (~120 steps),
+on-device QoI reductions (peak pressure, its location, 8 sensor histories).
+A cell-update is one cell advanced by one full 3-stage RK step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+                    [--impl ours|reference]
+
+value: cell-updates/s over K full solves with the clouds already resident in
+HBM (CUDA events on the launching stream; barrier + synchronize around the
+timed region; max over ranks).  e2e: the same metric through the C ABI call
+ofm_solve_batch with host arrays (cloud upload and QoI download inside the
+timed region).  --impl reference times the FP64 CPU oracle on the host cores
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "cell-updates/s/GPU"
+UNIT = "cell-updates/s"
+N_GRID = 64
+M_SAMPLES = 512
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FLOPS_FILE = os.path.join(ROOT, "paper_1705_04374_gb300", "data", "flops_per_cell_step.json")
+TRAFFIC_FILE = os.path.join(ROOT, "paper_1705_04374_gb300", "data", "ncu_traffic.json")
+KERNEL_SRC = os.path.join(ROOT, "paper_1705_04374_gb300", "csrc", "kernels.cuh")
+
+# FP32 / FP64 non-tensor peaks from unit counts and the maximum SM clock:
+# 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 at the nominal
+# 1.25 TFLOP/s of the part.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--samples", type=int, default=M_SAMPLES)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(precision):
+    w = W.cfg2(precision)
+    return w, w.solver
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+def oracle_cell_steps(sp, cloud, ids, steps_each):
+    """Time the FP64 oracle: each id one 64^3 cloud advanced steps_each steps."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from oracle import cloud as ocloud
+    from oracle import solver as osolver
+
+    def one(sid):
+        bub = ocloud.sample_cloud(cloud, W.BASE_SEED, sid)
+        Q = osolver.init_cloud(sp, N_GRID, bub)
+        g = osolver.grid_from_params(sp, N_GRID)
+        for _ in range(steps_each):
+            Q = osolver.rk3_step(g, Q, sp.cfl * g.h / osolver.max_speed(g, Q))
+        return N_GRID ** 3 * steps_each
+
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        total = sum(ex.map(one, ids))
+    return total, time.perf_counter() - t0, threads
+
+
+def cpu_baseline(sp, cloud):
+    cores = os.cpu_count() or 1
+    ids = list(range(cores))
+    steps_each = 2
+    cells, secs, threads = oracle_cell_steps(sp, cloud, ids, steps_each)
+    return {"value": cells / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(ids)} of the 512 clouds, {steps_each} RK3 steps each from the initial "
+                      f"condition on 64^3 (plain FP64 C oracle, one thread per cloud), "
+                      f"{cells:.3e} cell-updates in {secs:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w, sp = workload("fp64")
+    from oracle import build as obuild
+    obuild.build()
+    cores = os.cpu_count() or 1
+    vals = []
+    for k in range(args.warmup + args.steps):
+        ids = list(range(k * cores, (k + 1) * cores))
+        cells, secs, threads = oracle_cell_steps(sp, w.cloud, ids, 1)
+        if k >= args.warmup:
+            vals.append((cells, secs))
+    cells = sum(c for c, _ in vals)
+    secs = sum(s for _, s in vals)
+    v = cells / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: seeded random clouds", "config": config_dict("fp64", 0),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: {cores} of the 512 clouds (one per host thread), one RK3 "
+                                   "step from the initial condition on 64^3, plain FP64 C oracle"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def config_dict(precision, world):
+    return {"workload": "ensemble: 512 seeded clouds x 20 bubbles, 64^3, to t_end (~120 RK3 steps), "
+                        "QoIs: peak pressure + location, 8 sensor histories",
+            "grid": N_GRID, "samples_per_gpu": M_SAMPLES, "bubbles": 20,
+            "stencil_precision": precision, "reductions": "f64",
+            "graphs": "8-step CUDA-graph chunks",
+            "parallelism": f"replicas x{max(world, 1)} (independent samples per GPU)",
+            "l2": "inputs larger than L2: 3 state buffers of 3.76 GB (fp32) per GPU"}
+
+
+def load_json(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def kernel_hash():
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1705_04374_gb300 import api
+    from paper_1705_04374_gb300 import native as nv
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w, sp = workload(args.precision)
+    M = args.samples
+    ids = list(range(rank * M, (rank + 1) * M))
+    solver = api.Solver(sp, args.precision)
+    group = api.make_group(sp, N_GRID, ids, W.BASE_SEED)
+    batch = api.Batch(solver, w.cloud, [group])
+
+    def solve_resident():
+        batch.init()
+        while batch.run(1 << 20) > 0:
+            pass
+
+    for _ in range(args.warmup):
+        solve_resident()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    launches0 = batch.launches()
+    cells = 0.0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        solve_resident()
+        cells += batch.cell_steps()
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = batch.launches() - launches0
+    batch.qoi(allow_bad=True)
+    statuses = [q.status for q in group.qoi]
+    t = torch.tensor([ms, cells], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        t[0] = tmax[0]
+    ms_all, cells_all = float(t[0]), float(t[1])
+    value = cells_all / (ms_all / 1e3)
+
+    # kernel timing: one more solve with CUDA events around every stage kernel
+    batch.set_profiling(True)
+    solve_resident()
+    stage_ms, stage_n = batch.stage_time()
+    batch.set_profiling(False)
+    avg_stage_ms = stage_ms / max(stage_n, 1)
+    batch.close()
+    del batch
+    torch.cuda.empty_cache()
+
+    # end to end through the C ABI with host arrays (clouds from pinned memory)
+    cp = w.cloud
+    bub_host = torch.empty((M * cp.n_bubbles * 4,), dtype=torch.float64).pin_memory()
+    bub_np = bub_host.numpy().reshape(M * cp.n_bubbles, 4)
+    for i, sid in enumerate(ids):
+        bub_np[i * cp.n_bubbles:(i + 1) * cp.n_bubbles] = api.sample_cloud(cp, W.BASE_SEED, sid)
+    e2e_group = api.Group(N_GRID, ids, W.BASE_SEED, len(sp.sensors), sp.n_out_times)
+    e2e_group.c.bubbles = C.cast(C.c_void_p(bub_host.data_ptr()), C.POINTER(nv.ofm_bubble))
+    garr = (nv.ofm_group * 1)(e2e_group.c)
+    cpar = api.cloud_params(cp)
+    nbytes = C.c_size_t()
+    nv.check(nv.lib().ofm_batch_workspace_bytes(solver.h, C.byref(cpar), garr, 1, C.byref(nbytes)), "ws")
+    ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device="cuda")
+    ws_ptr = (ws.data_ptr() + 255) // 256 * 256
+    sptr = C.c_void_p(stream.cuda_stream)
+
+    def solve_e2e():
+        rc = nv.lib().ofm_solve_batch(solver.h, C.byref(cpar), garr, 1, C.c_void_p(ws_ptr), nbytes.value, sptr)
+        if rc not in (nv.OFM_OK, nv.OFM_ENUMERIC):
+            nv.check(rc, "ofm_solve_batch")
+        return sum(q.n_steps for q in e2e_group.qoi) * float(N_GRID ** 3)
+
+    # bytes one e2e step moves, from the library's own accounting of an identical solve
+    probe = api.Batch(solver, cp, [e2e_group])
+    probe.init()
+    while probe.run(1 << 20) > 0:
+        pass
+    probe.qoi(allow_bad=True)
+    h2d, d2h = probe.transfer_bytes()
+    probe.close()
+    del probe
+    torch.cuda.empty_cache()
+
+    solve_e2e()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_cells = 0.0
+    for _ in range(args.steps):
+        e2e_cells += solve_e2e()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s, e2e_cells], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tm = te.clone()
+        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(te[1:2], op=dist.ReduceOp.SUM)
+        te[0] = tm[0]
+    e2e_value = float(te[1]) / float(te[0])
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (the RK-stage kernel)
+    flops = load_json(FLOPS_FILE) or {}
+    f_stage = flops.get("flops_per_cell_stage")
+    cells_per_launch = M * N_GRID ** 3
+    peaks = load_json(PEAKS_FILE)
+    hbm_peak = None
+    hbm_src = "fallback"
+    if peaks:
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in peaks:
+                hbm_peak = float(peaks[k]) if not isinstance(peaks[k], dict) else float(peaks[k].get("value"))
+                hbm_src = "measured"
+                break
+    if hbm_peak is None:
+        hbm_peak = HBM_FALLBACK_GBS
+    es = 4 if args.precision == "fp32" else 8
+    bytes_per_cell_stage = (21 + 28 + 28) / 3.0 * es   # Q, dQ in; Q', dQ out (stage 1 skips dQ in)
+    traffic_rec = load_json(TRAFFIC_FILE) or {}
+    traffic = None
+    if traffic_rec.get("kernel_hash") == kernel_hash() and traffic_rec.get("precision") == args.precision:
+        traffic = traffic_rec.get("dram_bytes_per_cell_stage") * cells_per_launch
+    alu_peak = FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS
+    achieved_tflops = f_stage * cells_per_launch / (avg_stage_ms / 1e3) / 1e12 if f_stage else None
+    achieved_gbs = bytes_per_cell_stage * cells_per_launch / (avg_stage_ms / 1e3) / 1e9
+    alu_ceiling = alu_peak * 1e12 / f_stage if f_stage else float("inf")   # cell-stages/s
+    hbm_ceiling = hbm_peak * 1e9 / bytes_per_cell_stage
+    if alu_ceiling <= hbm_ceiling and achieved_tflops is not None:
+        roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved_tflops / alu_peak, "traffic": traffic,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if args.precision == "fp32"
+                    else "nominal FP64 of the part",
+                    "kernel": "stage_kernel (fused WENO5 + HLLC + 2N update)",
+                    "per_launch": {"cells": cells_per_launch, "flops_per_cell": f_stage,
+                                   "avg_ms": avg_stage_ms, "launches_timed": stage_n}}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm_peak, "traffic": traffic,
+                    "kernel": "stage_kernel", "avg_ms": avg_stage_ms}
+    roofline_hbm = {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src,
+                    "algorithmic_bytes_per_cell_stage": bytes_per_cell_stage}
+
+    cpu = None
+    try:
+        from oracle import build as obuild
+        obuild.build()
+        cpu = cpu_baseline(W.cfg2("fp64").solver, w.cloud)
+    except Exception as exc:  # reported, never silently replaced
+        cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"failed: {exc}"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_all / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic: seeded random clouds (no dataset exists for this workload)",
+        "config": config_dict(args.precision, world),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "api": "ofm_solve_batch (host clouds in pinned memory, "
+                                                 "QoIs and sensor histories back to the host)"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline": roofline,
+        "roofline_hbm": roofline_hbm,
+        "cpu_baseline": cpu,
+        "samples_failed": int(sum(1 for s in statuses if s)),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -185,6 +185,14 @@ int ofm_batch_cell_steps(ofm_batch* batch, double* cell_steps);
 /* Number of kernels this batch has launched so far (graph replays count
  * every kernel node). */
 int ofm_batch_kernel_launches(ofm_batch* batch, int64_t* launches);
+/* Profiling mode (on != 0): later ofm_batch_run steps are launched without
+ * graphs, with CUDA events on the batch's stream around each RK-stage kernel;
+ * ofm_batch_stage_time returns the accumulated stage-kernel time [ms] and the
+ * number of stage launches it covers.  Results are identical in both modes. */
+int ofm_batch_set_profiling(ofm_batch* batch, int on);
+int ofm_batch_stage_time(ofm_batch* batch, double* total_ms, int64_t* n_launches);
+/* Bytes this batch has copied host->device and device->host so far. */
+int ofm_batch_transfer_bytes(ofm_batch* batch, int64_t* h2d, int64_t* d2h);
 void ofm_batch_destroy(ofm_batch* batch);
 
 /* One call for the whole path: create, init, run to t_end, copy QoIs, destroy. */

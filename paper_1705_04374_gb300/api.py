@@ -176,6 +176,21 @@ class Batch:
         nv.check(nv.lib().ofm_batch_kernel_launches(self.h, C.byref(v)), "ofm_batch_kernel_launches")
         return v.value
 
+    def set_profiling(self, on: bool):
+        nv.check(nv.lib().ofm_batch_set_profiling(self.h, int(on)), "ofm_batch_set_profiling")
+
+    def stage_time(self):
+        ms = C.c_double()
+        n = C.c_int64()
+        nv.check(nv.lib().ofm_batch_stage_time(self.h, C.byref(ms), C.byref(n)), "ofm_batch_stage_time")
+        return ms.value, n.value
+
+    def transfer_bytes(self):
+        a = C.c_int64()
+        d = C.c_int64()
+        nv.check(nv.lib().ofm_batch_transfer_bytes(self.h, C.byref(a), C.byref(d)), "ofm_batch_transfer_bytes")
+        return a.value, d.value
+
     def close(self):
         if getattr(self, "h", None):
             nv.lib().ofm_batch_destroy(self.h)

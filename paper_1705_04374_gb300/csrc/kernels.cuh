@@ -786,6 +786,23 @@ int launch_step(const Params<T>& P, int parity, cudaStream_t st, long long* laun
 }
 
 template <typename T>
+int launch_stage(const Params<T>& P, int stage, int parity, cudaStream_t st, long long* launches) {
+    const size_t sm = smem_bytes(sizeof(T));
+    const dim3 grid((unsigned)P.total_blocks);
+    if (stage == 0)
+        stage_kernel<T, 0><<<grid, NT, sm, st>>>(P, parity);
+    else if (stage == 1)
+        stage_kernel<T, 1><<<grid, NT, sm, st>>>(P, parity);
+    else if (stage == 2)
+        stage_kernel<T, 2><<<grid, NT, sm, st>>>(P, parity);
+    else
+        finalize_kernel<T><<<P.total_slots, 256, 0, st>>>(P, 0, parity);
+    *launches += 1;
+    CUDA_TRY(cudaGetLastError());
+    return OFM_OK;
+}
+
+template <typename T>
 int launch_init(const Params<T>& P, cudaStream_t st, bool fill_ic, long long* launches) {
     reset_kernel<T><<<(P.total_slots + 127) / 128, 128, 0, st>>>(P);
     *launches += 1;

@@ -96,6 +96,11 @@ struct ofm_batch {
     cudaGraphExec_t chunk;
     bool chunk_ready;
     bool initialised;
+    bool profiling;           // steps without graphs, CUDA events around each stage kernel
+    cudaEvent_t pev[4];
+    double stage_ms;
+    long long stage_launches;
+    long long h2d_bytes, d2h_bytes;
     Params<double> pd;
     Params<float> pf;
     size_t off_t, off_dt, off_last, off_done, off_nsteps, off_kout, off_qoi, off_sold, off_hist,
@@ -346,6 +351,12 @@ extern "C" int ofm_batch_create(ofm_batch** out, ofm_solver* s, const ofm_cloud_
     b->launches = 0;
     b->chunk_ready = false;
     b->initialised = false;
+    b->profiling = false;
+    for (int k = 0; k < 4; ++k) b->pev[k] = nullptr;
+    b->stage_ms = 0.0;
+    b->stage_launches = 0;
+    b->h2d_bytes = 0;
+    b->d2h_bytes = 0;
     Layout Lo;
     layout(s, cloud, groups, n_groups, b, Lo);
     int slots = 0;
@@ -408,12 +419,16 @@ extern "C" int ofm_batch_create(ofm_batch** out, ofm_solver* s, const ofm_cloud_
             }
         }
     }
+    for (int k = 0; k < 4; ++k)
+        if (cudaEventCreate(&b->pev[k]) != cudaSuccess) return bail(fail(OFM_ECUDA, "event creation failed"));
     if (enter(b) != OFM_OK) return bail(OFM_ECUDA);
+    b->h2d_bytes += (long long)bub.size() * 8;
     if (!bub.empty() &&
         cudaMemcpyAsync(b->ws + b->off_bub, bub.data(), bub.size() * 8, cudaMemcpyHostToDevice, b->priv) != cudaSuccess)
         return bail(fail(OFM_ECUDA, "bubble upload failed"));
     for (int g = 0; g < n_groups; ++g) {
         const std::vector<int>& sc = b->gh[g].sens_cells;
+        b->h2d_bytes += (long long)sc.size() * (long long)sizeof(int);
         if (!sc.empty() &&
             cudaMemcpyAsync(b->ws + b->gh[g].off_sens, sc.data(), sc.size() * sizeof(int), cudaMemcpyHostToDevice,
                             b->priv) != cudaSuccess)
@@ -446,7 +461,28 @@ extern "C" int ofm_batch_run(ofm_batch* b, int max_steps, int* n_active) {
     int done_steps = 0;
     int active = 1;
     while (done_steps < max_steps) {
-        if ((b->global_steps & 1) == 0 && max_steps - done_steps >= CHUNK_STEPS) {
+        if (b->profiling) {
+            const int parity = (int)(b->global_steps & 1);
+            for (int k = 0; k < 4; ++k) {
+                CUDA_TRY(cudaEventRecord(b->pev[k], b->priv));
+                if (k == 3) break;
+                rc = b->precision == OFM_FP64 ? launch_stage(b->pd, k, k == 1 ? 1 - parity : parity, b->priv, &b->launches)
+                                              : launch_stage(b->pf, k, k == 1 ? 1 - parity : parity, b->priv, &b->launches);
+                if (rc != OFM_OK) return rc;
+            }
+            rc = b->precision == OFM_FP64 ? launch_stage(b->pd, 3, 1 - parity, b->priv, &b->launches)
+                                          : launch_stage(b->pf, 3, 1 - parity, b->priv, &b->launches);
+            if (rc != OFM_OK) return rc;
+            CUDA_TRY(cudaEventSynchronize(b->pev[3]));
+            for (int k = 0; k < 3; ++k) {
+                float ms = 0.f;
+                CUDA_TRY(cudaEventElapsedTime(&ms, b->pev[k], b->pev[k + 1]));
+                b->stage_ms += ms;
+            }
+            b->stage_launches += 3;
+            b->global_steps += 1;
+            done_steps += 1;
+        } else if ((b->global_steps & 1) == 0 && max_steps - done_steps >= CHUNK_STEPS) {
             if (!b->chunk_ready) {
                 rc = b->precision == OFM_FP64 ? build_chunk(b, b->pd) : build_chunk(b, b->pf);
                 if (rc != OFM_OK) return rc;
@@ -465,6 +501,7 @@ extern "C" int ofm_batch_run(ofm_batch* b, int max_steps, int* n_active) {
         }
         const size_t off = b->off_active;
         CUDA_TRY(cudaMemcpyAsync(b->h_active, b->ws + off, sizeof(int), cudaMemcpyDeviceToHost, b->priv));
+        b->d2h_bytes += (long long)sizeof(int);
         CUDA_TRY(cudaStreamSynchronize(b->priv));
         active = *b->h_active;
         if (active == 0) break;
@@ -493,6 +530,8 @@ extern "C" int ofm_batch_qoi(ofm_batch* b) {
     CUDA_TRY(cudaMemcpyAsync(tt.data(), b->ws + b->off_t, tt.size() * 8, cudaMemcpyDeviceToHost, b->priv));
     if (hist_n)
         CUDA_TRY(cudaMemcpyAsync(hist.data(), b->ws + b->off_hist, hist_n * 8, cudaMemcpyDeviceToHost, b->priv));
+    b->d2h_bytes += (long long)(q.size() * sizeof(DevQoi) + nsteps.size() * 4 + done.size() * 4 + tt.size() * 8 +
+                                hist_n * 8);
     CUDA_TRY(cudaStreamSynchronize(b->priv));
     const ofm_solver* s = b->solver;
     int any_bad = 0;
@@ -582,6 +621,7 @@ extern "C" int ofm_batch_set_state(ofm_batch* b, int group, int sample, const vo
     rc = enter(b);
     if (rc != OFM_OK) return rc;
     CUDA_TRY(cudaMemcpyAsync(b->ws + b->gh[group].off_QA + off, host_buf, n, cudaMemcpyHostToDevice, b->priv));
+    b->h2d_bytes += (long long)n;
     rc = b->precision == OFM_FP64 ? launch_init(b->pd, b->priv, false, &b->launches) : launch_init(b->pf, b->priv, false, &b->launches);
     if (rc != OFM_OK) return rc;
     CUDA_TRY(cudaStreamSynchronize(b->priv));
@@ -610,9 +650,34 @@ extern "C" int ofm_batch_kernel_launches(ofm_batch* b, int64_t* launches) {
     return OFM_OK;
 }
 
+extern "C" int ofm_batch_set_profiling(ofm_batch* b, int on) {
+    ofm::clear_error();
+    if (!b) return fail(OFM_EINVAL, "NULL batch");
+    b->profiling = on != 0;
+    return OFM_OK;
+}
+
+extern "C" int ofm_batch_stage_time(ofm_batch* b, double* total_ms, int64_t* n_launches) {
+    ofm::clear_error();
+    if (!b || !total_ms || !n_launches) return fail(OFM_EINVAL, "NULL argument");
+    *total_ms = b->stage_ms;
+    *n_launches = b->stage_launches;
+    return OFM_OK;
+}
+
+extern "C" int ofm_batch_transfer_bytes(ofm_batch* b, int64_t* h2d, int64_t* d2h) {
+    ofm::clear_error();
+    if (!b || !h2d || !d2h) return fail(OFM_EINVAL, "NULL argument");
+    *h2d = b->h2d_bytes;
+    *d2h = b->d2h_bytes;
+    return OFM_OK;
+}
+
 extern "C" void ofm_batch_destroy(ofm_batch* b) {
     if (!b) return;
     if (b->priv) cudaStreamSynchronize(b->priv);
+    for (int k = 0; k < 4; ++k)
+        if (b->pev[k]) cudaEventDestroy(b->pev[k]);
     if (b->chunk_ready) cudaGraphExecDestroy(b->chunk);
     if (b->own_ws && b->ws) cudaFree(b->ws);
     if (b->h_active) cudaFreeHost(b->h_active);

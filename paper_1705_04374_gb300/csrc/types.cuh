@@ -107,6 +107,9 @@ template <typename T>
 int launch_step(const Params<T>& P, int parity, cudaStream_t st, long long* launches);
 template <typename T>
 int launch_init(const Params<T>& P, cudaStream_t st, bool fill_ic, long long* launches);
+// stage 0..2: one RK stage kernel; stage 3: the step's finalize kernel.
+template <typename T>
+int launch_stage(const Params<T>& P, int stage, int parity, cudaStream_t st, long long* launches);
 template <typename T>
 int launch_totals(const Params<T>& P, cudaStream_t st, int which, long long* launches);
 

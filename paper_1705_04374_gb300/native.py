@@ -82,6 +82,9 @@ SIGNATURES = {
     "ofm_batch_set_state": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.c_size_t]),
     "ofm_batch_cell_steps": (C.c_int, [_vp, _P(C.c_double)]),
     "ofm_batch_kernel_launches": (C.c_int, [_vp, _P(C.c_int64)]),
+    "ofm_batch_set_profiling": (C.c_int, [_vp, C.c_int]),
+    "ofm_batch_stage_time": (C.c_int, [_vp, _P(C.c_double), _P(C.c_int64)]),
+    "ofm_batch_transfer_bytes": (C.c_int, [_vp, _P(C.c_int64), _P(C.c_int64)]),
     "ofm_batch_destroy": (None, [_vp]),
     "ofm_solve_batch": (C.c_int, [_vp, _P(ofm_cloud_params), _P(ofm_group), C.c_int, _vp, C.c_size_t,
                                   _vp]),
