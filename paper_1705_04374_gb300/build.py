@@ -25,7 +25,8 @@ _NV = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I
 SOURCES = {
     # FP64 kernels round exactly like the FP64 reference: no FMA contraction
     "kernels_fp64.o": _NV + ["-fmad=false", "-c", os.path.join(CSRC, "kernels_fp64.cu")],
-    "kernels_fp32.o": _NV + ["-c", os.path.join(CSRC, "kernels_fp32.cu")],
+    # FP32 stencil: approximate division / square root (2 ulp), flush-to-zero
+    "kernels_fp32.o": _NV + ["-use_fast_math", "-c", os.path.join(CSRC, "kernels_fp32.cu")],
     "solver.o": _NV + ["-c", os.path.join(CSRC, "solver.cu")],
     "host.o": ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I", INCLUDE,
                "-c", os.path.join(CSRC, "host.cpp")],

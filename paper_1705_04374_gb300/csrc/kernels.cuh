@@ -202,8 +202,21 @@ __device__ __forceinline__ void hllc(const Eos<T>& e, const T* wl, const T* wr, 
 // --------------------------------------------------------------------------
 // Tile geometry helpers
 // --------------------------------------------------------------------------
-__device__ __forceinline__ int box_index(int bx, int by, int bz) {
-    return ((bz + HALO) * BX + (by + HALO)) * BX + (bx + HALO);
+// Compact staging layout of the tile and its halo (no corners): rows along x.
+// Rows whose (y, z) both lie in the tile hold x = -3..10 (14 cells); rows in a
+// y- or z-halo slab hold x = 0..7.  row_off(y, z) + x is the staged index.
+constexpr int ROWS_INT = TS * TS * BX;           // 896 cells in full-width rows
+constexpr int ROWS_Y = ROWS_INT + 2 * HALO * TS * TS;  // start of z-halo rows (1280)
+
+__device__ __forceinline__ int row_off(int y, int z) {
+    const bool yi = (unsigned)y < (unsigned)TS, zi = (unsigned)z < (unsigned)TS;
+    if (yi && zi) return (z * TS + y) * BX + HALO;
+    if (zi) {
+        const int hy = y < 0 ? y + HALO : y - TS + HALO;  // 0..5
+        return ROWS_INT + (hy * TS + z) * TS;
+    }
+    const int hz = z < 0 ? z + HALO : z - TS + HALO;      // 0..5
+    return ROWS_Y + (hz * TS + y) * TS;
 }
 
 // Staged cell i in [0, NCROSS): the tile, then six 3-deep halo slabs
@@ -432,12 +445,164 @@ __global__ void __launch_bounds__(NT) reduce_kernel(const __grid_constant__ Para
     block_reduce_write(r, G.part + (size_t)bw.s_local * G.tps + tile);
 }
 
+// Both WENO5 face states of the face between the cells holding c0 and p1,
+// from the six averages m2..p3, in single precision.  The smoothness
+// indicators and candidate values are written with the first differences
+// d = v_{j+1} - v_j and second differences D_j = v_{j-1} - 2 v_j + v_{j+1},
+// shared between the two sides:
+//   beta: 13/12 D^2 + 1/4 (D +- 2d)^2 or 13/12 D^2 + 1/4 (d + d')^2,
+//   candidates: v + D/3 + d/2, v - D/6 + d/2, ...
+// which is the same polynomial algebra as the textbook form.
+__device__ __forceinline__ void weno5_pair(float m2, float m1, float c0, float p1, float p2, float p3,
+                                           float eps, float& wl, float& wr) {
+    const float d0 = m1 - m2, d1 = c0 - m1, d2 = p1 - c0, d3 = p2 - p1, d4 = p3 - p2;
+    const float Dm = d1 - d0, D0 = d2 - d1, D1 = d3 - d2, D2 = d4 - d3;
+    const float k = 13.0f / 12.0f;
+    const float sm = k * Dm * Dm, s0 = k * D0 * D0, s1 = k * D1 * D1, s2 = k * D2 * D2;
+    const float hd2 = 0.5f * d2;
+    // left state (cell c0), face to its right
+    {
+        const float t0 = Dm + 2.0f * d1, t1 = d1 + d2, t2 = D1 - 2.0f * d2;
+        float e0 = eps + fmaf(0.25f * t0, t0, sm);
+        float e1 = eps + fmaf(0.25f * t1, t1, s0);
+        float e2 = eps + fmaf(0.25f * t2, t2, s1);
+        e0 *= e0;
+        e1 *= e1;
+        e2 *= e2;
+        const float a0 = 0.1f * (e1 * e2), a1 = 0.6f * (e0 * e2), a2 = 0.3f * (e0 * e1);
+        const float q0 = c0 + fmaf(Dm, 1.0f / 3.0f, 0.5f * d1);
+        const float q1 = c0 + fmaf(D0, -1.0f / 6.0f, hd2);
+        const float q2 = c0 + fmaf(D1, -1.0f / 6.0f, hd2);
+        wl = fmaf(a0, q0, fmaf(a1, q1, a2 * q2)) / (a0 + a1 + a2);
+    }
+    // right state (cell p1, mirrored stencil), face to its left
+    {
+        const float t0 = D2 - 2.0f * d3, t1 = d2 + d3, t2 = D0 + 2.0f * d2;
+        float e0 = eps + fmaf(0.25f * t0, t0, s2);
+        float e1 = eps + fmaf(0.25f * t1, t1, s1);
+        float e2 = eps + fmaf(0.25f * t2, t2, s0);
+        e0 *= e0;
+        e1 *= e1;
+        e2 *= e2;
+        const float a0 = 0.1f * (e1 * e2), a1 = 0.6f * (e0 * e2), a2 = 0.3f * (e0 * e1);
+        const float q0 = p1 + fmaf(D2, 1.0f / 3.0f, -0.5f * d3);
+        const float q1 = p1 - fmaf(D1, 1.0f / 6.0f, hd2);
+        const float q2 = p1 - fmaf(D0, 1.0f / 6.0f, hd2);
+        wr = fmaf(a0, q0, fmaf(a1, q1, a2 * q2)) / (a0 + a1 + a2);
+    }
+}
+
+// HLLC in the face frame (un normal, ut1/ut2 tangential), single precision.
+// Output: F[0..1] masses, F[2] normal momentum, F[3..4] tangential momenta,
+// F[5] energy, F[6] alpha2 flux, F[7] face velocity.
+__device__ __forceinline__ void hllc_frame(const Eos<float>& e, const float* wl, const float* wr, float* F) {
+    const float rL = wl[0] + wl[1], rR = wr[0] + wr[1];
+    const float uL = wl[2], uR = wr[2];
+    const float pL = wl[5], pR = wr[5];
+    float GL, PiL, GR, PiR;
+    closure(e, wl[6], GL, PiL);
+    closure(e, wr[6], GR, PiR);
+    const float EL = GL * pL + PiL + 0.5f * rL * (wl[2] * wl[2] + wl[3] * wl[3] + wl[4] * wl[4]);
+    const float ER = GR * pR + PiR + 0.5f * rR * (wr[2] * wr[2] + wr[3] * wr[3] + wr[4] * wr[4]);
+    const float cL = sqrtf(((GL + 1.0f) * pL + PiL) / (GL * rL));
+    const float cR = sqrtf(((GR + 1.0f) * pR + PiR) / (GR * rR));
+    const float sL = fminf(uL - cL, uR - cR);
+    const float sR = fmaxf(uL + cL, uR + cR);
+    const float mL = rL * (sL - uL), mR = rR * (sR - uR);
+    const float ss = (pR - pL + uL * mL - uR * mR) / (mL - mR);
+    float ufL = uL, ufR = uR;
+    if (sL < 0.0f) ufL = uL + sL * ((sL - uL) / (sL - ss) - 1.0f);
+    if (sR > 0.0f) ufR = uR + sR * ((sR - uR) / (sR - ss) - 1.0f);
+    const bool left = ss >= 0.0f;
+    const float* w = left ? wl : wr;
+    const float r = left ? rL : rR, un = left ? uL : uR, p = left ? pL : pR, E = left ? EL : ER;
+    const float sK = left ? sL : sR;
+    const bool star = left ? (sL < 0.0f) : (sR > 0.0f);
+    const float m1 = w[0], m2 = w[1], t1 = w[3], t2 = w[4];
+    const float qn = r * un, q1 = r * t1, q2 = r * t2;
+    float f0 = m1 * un, f1 = m2 * un, fn = qn * un + p, f1t = q1 * un, f2t = q2 * un, f5 = (E + p) * un;
+    if (star) {
+        const float chi = (sK - un) / (sK - ss);
+        const float cm1 = chi - 1.0f;
+        const float cr = chi * r;
+        f0 += sK * (cm1 * m1);
+        f1 += sK * (cm1 * m2);
+        fn += sK * (cr * ss - qn);
+        f1t += sK * (cm1 * q1);
+        f2t += sK * (cm1 * q2);
+        f5 += sK * (chi * (E + (ss - un) * (r * ss + p / (sK - un))) - E);
+    }
+    const float uf = ss > 0.0f ? ufL : (ss < 0.0f ? ufR : 0.5f * (ufL + ufR));
+    F[0] = f0;
+    F[1] = f1;
+    F[2] = fn;
+    F[3] = f1t;
+    F[4] = f2t;
+    F[5] = f5;
+    F[6] = (left ? wl[6] : wr[6]) * uf;
+    F[7] = uf;
+}
+
+// One face in single precision: stencil of six staged cells (staged indices
+// i6), direction dir.  Returns F in the face frame (see hllc_frame).
+__device__ __forceinline__ void face_fp32(const Eos<float>& e, const float* __restrict__ sW, const int* i6,
+                                          int dir, float* F) {
+    float wl[7], wr[7];
+#pragma unroll
+    for (int v = 0; v < 7; ++v) {
+        const float* P = sW + v * NCROSS;
+        weno5_pair(P[i6[0]], P[i6[1]], P[i6[2]], P[i6[3]], P[i6[4]], P[i6[5]], e.eps, wl[v], wr[v]);
+    }
+    if (!admissible(e, wl)) {
+#pragma unroll
+        for (int v = 0; v < 7; ++v) wl[v] = sW[v * NCROSS + i6[2]];
+    }
+    if (!admissible(e, wr)) {
+#pragma unroll
+        for (int v = 0; v < 7; ++v) wr[v] = sW[v * NCROSS + i6[3]];
+    }
+    // rotate velocities into the face frame: slot 2 normal, 3 and 4 tangential
+    const float lx = wl[2], ly = wl[3], lz = wl[4], rx = wr[2], ry = wr[3], rz = wr[4];
+    wl[2] = dir == 0 ? lx : (dir == 1 ? ly : lz);
+    wl[3] = dir == 0 ? ly : (dir == 1 ? lz : lx);
+    wl[4] = dir == 0 ? lz : (dir == 1 ? lx : ly);
+    wr[2] = dir == 0 ? rx : (dir == 1 ? ry : rz);
+    wr[3] = dir == 0 ? ry : (dir == 1 ? rz : rx);
+    wr[4] = dir == 0 ? rz : (dir == 1 ? rx : ry);
+    hllc_frame(e, wl, wr, F);
+}
+
+// One face in double precision, in the FP64 reference's operation order.
+template <int DIR>
+__device__ __forceinline__ void face_fp64(const Eos<double>& e, const double* __restrict__ sW, const int* i6,
+                                          double* F) {
+    double wl[7], wr[7];
+#pragma unroll
+    for (int v = 0; v < 7; ++v) {
+        const double* P = sW + v * NCROSS;
+        const double m2 = P[i6[0]], m1 = P[i6[1]], c0 = P[i6[2]], p1 = P[i6[3]], p2 = P[i6[4]], p3 = P[i6[5]];
+        wl[v] = weno5(m2, m1, c0, p1, p2, e.eps);
+        wr[v] = weno5(p3, p2, p1, c0, m1, e.eps);
+    }
+    if (!admissible(e, wl)) {
+#pragma unroll
+        for (int v = 0; v < 7; ++v) wl[v] = sW[v * NCROSS + i6[2]];
+    }
+    if (!admissible(e, wr)) {
+#pragma unroll
+        for (int v = 0; v < 7; ++v) wr[v] = sW[v * NCROSS + i6[3]];
+    }
+    hllc<double, DIR>(e, wl, wr, F);
+}
+
 // One RK stage.  parity 0: read Q_a, write Q_b; parity 1: the reverse.
 template <typename T, int STAGE>
-__global__ void __launch_bounds__(NT) stage_kernel(const __grid_constant__ Params<T> P, int parity) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
+    stage_kernel(const __grid_constant__ Params<T> P, int parity) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sW = reinterpret_cast<T*>(smem_raw);  // [7][BOX3] primitives
-    T* sF = sW + 7 * BOX3;                   // [8][NFACE] face fluxes + face velocity
+    T* sW = reinterpret_cast<T*>(smem_raw);  // [7][NCROSS] primitives, compact layout
+    T* sF = sW + 7 * NCROSS;                 // [8][NFACE] face fluxes + face velocity
+    int* sRow = reinterpret_cast<int*>(sF + 8 * NFACE);  // [BX][BX] row offsets
 
     BlockWork<T> bw;
     decode_block(P, blockIdx.x, bw);
@@ -454,6 +619,11 @@ __global__ void __launch_bounds__(NT) stage_kernel(const __grid_constant__ Param
     const Eos<T> e = P.eos;
     const int bc = P.bc;
 
+    for (int i = threadIdx.x; i < BX * BX; i += NT) {
+        const int y = i % BX - HALO, z = i / BX - HALO;
+        const bool yi = (unsigned)y < (unsigned)TS, zi = (unsigned)z < (unsigned)TS;
+        sRow[i] = (yi || zi) ? row_off(y, z) : -1;
+    }
     // 1. stage the tile and its halo as primitives
     for (int i = threadIdx.x; i < NCROSS; i += NT) {
         int bx, by, bz;
@@ -466,9 +636,9 @@ __global__ void __launch_bounds__(NT) stage_kernel(const __grid_constant__ Param
 #pragma unroll
         for (int v = 0; v < 7; ++v) q[v] = Qin[v * n3 + gi];
         cons2prim(e, q, w);
-        const int bi = box_index(bx, by, bz);
+        const int si = row_off(by, bz) + bx;
 #pragma unroll
-        for (int v = 0; v < 7; ++v) sW[v * BOX3 + bi] = w[v];
+        for (int v = 0; v < 7; ++v) sW[v * NCROSS + si] = w[v];
     }
     __syncthreads();
 
@@ -482,53 +652,47 @@ __global__ void __launch_bounds__(NT) stage_kernel(const __grid_constant__ Param
     }
 
     // 2. faces, direction by direction
-#pragma unroll
+#pragma unroll 1
     for (int dir = 0; dir < 3; ++dir) {
-        const int S = dir == 0 ? 1 : (dir == 1 ? BX : BX * BX);
         for (int f = threadIdx.x; f < NFACE; f += NT) {
-            int lx, ly, lz;  // left cell of face f
+            int i6[6];
             if (dir == 0) {
                 const int fx = f % 9, q = f / 9;
-                lx = fx - 1;
-                ly = q & 7;
-                lz = q >> 3;
+                const int base = sRow[((q >> 3) + HALO) * BX + (q & 7) + HALO] + fx - 1;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) i6[k] = base + k - 2;
             } else if (dir == 1) {
-                lx = f & 7;
-                const int q = f >> 3;
-                ly = q % 9 - 1;
-                lz = q / 9;
+                const int x = f & 7, q = f >> 3, ly = q % 9 - 1, z = q / 9;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) i6[k] = sRow[(z + HALO) * BX + ly + k - 2 + HALO] + x;
             } else {
-                lx = f & 7;
-                ly = (f >> 3) & 7;
-                lz = (f >> 6) - 1;
-            }
-            const int base = box_index(lx, ly, lz);
-            T wl[7], wr[7];
+                const int x = f & 7, y = (f >> 3) & 7, lz = (f >> 6) - 1;
 #pragma unroll
-            for (int v = 0; v < 7; ++v) {
-                const T* Pv = sW + v * BOX3 + base;
-                const T m2 = Pv[-2 * S], m1 = Pv[-S], c0 = Pv[0];
-                const T p1 = Pv[S], p2 = Pv[2 * S], p3 = Pv[3 * S];
-                wl[v] = weno5(m2, m1, c0, p1, p2, e.eps);
-                wr[v] = weno5(p3, p2, p1, c0, m1, e.eps);
-            }
-            if (!admissible(e, wl)) {
-#pragma unroll
-                for (int v = 0; v < 7; ++v) wl[v] = sW[v * BOX3 + base];
-            }
-            if (!admissible(e, wr)) {
-#pragma unroll
-                for (int v = 0; v < 7; ++v) wr[v] = sW[v * BOX3 + base + S];
+                for (int k = 0; k < 6; ++k) i6[k] = sRow[(lz + k - 2 + HALO) * BX + y + HALO] + x;
             }
             T F[8];
-            if (dir == 0)
-                hllc<T, 0>(e, wl, wr, F);
-            else if (dir == 1)
-                hllc<T, 1>(e, wl, wr, F);
-            else
-                hllc<T, 2>(e, wl, wr, F);
+            if constexpr (std::is_same<T, double>::value) {
+                if (dir == 0)
+                    face_fp64<0>(e, sW, i6, F);
+                else if (dir == 1)
+                    face_fp64<1>(e, sW, i6, F);
+                else
+                    face_fp64<2>(e, sW, i6, F);
 #pragma unroll
-            for (int v = 0; v < 8; ++v) sF[v * NFACE + f] = F[v];
+                for (int v = 0; v < 8; ++v) sF[v * NFACE + f] = F[v];
+            } else {
+                face_fp32(e, sW, i6, dir, F);
+                const int r1 = dir == 0 ? 3 : (dir == 1 ? 4 : 2);   // first tangential row
+                const int r2 = dir == 0 ? 4 : (dir == 1 ? 2 : 3);   // second tangential row
+                sF[0 * NFACE + f] = F[0];
+                sF[1 * NFACE + f] = F[1];
+                sF[(2 + dir) * NFACE + f] = F[2];
+                sF[r1 * NFACE + f] = F[3];
+                sF[r2 * NFACE + f] = F[4];
+                sF[5 * NFACE + f] = F[5];
+                sF[6 * NFACE + f] = F[6];
+                sF[7 * NFACE + f] = F[7];
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -536,17 +700,8 @@ __global__ void __launch_bounds__(NT) stage_kernel(const __grid_constant__ Param
             const int c = threadIdx.x + k * NT;
             if (c < NCELL) {
                 const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-                int fl, step;
-                if (dir == 0) {
-                    fl = x + 9 * (y + 8 * z);
-                    step = 1;
-                } else if (dir == 1) {
-                    fl = x + 8 * (y + 9 * z);
-                    step = 8;
-                } else {
-                    fl = x + 8 * (y + 8 * z);
-                    step = 64;
-                }
+                const int fl = dir == 0 ? x + 9 * (y + 8 * z) : (dir == 1 ? x + 8 * (y + 9 * z) : c);
+                const int step = dir == 0 ? 1 : (dir == 1 ? 8 : 64);
 #pragma unroll
                 for (int v = 0; v < 7; ++v)
                     rhs[k][v] -= (sF[v * NFACE + fl + step] - sF[v * NFACE + fl]) * invh;
@@ -565,9 +720,9 @@ __global__ void __launch_bounds__(NT) stage_kernel(const __grid_constant__ Param
         const int c = threadIdx.x + k * NT;
         if (c < NCELL) {
             const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-            const int bi = box_index(x, y, z);
-            const T p = sW[5 * BOX3 + bi];
-            const T a2raw = sW[6 * BOX3 + bi];
+            const int si = (z * TS + y) * BX + HALO + x;   // row_off(y, z) + x for tile cells
+            const T p = sW[5 * NCROSS + si];
+            const T a2raw = sW[6 * NCROSS + si];
             const T a2 = clamp01(a2raw);
             const T a1 = T(1) - a2;
             const T z1 = e.g1 * (p + e.pc1);  // rho_1 c_1^2

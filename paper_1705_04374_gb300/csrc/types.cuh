@@ -96,7 +96,9 @@ constexpr double RK_A[3] = {0.0, -2.915492524638791, -0.000000093517376};
 constexpr double RK_B[3] = {0.924574, 0.287713063186749, 0.626538109512740};
 
 
-constexpr size_t smem_bytes(size_t elem) { return elem * (7 * BOX3 + 8 * NFACE); }
+// Stage-kernel dynamic shared memory: primitives of the staged cells, face
+// fluxes of one direction, and the staging layout's row-offset table.
+constexpr size_t smem_bytes(size_t elem) { return elem * (7 * NCROSS + 8 * NFACE) + sizeof(int) * BX * BX; }
 
 // Launch wrappers, instantiated for double in kernels_fp64.cu (compiled
 // without FMA contraction, in the oracle's operation order) and for float in
