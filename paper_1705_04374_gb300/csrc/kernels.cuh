@@ -446,49 +446,46 @@ __global__ void __launch_bounds__(NT) reduce_kernel(const __grid_constant__ Para
 }
 
 // Both WENO5 face states of the face between the cells holding c0 and p1,
-// from the six averages m2..p3, in single precision.  The smoothness
-// indicators and candidate values are written with the first differences
-// d = v_{j+1} - v_j and second differences D_j = v_{j-1} - 2 v_j + v_{j+1},
-// shared between the two sides:
-//   beta: 13/12 D^2 + 1/4 (D +- 2d)^2 or 13/12 D^2 + 1/4 (d + d')^2,
-//   candidates: v + D/3 + d/2, v - D/6 + d/2, ...
-// which is the same polynomial algebra as the textbook form.
+// from the six averages m2..p3, in single precision.  Same algebra as the
+// textbook form, arranged to share work between the two sides:
+//   * first differences d_j and second differences D_j = d_j - d_{j-1};
+//   * 4 beta_k = (13/3) D^2 + t^2 with t = D +- 2d or d + d'; scaling every
+//     beta and eps by 4 scales every (eps + beta)^2 by 16, which cancels in
+//     the normalised weights;
+//   * candidates as increments on the cell value: q_k - v = D/3 + d/2,
+//     -D/6 + d/2, ...; the weights multiply out the three squared
+//     denominators so one division normalises them.
 __device__ __forceinline__ void weno5_pair(float m2, float m1, float c0, float p1, float p2, float p3,
-                                           float eps, float& wl, float& wr) {
+                                           float eps4, float& wl, float& wr) {
     const float d0 = m1 - m2, d1 = c0 - m1, d2 = p1 - c0, d3 = p2 - p1, d4 = p3 - p2;
     const float Dm = d1 - d0, D0 = d2 - d1, D1 = d3 - d2, D2 = d4 - d3;
-    const float k = 13.0f / 12.0f;
-    const float sm = k * Dm * Dm, s0 = k * D0 * D0, s1 = k * D1 * D1, s2 = k * D2 * D2;
+    const float k = 13.0f / 3.0f;
+    const float sm = fmaf(k * Dm, Dm, eps4), s0 = fmaf(k * D0, D0, eps4);
+    const float s1 = fmaf(k * D1, D1, eps4), s2 = fmaf(k * D2, D2, eps4);
     const float hd2 = 0.5f * d2;
-    // left state (cell c0), face to its right
-    {
-        const float t0 = Dm + 2.0f * d1, t1 = d1 + d2, t2 = D1 - 2.0f * d2;
-        float e0 = eps + fmaf(0.25f * t0, t0, sm);
-        float e1 = eps + fmaf(0.25f * t1, t1, s0);
-        float e2 = eps + fmaf(0.25f * t2, t2, s1);
+    {   // left state (cell c0), face to its right
+        const float t0 = fmaf(2.0f, d1, Dm), t1 = d1 + d2, t2 = fmaf(-2.0f, d2, D1);
+        float e0 = fmaf(t0, t0, sm), e1 = fmaf(t1, t1, s0), e2 = fmaf(t2, t2, s1);
         e0 *= e0;
         e1 *= e1;
         e2 *= e2;
-        const float a0 = 0.1f * (e1 * e2), a1 = 0.6f * (e0 * e2), a2 = 0.3f * (e0 * e1);
-        const float q0 = c0 + fmaf(Dm, 1.0f / 3.0f, 0.5f * d1);
-        const float q1 = c0 + fmaf(D0, -1.0f / 6.0f, hd2);
-        const float q2 = c0 + fmaf(D1, -1.0f / 6.0f, hd2);
-        wl = fmaf(a0, q0, fmaf(a1, q1, a2 * q2)) / (a0 + a1 + a2);
+        const float a0 = e1 * e2, a1 = 6.0f * (e0 * e2), a2 = 3.0f * (e0 * e1);
+        const float q0 = fmaf(Dm, 1.0f / 3.0f, 0.5f * d1);
+        const float q1 = fmaf(D0, -1.0f / 6.0f, hd2);
+        const float q2 = fmaf(D1, -1.0f / 6.0f, hd2);
+        wl = c0 + fmaf(a0, q0, fmaf(a1, q1, a2 * q2)) / (a0 + a1 + a2);
     }
-    // right state (cell p1, mirrored stencil), face to its left
-    {
-        const float t0 = D2 - 2.0f * d3, t1 = d2 + d3, t2 = D0 + 2.0f * d2;
-        float e0 = eps + fmaf(0.25f * t0, t0, s2);
-        float e1 = eps + fmaf(0.25f * t1, t1, s1);
-        float e2 = eps + fmaf(0.25f * t2, t2, s0);
+    {   // right state (cell p1, mirrored stencil), face to its left
+        const float t0 = fmaf(-2.0f, d3, D2), t1 = d2 + d3, t2 = fmaf(2.0f, d2, D0);
+        float e0 = fmaf(t0, t0, s2), e1 = fmaf(t1, t1, s1), e2 = fmaf(t2, t2, s0);
         e0 *= e0;
         e1 *= e1;
         e2 *= e2;
-        const float a0 = 0.1f * (e1 * e2), a1 = 0.6f * (e0 * e2), a2 = 0.3f * (e0 * e1);
-        const float q0 = p1 + fmaf(D2, 1.0f / 3.0f, -0.5f * d3);
-        const float q1 = p1 - fmaf(D1, 1.0f / 6.0f, hd2);
-        const float q2 = p1 - fmaf(D0, 1.0f / 6.0f, hd2);
-        wr = fmaf(a0, q0, fmaf(a1, q1, a2 * q2)) / (a0 + a1 + a2);
+        const float a0 = e1 * e2, a1 = 6.0f * (e0 * e2), a2 = 3.0f * (e0 * e1);
+        const float q0 = fmaf(D2, 1.0f / 3.0f, -0.5f * d3);
+        const float q1 = fmaf(D1, -1.0f / 6.0f, -hd2);
+        const float q2 = fmaf(D0, -1.0f / 6.0f, -hd2);
+        wr = p1 + fmaf(a0, q0, fmaf(a1, q1, a2 * q2)) / (a0 + a1 + a2);
     }
 }
 
@@ -551,7 +548,7 @@ __device__ __forceinline__ void face_fp32(const Eos<float>& e, const float* __re
 #pragma unroll
     for (int v = 0; v < 7; ++v) {
         const float* P = sW + v * NCROSS;
-        weno5_pair(P[i6[0]], P[i6[1]], P[i6[2]], P[i6[3]], P[i6[4]], P[i6[5]], e.eps, wl[v], wr[v]);
+        weno5_pair(P[i6[0]], P[i6[1]], P[i6[2]], P[i6[3]], P[i6[4]], P[i6[5]], 4.0f * e.eps, wl[v], wr[v]);
     }
     if (!admissible(e, wl)) {
 #pragma unroll
@@ -595,6 +592,23 @@ __device__ __forceinline__ void face_fp64(const Eos<double>& e, const double* __
     hllc<double, DIR>(e, wl, wr, F);
 }
 
+// Asynchronous global -> shared copies (cp.async) of 4 or 8 bytes, and an L2
+// prefetch of a contiguous global range (bulk, no registers or shared memory).
+template <typename T>
+__device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ void prefetch_l2(const void* gmem, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
+}
+
 // One RK stage.  parity 0: read Q_a, write Q_b; parity 1: the reverse.
 template <typename T, int STAGE>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
@@ -619,12 +633,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
     const Eos<T> e = P.eos;
     const int bc = P.bc;
 
-    for (int i = threadIdx.x; i < BX * BX; i += NT) {
-        const int y = i % BX - HALO, z = i / BX - HALO;
-        const bool yi = (unsigned)y < (unsigned)TS, zi = (unsigned)z < (unsigned)TS;
-        sRow[i] = (yi || zi) ? row_off(y, z) : -1;
-    }
-    // 1. stage the tile and its halo as primitives
+    // 1. stage the tile and its halo: raw Q by asynchronous copies (all in
+    //    flight at once), then primitives in place
     for (int i = threadIdx.x; i < NCROSS; i += NT) {
         int bx, by, bz;
         cross_decode(i, bx, by, bz);
@@ -632,13 +642,32 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
         const int gy = bc_map(bw.y0 + by, N, bc);
         const int gz = bc_map(bw.z0 + bz, N, bc);
         const size_t gi = ((size_t)gz * N + gy) * N + gx;
-        T q[7], w[7];
-#pragma unroll
-        for (int v = 0; v < 7; ++v) q[v] = Qin[v * n3 + gi];
-        cons2prim(e, q, w);
         const int si = row_off(by, bz) + bx;
 #pragma unroll
-        for (int v = 0; v < 7; ++v) sW[v * NCROSS + si] = w[v];
+        for (int v = 0; v < 7; ++v) cp_async(sW + v * NCROSS + si, Qin + v * n3 + gi);
+    }
+    if (STAGE > 0) {
+        // the update reads dQ of the tile's own cells: pull those rows into L2 now
+        for (int r = threadIdx.x; r < 7 * TS * TS; r += NT) {
+            const int v = r / (TS * TS), yz = r % (TS * TS);
+            const size_t gi = ((size_t)(bw.z0 + yz / TS) * N + (bw.y0 + yz % TS)) * N + bw.x0;
+            prefetch_l2(dQ + v * n3 + gi, TS * sizeof(T));
+        }
+    }
+    for (int i = threadIdx.x; i < BX * BX; i += NT) {
+        const int y = i % BX - HALO, z = i / BX - HALO;
+        const bool yi = (unsigned)y < (unsigned)TS, zi = (unsigned)z < (unsigned)TS;
+        sRow[i] = (yi || zi) ? row_off(y, z) : -1;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int i = threadIdx.x; i < NCROSS; i += NT) {
+        T q[7], w[7];
+#pragma unroll
+        for (int v = 0; v < 7; ++v) q[v] = sW[v * NCROSS + i];
+        cons2prim(e, q, w);
+#pragma unroll
+        for (int v = 0; v < 7; ++v) sW[v * NCROSS + i] = w[v];
     }
     __syncthreads();
 
