@@ -205,6 +205,33 @@ int ofm_solve_level(ofm_solver* solver, const ofm_cloud_params* cloud, int N, in
                     void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Allocation-free single-level solve.  The paper has no counterpart: this is
+ * an interface for callers that cannot allocate device memory, e.g. code
+ * running under a framework whose caching allocator already owns the
+ * device's memory, or a latency-critical loop in which cudaMalloc/cudaFree
+ * would synchronise the device.  It computes exactly what ofm_solve_level
+ * computes (same kernels, same results) but allocates no device or pinned
+ * memory and creates no streams or events: all device scratch lives in one
+ * file-scope __device__ array of OFM_STATIC_SCRATCH_BYTES (32 MiB) that every
+ * GPU loading this library holds until the process exits.  Inputs (sample ids,
+ * clouds from `cloud`) and outputs (`out`, `sensor_hist`, as in
+ * ofm_solve_level) are host arrays owned by the caller.
+ *   - Sizes whose scratch would exceed the array are rejected with
+ *     OFM_ENOMEM and a message giving the bytes needed (for example one FP32
+ *     sample on 64^3 fits; 512 do not).
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address (cudaGetSymbolAddress) and caches it; make that
+ *     first call before any stream capture.
+ *   - Every call uses the same array and re-initialises what it reads; calls
+ *     that overlap on the GPU (other streams or host threads) race on it.
+ *   - Synchronises `stream` before returning.
+ * ------------------------------------------------------------------------- */
+#define OFM_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int ofm_solve_level_static(const ofm_solver* solver, const ofm_cloud_params* cloud, int N, int n,
+                           const uint64_t* sample_ids, uint64_t seed, ofm_qoi* out, double* sensor_hist,
+                           void* stream);
+
+/* ---------------------------------------------------------------------------
  * OF-MLMC estimator (Section 2.4), host FP64.
  *
  * q[l] points to M[l] rows of (q_l, q_{l-1}) pairs on shared inputs

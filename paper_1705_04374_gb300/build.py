@@ -1,9 +1,9 @@
 """Build the CUDA library ``libofmlmc.so`` in-tree for sm_103a.
 
-Four translation units compiled in parallel: the solver kernels once per
+Translation units compiled in parallel: the solver kernels once per
 precision (``kernels_fp64.cu`` without FMA contraction, ``kernels_fp32.cu``),
-the device-facing C ABI (``solver.cu``) with nvcc, and ``host.cpp`` (sampler,
-estimator, errors) with g++ -ffp-contract=off.  The CUDA runtime is linked
+the device-facing C ABI (``solver.cu``, ``solver_static.cu``) with nvcc, and
+``host.cpp`` (sampler, estimator, errors) with g++ -ffp-contract=off.  The CUDA runtime is linked
 statically so the library has no run-time dependency beyond the driver.
 """
 from __future__ import annotations
@@ -28,6 +28,7 @@ SOURCES = {
     # FP32 stencil: approximate division / square root (2 ulp), flush-to-zero
     "kernels_fp32.o": _NV + ["-use_fast_math", "-c", os.path.join(CSRC, "kernels_fp32.cu")],
     "solver.o": _NV + ["-c", os.path.join(CSRC, "solver.cu")],
+    "solver_static.o": _NV + ["-c", os.path.join(CSRC, "solver_static.cu")],
     "host.o": ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I", INCLUDE,
                "-c", os.path.join(CSRC, "host.cpp")],
 }

@@ -4,6 +4,14 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "ofmlmc.h"
+
+// Solver handle: the caller's configuration and its non-dimensional units.
+struct ofm_solver {
+    ofm_solver_config cfg;
+    double p_ref, L, u_ref, t_ref;
+};
+
 namespace ofm {
 
 // Record `fmt` as the calling thread's last error and return `code`.

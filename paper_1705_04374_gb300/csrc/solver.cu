@@ -63,11 +63,6 @@ struct Layout {
 
 }  // namespace
 
-struct ofm_solver {
-    ofm_solver_config cfg;
-    double p_ref, L, u_ref, t_ref;
-};
-
 struct GroupHost {
     int N, M;
     ofm_qoi* qoi_out;

@@ -20,6 +20,7 @@ OFM_RADII_UNIFORM, OFM_RADII_LOGNORMAL = 0, 1
 OFM_MODE_TOL, OFM_MODE_BUDGET = 0, 1
 OFM_ST_NONFINITE, OFM_ST_NEGATIVE, OFM_ST_MAXSTEPS = 1, 2, 4
 OFM_MAX_SENSORS, OFM_MAX_GROUPS, OFM_MAX_LEVELS = 8, 8, 16
+OFM_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 class ofm_bubble(C.Structure):
@@ -90,6 +91,8 @@ SIGNATURES = {
                                   _vp]),
     "ofm_solve_level": (C.c_int, [_vp, _P(ofm_cloud_params), C.c_int, C.c_int, _P(C.c_uint64),
                                   C.c_uint64, _P(ofm_qoi), _P(C.c_double), _vp, C.c_size_t, _vp]),
+    "ofm_solve_level_static": (C.c_int, [_vp, _P(ofm_cloud_params), C.c_int, C.c_int, _P(C.c_uint64),
+                                         C.c_uint64, _P(ofm_qoi), _P(C.c_double), _vp]),
     "ofm_estimate": (C.c_int, [C.c_int, _P(C.c_int64), _P(_P(C.c_double)), _P(C.c_double),
                                _P(ofm_estimate_out)]),
     "ofm_optimal_samples": (C.c_int, [C.c_int, _P(C.c_double), _P(C.c_double), _P(C.c_int64),
