@@ -266,6 +266,67 @@ int ofm_optimal_samples(int L, const double* sigma_tilde2, const double* W, cons
 /* Eq. (warmup): M_l = ceil(W_L / W_l / 2^(L-l)). */
 int ofm_warmup_samples(int L, const double* W, int64_t* M_out);
 
+/* ---------------------------------------------------------------------------
+ * Surrogate control variate (not in the paper).  An MLP s(x) of the cloud
+ * geometry x predicts the finest-level QoI; it enters the estimator only as
+ * an extra control variate for the top-level term D = q_L - alpha_{L-1} q_{L-1}:
+ *   E[D] ~ mean_M(D) + beta (mean_N(s) - mean_M(s)),
+ * with s evaluated on the M finest-pair inputs and on N independent extra
+ * inputs.  beta = Cov(D, s)/(V[s] (1 + M/N)) minimises the variance, which is
+ * then (V[D] - Cov(D, s)^2/(V[s] (1 + M/N)))/M.  The estimate is unbiased for
+ * any fixed beta, so a poor surrogate costs variance, never bias.
+ * Host FP64; arrays are host pointers; M >= 2, N >= 1.
+ * ------------------------------------------------------------------------- */
+int ofm_surrogate_cv(const double* D, const double* s_paired, int64_t M, const double* s_extra, int64_t N,
+                     double* beta, double* corrected_mean, double* variance);
+
+/* ---------------------------------------------------------------------------
+ * MLP (the surrogate network): d_in -> hidden (x n_hidden, exact-erf GELU) ->
+ * d_out.  Parameters are one FP32 vector: for each layer l, W_l as
+ * (fan_in x fan_out) row-major, then b_l (fan_out).  Every GEMM rounds its
+ * operands to BF16 (round to nearest even) and accumulates in FP32 on the
+ * tensor cores; activations, gradients, master weights and Adam moments are
+ * FP32.  Inputs are standardised by (x - x_mean)/x_std and targets by
+ * (t - y_mean)/y_std (ofm_mlp_set_scaling; identity until set); the loss is
+ * the mean squared error in standardised target space; forward returns
+ * de-standardised outputs.  X, T, Y are device pointers, row-major
+ * (rows x d_in / d_out).  Training is full-batch Adam (beta 0.9/0.999,
+ * eps 1e-8) with n <= max_rows; forward takes any n (chunks of max_rows).
+ * All reductions have a fixed order (deterministic).
+ * ------------------------------------------------------------------------- */
+#define OFM_MLP_MAX_LAYERS 8
+#define OFM_MLP_MAX_STEPS 200000
+typedef struct ofm_mlp ofm_mlp;
+int ofm_mlp_workspace_bytes(int d_in, int hidden, int n_hidden, int d_out, int max_rows, size_t* bytes);
+int ofm_mlp_create(ofm_mlp** out, int d_in, int hidden, int n_hidden, int d_out, int max_rows, void* workspace,
+                   size_t workspace_bytes);
+void ofm_mlp_destroy(ofm_mlp* mlp);
+int ofm_mlp_param_count(const ofm_mlp* mlp, int64_t* n);
+/* Host copies of the parameter vector; set also resets the Adam state. */
+int ofm_mlp_set_params(ofm_mlp* mlp, const float* host_params);
+int ofm_mlp_get_params(ofm_mlp* mlp, float* host_params);
+/* Host arrays of d_in / d_out entries; a zero std leaves that entry unscaled. */
+int ofm_mlp_set_scaling(ofm_mlp* mlp, const float* x_mean, const float* x_std, const float* y_mean,
+                        const float* y_std);
+int ofm_mlp_forward(ofm_mlp* mlp, const float* X, int n, float* Y, void* stream);
+/* Loss and gradient (host copies) at the current parameters, without a step. */
+int ofm_mlp_gradients(ofm_mlp* mlp, const float* X, const float* T, int n, float* grads_host, float* loss_host,
+                      void* stream);
+/* `steps` Adam steps (one CUDA graph per step, replayed); the loss before
+ * each step goes to loss_hist_host[steps] if not NULL.  Synchronises. */
+int ofm_mlp_train(ofm_mlp* mlp, const float* X, const float* T, int n, int steps, float lr, float* loss_hist_host,
+                  void* stream);
+/* Column mean and standard deviation (M-1) of a device matrix, into device
+ * FP64 arrays, fixed summation order. */
+int ofm_column_moments(const float* X, int rows, int cols, double* mean_dev, double* std_dev, void* stream);
+/* Surrogate inputs: per cloud, its bubbles sorted by the distance of the
+ * centre from the domain centre (ties by index), each as
+ * ((x - L/2)/scale, (y - L/2)/scale, (z - L/2)/scale, r/scale).
+ * bubbles_dev: device [n_clouds][n_bubbles][4] doubles (metres);
+ * X_dev: device [n_clouds][4 n_bubbles] floats. */
+int ofm_cloud_features(const double* bubbles_dev, int n_clouds, int n_bubbles, double domain_L, double scale,
+                       float* X_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,6 +18,18 @@ from scipy.special import erf
 SQRT1_2 = 1.0 / math.sqrt(2.0)
 
 
+def bf16(x) -> np.ndarray:
+    """Round to the nearest BF16 value (ties to even), via the FP32 value.
+
+    BF16 keeps the top 16 bits of an IEEE single; rounding adds 0x7FFF plus
+    the lowest kept bit before truncating (finite inputs).
+    """
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 def gelu(x: np.ndarray) -> np.ndarray:
     return 0.5 * x * (1.0 + erf(x * SQRT1_2))
 
@@ -26,13 +38,21 @@ def gelu_grad(x: np.ndarray) -> np.ndarray:
     return 0.5 * (1.0 + erf(x * SQRT1_2)) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
 
 
-def forward(params: List[Tuple[np.ndarray, np.ndarray]], X: np.ndarray):
-    """Returns (output, cache of pre-activations and activations)."""
+def _op(a, lowp: bool):
+    return bf16(a) if lowp else a
+
+
+def forward(params: List[Tuple[np.ndarray, np.ndarray]], X: np.ndarray, lowp: bool = False):
+    """Returns (output, cache of pre-activations and activations).
+
+    lowp: round every GEMM operand to BF16 (the network's specified operand
+    precision); products and sums stay FP64.
+    """
     acts = [X]
     pres = []
     h = X
     for i, (Wt, b) in enumerate(params):
-        z = h @ Wt + b
+        z = _op(h, lowp) @ _op(Wt, lowp) + b
         pres.append(z)
         h = gelu(z) if i + 1 < len(params) else z
         acts.append(h)
@@ -43,8 +63,8 @@ def mse_loss(y: np.ndarray, t: np.ndarray) -> float:
     return float(np.mean((y - t) ** 2))
 
 
-def backward(params, cache, y: np.ndarray, t: np.ndarray):
-    """Gradients of the MSE loss w.r.t. every (W, b)."""
+def backward(params, cache, y: np.ndarray, t: np.ndarray, lowp: bool = False):
+    """Gradients of the MSE loss w.r.t. every (W, b); lowp as in forward."""
     acts, pres = cache
     g = 2.0 * (y - t) / y.size
     grads = [None] * len(params)
@@ -52,8 +72,8 @@ def backward(params, cache, y: np.ndarray, t: np.ndarray):
         Wt, _ = params[i]
         if i + 1 < len(params):
             g = g * gelu_grad(pres[i])
-        grads[i] = (acts[i].T @ g, g.sum(axis=0))
-        g = g @ Wt.T
+        grads[i] = (_op(acts[i], lowp).T @ _op(g, lowp), g.sum(axis=0))
+        g = _op(g, lowp) @ _op(Wt, lowp).T
     return grads
 
 
@@ -93,3 +113,33 @@ def train(params, X, T, epochs: int, batch: int, lr: float = 1e-3):
             losses.append(mse_loss(y, tb))
             params = opt.step(params, backward(params, cache, y, tb))
     return params, losses
+
+
+def flatten(params) -> np.ndarray:
+    """Parameter vector: for each layer W (fan_in x fan_out, row-major) then b."""
+    return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in params])
+
+
+def unflatten(vec: np.ndarray, sizes) -> list:
+    out, at = [], 0
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        W = vec[at:at + a * b].reshape(a, b)
+        at += a * b
+        bb = vec[at:at + b]
+        at += b
+        out.append((W.copy(), bb.copy()))
+    return out
+
+
+def cloud_features(bubbles: np.ndarray, domain_L: float, scale: float) -> np.ndarray:
+    """Bubbles (nb, 4) in metres -> features sorted by distance of the centre
+    from the domain centre (ties by index): ((x-c)/s, (y-c)/s, (z-c)/s, r/s)."""
+    c = 0.5 * domain_L
+    inv = 1.0 / scale
+    d = bubbles[:, :3] - c
+    key = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]
+    order = np.lexsort((np.arange(len(key)), key))
+    f = np.empty((len(key), 4))
+    f[:, :3] = (bubbles[order, :3] - c) * inv
+    f[:, 3] = bubbles[order, 3] * inv
+    return f.ravel()

@@ -29,6 +29,7 @@ SOURCES = {
     "kernels_fp32.o": _NV + ["-use_fast_math", "-c", os.path.join(CSRC, "kernels_fp32.cu")],
     "solver.o": _NV + ["-c", os.path.join(CSRC, "solver.cu")],
     "solver_static.o": _NV + ["-c", os.path.join(CSRC, "solver_static.cu")],
+    "mlp.o": _NV + ["-c", os.path.join(CSRC, "mlp.cu")],
     "host.o": ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I", INCLUDE,
                "-c", os.path.join(CSRC, "host.cpp")],
 }

@@ -234,3 +234,18 @@ extern "C" int ofm_optimal_samples(int L, const double* st2, const double* W, co
         }
     }
 }
+
+extern "C" int ofm_surrogate_cv(const double* D, const double* s_paired, int64_t M, const double* s_extra, int64_t N,
+                                double* beta, double* corrected_mean, double* variance) {
+    if (!D || !s_paired || !s_extra || M < 2 || N < 1 || !beta || !corrected_mean || !variance)
+        return fail(OFM_EINVAL, "ofm_surrogate_cv: bad arguments");
+    std::vector<double> d(D, D + M), sp(s_paired, s_paired + M), se(s_extra, s_extra + N);
+    const double vs = var_of(sp);
+    const double c = cov_of(d, sp);
+    const double f = 1.0 + (double)M / (double)N;
+    const double b = vs > 0.0 ? c / (vs * f) : 0.0;
+    *beta = b;
+    *corrected_mean = mean_of(d) + b * (mean_of(se) - mean_of(sp));
+    *variance = vs > 0.0 ? (var_of(d) - c * c / (vs * f)) / (double)M : var_of(d) / (double)M;
+    return OFM_OK;
+}

@@ -93,6 +93,20 @@ SIGNATURES = {
                                   C.c_uint64, _P(ofm_qoi), _P(C.c_double), _vp, C.c_size_t, _vp]),
     "ofm_solve_level_static": (C.c_int, [_vp, _P(ofm_cloud_params), C.c_int, C.c_int, _P(C.c_uint64),
                                          C.c_uint64, _P(ofm_qoi), _P(C.c_double), _vp]),
+    "ofm_surrogate_cv": (C.c_int, [_P(C.c_double), _P(C.c_double), C.c_int64, _P(C.c_double), C.c_int64,
+                                   _P(C.c_double), _P(C.c_double), _P(C.c_double)]),
+    "ofm_mlp_workspace_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P(C.c_size_t)]),
+    "ofm_mlp_create": (C.c_int, [_P(_vp), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, C.c_size_t]),
+    "ofm_mlp_destroy": (None, [_vp]),
+    "ofm_mlp_param_count": (C.c_int, [_vp, _P(C.c_int64)]),
+    "ofm_mlp_set_params": (C.c_int, [_vp, _P(C.c_float)]),
+    "ofm_mlp_get_params": (C.c_int, [_vp, _P(C.c_float)]),
+    "ofm_mlp_set_scaling": (C.c_int, [_vp, _P(C.c_float), _P(C.c_float), _P(C.c_float), _P(C.c_float)]),
+    "ofm_mlp_forward": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp]),
+    "ofm_mlp_gradients": (C.c_int, [_vp, _vp, _vp, C.c_int, _P(C.c_float), _P(C.c_float), _vp]),
+    "ofm_mlp_train": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _P(C.c_float), _vp]),
+    "ofm_column_moments": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp]),
+    "ofm_cloud_features": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp]),
     "ofm_estimate": (C.c_int, [C.c_int, _P(C.c_int64), _P(_P(C.c_double)), _P(C.c_double),
                                _P(ofm_estimate_out)]),
     "ofm_optimal_samples": (C.c_int, [C.c_int, _P(C.c_double), _P(C.c_double), _P(C.c_int64),

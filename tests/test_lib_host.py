@@ -105,3 +105,14 @@ def test_workspace_size_accounts_for_three_state_buffers():
         nv.check(L.ofm_batch_workspace_bytes(s.h, C.byref(cp), garr, 1, C.byref(n)), "ws")
         state = 3 * 3 * 7 * 64 ** 3 * es
         assert state <= n.value < state * 1.05
+
+
+def test_surrogate_cv_host_matches_oracle():
+    from paper_1705_04374_gb300 import surrogate as S
+    rng = np.random.default_rng(0)
+    D = rng.normal(size=50)
+    sp = D * 0.8 + rng.normal(size=50) * 0.3
+    se = rng.normal(size=400) * 0.9
+    a, b = S.surrogate_cv(D, sp, se), E.surrogate_cv(D, sp, se)
+    for k in ("beta", "mean", "var"):
+        assert abs(a[k] - b[k]) <= 1e-13 * max(1.0, abs(b[k]))
