@@ -267,6 +267,50 @@ int ofm_optimal_samples(int L, const double* sigma_tilde2, const double* W, cons
 int ofm_warmup_samples(int L, const double* W, int64_t* M_out);
 
 /* ---------------------------------------------------------------------------
+ * Adaptive OF-MLMC over GPU solves (Section 2.4.3, steps 1-8).
+ * Level l solves on N[l]^3; pair i of level l uses the cloud of sample id
+ * (l << 40) | i for both its members (N[l] and N[l-1]).  Step 1 takes the
+ * warm-up numbers of Eq. (warmup) from the cost model W_l ~ N_l^4 (+ N_{l-1}^4),
+ * raised to min_samples (>= 2: without the optional Bayesian fit of step 3 a
+ * variance needs two samples).  Each iteration solves every level's missing
+ * pairs in one uneven batch (split only if it exceeds max_batch_bytes; 0 =
+ * 80% of the free device memory), measures the pair costs W_l as mean
+ * cell-steps per pair, excludes pairs with a failed member (status != 0),
+ * computes the estimator (ofm_estimate) and stops when eps_OF <= target (tol
+ * mode) or the cell-steps spent reach target (budget mode); otherwise step 7
+ * re-optimises M_l (ofm_optimal_samples, keeping computed pairs).
+ * pairs_out / ids_out (host, may be NULL): the (q_l, q_{l-1}) rows and sample
+ * ids of the pairs used, level by level; pairs_capacity rows.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int L;                     /* finest level index (levels 0..L, L <= 3) */
+    int N[OFM_MAX_LEVELS];     /* grid per level, coarse to fine */
+    int mode;                  /* OFM_MODE_TOL or OFM_MODE_BUDGET */
+    double target;             /* tau [QoI units] or budget [cell-steps] */
+    int qoi;                   /* 0: p_peak; 1 + k: sensor_peak[k] */
+    uint64_t seed;
+    int max_iterations;
+    int min_samples;
+    size_t max_batch_bytes;
+    double max_cell_steps;     /* safety cap on the total work (0 = none): an iteration that
+                                  would exceed it is not started and result.capped is set */
+} ofm_run_config;
+
+typedef struct {
+    int iterations;
+    int64_t M[OFM_MAX_LEVELS];   /* pairs used per level (failed ones excluded) */
+    double W[OFM_MAX_LEVELS];    /* mean cell-steps per pair */
+    double gpu_seconds;          /* device time of the solves (CUDA events) */
+    double cell_steps;           /* total cell-steps solved */
+    int64_t failed;              /* pairs excluded */
+    int capped;                  /* 1 if max_cell_steps stopped the loop */
+    ofm_estimate_out est;        /* final estimator, Eqs. (ocv-mlmc), (ocv-mlmc-err) */
+} ofm_run_result;
+
+int ofm_run(ofm_solver* solver, const ofm_cloud_params* cloud, const ofm_run_config* config, double* pairs_out,
+            uint64_t* ids_out, int64_t pairs_capacity, ofm_run_result* result, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Surrogate control variate (not in the paper).  An MLP s(x) of the cloud
  * geometry x predicts the finest-level QoI; it enters the estimator only as
  * an extra control variate for the top-level term D = q_L - alpha_{L-1} q_{L-1}:

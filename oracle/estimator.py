@@ -141,10 +141,16 @@ def estimate(pairs, W):
 
 
 def optimal_M(sig_t2, W, target: float, mode: str) -> np.ndarray:
-    """Eq. (M-tol) (mode 'tol', target = tau) or Eq. (M-budget) (mode 'budget', target = B)."""
+    """Eq. (M-tol) (mode 'tol', target = tau) or Eq. (M-budget) (mode 'budget', target = B).
+
+    Both formulas divide by sum_k sqrt(sigma~^2_k W_k); when every sigma~^2 is
+    zero (a QoI without sampling variance) no sample is needed: zeros.
+    """
     s = np.asarray(sig_t2, dtype=np.float64)
     W = np.asarray(W, dtype=np.float64)
     total = float(np.sum(np.sqrt(s * W)))
+    if total == 0.0:
+        return np.zeros(len(s), dtype=np.int64)
     if mode == "tol":
         raw = (1.0 / target ** 2) * np.sqrt(s / W) * total
     elif mode == "budget":

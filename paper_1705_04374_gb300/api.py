@@ -248,3 +248,42 @@ def warmup_samples(W) -> np.ndarray:
     out = (C.c_int64 * (L + 1))()
     nv.check(nv.lib().ofm_warmup_samples(L, Wc, out), "ofm_warmup_samples")
     return np.array(out[:])
+
+
+def run_ofmlmc(solver: Solver, cloud, levels, target: float, mode: str = "tol", qoi: int = 0,
+               seed: int = 20170509, max_iterations: int = 10, min_samples: int = 2,
+               max_batch_bytes: int = 0, capacity: int = 1 << 16, max_cell_steps: float = 0.0):
+    """ofm_run: the adaptive OF-MLMC loop over GPU solves.  Returns (result dict, pairs per level, ids per level)."""
+    cfg = nv.ofm_run_config()
+    cfg.L = len(levels) - 1
+    for i, n in enumerate(levels):
+        cfg.N[i] = n
+    cfg.mode = nv.OFM_MODE_TOL if mode == "tol" else nv.OFM_MODE_BUDGET
+    cfg.target = target
+    cfg.qoi = qoi
+    cfg.seed = seed
+    cfg.max_iterations = max_iterations
+    cfg.min_samples = min_samples
+    cfg.max_batch_bytes = max_batch_bytes
+    cfg.max_cell_steps = max_cell_steps
+    cp = cloud_params(cloud)
+    pairs = np.zeros((capacity, 2))
+    ids = np.zeros(capacity, dtype=np.uint64)
+    res = nv.ofm_run_result()
+    nv.check(nv.lib().ofm_run(solver.h, C.byref(cp), C.byref(cfg), pairs.ctypes.data_as(C.POINTER(C.c_double)),
+                              ids.ctypes.data_as(C.POINTER(C.c_uint64)), capacity, C.byref(res),
+                              _torch_stream_ptr()), "ofm_run")
+    L = cfg.L
+    M = [res.M[l] for l in range(L + 1)]
+    per_pairs, per_ids, at = [], [], 0
+    for l in range(L + 1):
+        per_pairs.append(pairs[at:at + M[l]].copy())
+        per_ids.append(ids[at:at + M[l]].copy())
+        at += M[l]
+    n = L + 1
+    est = dict(alpha=np.array(res.est.alpha[:n]), sigma2=np.array(res.est.sigma2[:n]),
+               cov=np.array(res.est.cov[:n]), sigma_tilde2=np.array(res.est.sigma_tilde2[:n]),
+               mean=res.est.mean, eps2=res.est.eps2)
+    out = dict(iterations=res.iterations, M=M, W=[res.W[l] for l in range(n)], gpu_seconds=res.gpu_seconds,
+               cell_steps=res.cell_steps, failed=res.failed, capped=res.capped, est=est)
+    return out, per_pairs, per_ids

@@ -30,6 +30,7 @@ SOURCES = {
     "solver.o": _NV + ["-c", os.path.join(CSRC, "solver.cu")],
     "solver_static.o": _NV + ["-c", os.path.join(CSRC, "solver_static.cu")],
     "mlp.o": _NV + ["-c", os.path.join(CSRC, "mlp.cu")],
+    "run.o": _NV + ["-c", os.path.join(CSRC, "run.cu")],
     "host.o": ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I", INCLUDE,
                "-c", os.path.join(CSRC, "host.cpp")],
 }

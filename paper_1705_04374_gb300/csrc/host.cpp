@@ -213,6 +213,10 @@ extern "C" int ofm_optimal_samples(int L, const double* st2, const double* W, co
         if (!(rem > 0.0))
             return fail(OFM_EINVAL, "ofm_optimal_samples: target already consumed by kept samples");
         const double t = mode == OFM_MODE_TOL ? std::sqrt(rem) : rem;
+        if (total == 0.0) {  // no sampling variance left on the free levels: they need no samples
+            for (int l = 0; l < n; ++l) M_out[l] = fixed[l] ? M_done[l] : (M_done ? M_done[l] : 0);
+            return OFM_OK;
+        }
         bool newly = false;
         for (int l = 0; l < n; ++l) {
             if (fixed[l]) {

@@ -62,6 +62,18 @@ class ofm_estimate_out(C.Structure):
                 ("mean", C.c_double), ("eps2", C.c_double)]
 
 
+class ofm_run_config(C.Structure):
+    _fields_ = [("L", C.c_int), ("N", C.c_int * OFM_MAX_LEVELS), ("mode", C.c_int), ("target", C.c_double),
+                ("qoi", C.c_int), ("seed", C.c_uint64), ("max_iterations", C.c_int), ("min_samples", C.c_int),
+                ("max_batch_bytes", C.c_size_t), ("max_cell_steps", C.c_double)]
+
+
+class ofm_run_result(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("M", C.c_int64 * OFM_MAX_LEVELS), ("W", C.c_double * OFM_MAX_LEVELS),
+                ("gpu_seconds", C.c_double), ("cell_steps", C.c_double), ("failed", C.c_int64),
+                ("capped", C.c_int), ("est", ofm_estimate_out)]
+
+
 _vp = C.c_void_p
 _P = C.POINTER
 
@@ -93,6 +105,8 @@ SIGNATURES = {
                                   C.c_uint64, _P(ofm_qoi), _P(C.c_double), _vp, C.c_size_t, _vp]),
     "ofm_solve_level_static": (C.c_int, [_vp, _P(ofm_cloud_params), C.c_int, C.c_int, _P(C.c_uint64),
                                          C.c_uint64, _P(ofm_qoi), _P(C.c_double), _vp]),
+    "ofm_run": (C.c_int, [_vp, _P(ofm_cloud_params), _P(ofm_run_config), _P(C.c_double), _P(C.c_uint64),
+                          C.c_int64, _P(ofm_run_result), _vp]),
     "ofm_surrogate_cv": (C.c_int, [_P(C.c_double), _P(C.c_double), C.c_int64, _P(C.c_double), C.c_int64,
                                    _P(C.c_double), _P(C.c_double), _P(C.c_double)]),
     "ofm_mlp_workspace_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P(C.c_size_t)]),

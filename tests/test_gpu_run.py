@@ -1,0 +1,90 @@
+"""The adaptive OF-MLMC driver (ofm_run) over GPU solves, against the oracle."""
+from concurrent.futures import ThreadPoolExecutor
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import cloud as ocloud
+from oracle import estimator as E
+from oracle import solver as osolver
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1705_04374_gb300 import api  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    torch.cuda.set_device(0)
+
+
+def test_two_level_run_matches_oracle_estimator_and_solves():
+    w = W.cfg1()
+    sp = w.solver
+    s = api.Solver(sp, "fp64")
+    # warm-up iteration only (steps 1-5)
+    res, pairs, ids = api.run_ofmlmc(s, w.cloud, [16, 32], target=1.0, qoi=1, seed=W.BASE_SEED,
+                                     max_iterations=1, max_cell_steps=5e8)
+    assert res["iterations"] == 1 and res["failed"] == 0
+    # warm-up numbers: Eq. (warmup) with W ~ N^4, at least 2 per level
+    assert res["M"] == [9, 2]
+    assert res["W"][1] > res["W"][0] > 0
+    # the estimator on the returned pairs is the oracle's estimator
+    ref = E.estimate(pairs, res["W"])
+    for k in ("alpha", "sigma2", "cov", "sigma_tilde2"):
+        assert np.allclose(res["est"][k], ref[k], rtol=1e-12, atol=1e-12), k
+    assert abs(res["est"]["mean"] - ref["mean"]) <= 1e-12 * abs(ref["mean"])
+    # sampled pairs equal the oracle's solves of the same clouds (pair members share the cloud)
+    picks = [(0, 0), (0, res["M"][0] - 1), (1, 0), (1, res["M"][1] - 1)]
+
+    def one(lp):
+        l, i = lp
+        sid = int(ids[l][i])
+        bub = ocloud.sample_cloud(w.cloud, W.BASE_SEED, sid)
+        qf, _, _ = osolver.solve(sp, [16, 32][l], bub)
+        qc = osolver.solve(sp, 16, bub)[0] if l == 1 else None
+        return lp, qf, qc
+    with ThreadPoolExecutor(max(1, os.cpu_count() or 1)) as ex:
+        for (l, i), qf, qc in ex.map(one, picks):
+            assert abs(pairs[l][i, 0] - qf["sensor_peak"][0]) <= 1e-9 * abs(qf["sensor_peak"][0])
+            if qc is not None:
+                assert abs(pairs[l][i, 1] - qc["sensor_peak"][0]) <= 1e-9 * abs(qc["sensor_peak"][0])
+    # steps 6-8: a second iteration towards half the warm-up error takes the
+    # oracle's step-7 sample numbers (keeping the warm-up pairs)
+    tau = 0.5 * np.sqrt(res["est"]["eps2"])
+    want = E.optimal_M_keep(res["est"]["sigma_tilde2"], res["W"], res["M"], tau, "tol")
+    planned = float(np.sum((want - np.array(res["M"])) * np.array(res["W"])))
+    if planned < 5e8:
+        res2, pairs2, _ = api.run_ofmlmc(s, w.cloud, [16, 32], target=tau, qoi=1, seed=W.BASE_SEED,
+                                         max_iterations=2, max_cell_steps=1e9)
+        assert res2["M"] == list(want)
+        for l in range(2):   # the warm-up pairs are kept, unchanged
+            assert np.array_equal(pairs2[l][:res["M"][l]], pairs[l])
+
+
+def test_budget_mode_stops_when_spent():
+    w = W.tiny(16, 4)
+    s = api.Solver(w.solver, "fp32")
+    budget = 3.0e8
+    res, pairs, ids = api.run_ofmlmc(s, w.cloud, [8, 16], target=budget, mode="budget", qoi=1,
+                                     max_iterations=6, max_cell_steps=2e9)
+    assert res["gpu_seconds"] > 0
+    if res["iterations"] < 6:
+        assert res["cell_steps"] >= 0.9 * budget
+
+
+def test_memory_admission_splits_batches_without_changing_results():
+    w = W.tiny(16, 4)
+    s = api.Solver(w.solver, "fp32")
+    a, pa, ia = api.run_ofmlmc(s, w.cloud, [8, 16], target=1e9, qoi=0, max_iterations=1, max_cell_steps=1e8)
+    b, pb, ib = api.run_ofmlmc(s, w.cloud, [8, 16], target=1e9, qoi=0, max_iterations=1, max_cell_steps=1e8,
+                               max_batch_bytes=600 * 1024)
+    for l in range(2):
+        assert np.array_equal(ia[l], ib[l])
+        assert np.array_equal(pa[l], pb[l])
+    assert a["est"]["mean"] == b["est"]["mean"]

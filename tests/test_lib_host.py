@@ -116,3 +116,8 @@ def test_surrogate_cv_host_matches_oracle():
     a, b = S.surrogate_cv(D, sp, se), E.surrogate_cv(D, sp, se)
     for k in ("beta", "mean", "var"):
         assert abs(a[k] - b[k]) <= 1e-13 * max(1.0, abs(b[k]))
+
+
+def test_zero_variance_needs_no_samples_in_the_library():
+    assert list(api.optimal_samples([0.0, 0.0], [1.0, 16.0], 0.1, "tol", [5, 3])) == [5, 3]
+    assert list(api.optimal_samples([0.0, 0.0], [1.0, 16.0], 1e3, "budget")) == [0, 0]

@@ -161,3 +161,8 @@ def test_adaptive_loop_reaches_tolerance_on_toy():
     assert len(est["history"]) <= 4
     assert abs(est["mean"] - mean[L]) < 5 * 0.02
     assert est["history"][0] == list(np.maximum(E.warmup_M(W), 2))
+
+
+def test_zero_variance_needs_no_samples():
+    assert list(E.optimal_M([0.0, 0.0], [1.0, 16.0], 0.1, "tol")) == [0, 0]
+    assert list(E.optimal_M([0.0, 0.0], [1.0, 16.0], 1e3, "budget")) == [0, 0]
