@@ -1,0 +1,323 @@
+"""Estimator-level experiments on one GPU (each prints one JSON object).
+
+    python -m paper_1705_04374_gb300.experiments uneven3 [--quick]
+    python -m paper_1705_04374_gb300.experiments surrogate [--quick]
+    python -m paper_1705_04374_gb300.experiments rmse [--quick]
+
+uneven3   three levels 32^3 / 64^3 / 128^3 with 1024 / 128 / 16 pairs of 50-bubble
+          clouds (FP32 stencil, FP64 reductions) in one uneven batch; device time,
+          cell-updates/s, pair costs, the OF-MLMC estimator; and the same solves
+          as one batch per group, for comparison.
+surrogate the MLP surrogate trained on the solver's own samples and used as the
+          estimator's extra control variate: (a) on the level-0 term, geometry
+          only, expectation from 65,536 extra clouds; (b) on the top term,
+          geometry plus the coarse QoI.  Variance with and without it, and the
+          plain estimator's variance at equal GPU-seconds.
+rmse      GPU-seconds to a fixed OF-MLMC RMSE: the adaptive loop in plain FP64
+          against FP32 (+ the level-0 surrogate), with the FP32 bias measured on
+          common samples and included in the RMSE.
+
+Every computation runs in the library's kernels and host code (C ABI); this
+module only orders the calls and times them with CUDA events.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+from paper_1705_04374_gb300 import api  # noqa: E402
+from paper_1705_04374_gb300 import native as nv  # noqa: E402
+from paper_1705_04374_gb300 import surrogate as S  # noqa: E402
+
+ID_SHIFT = 40
+QOI = 1   # the centre sensor's peak pressure (the paper's estimator QoI is the centre sensor)
+
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _qoi(q, which):
+    return q["p_peak"] if which == 0 else q["sensor_peak"][which - 1]
+
+
+def solve_groups(solver, cloud, spec, seed=W.BASE_SEED):
+    """spec: list of (N, ids).  One uneven batch; returns (per-group QoI dicts, device seconds, cell-steps)."""
+    import torch
+    sp = solver.sp
+    groups = [api.make_group(sp, N, ids, seed) for (N, ids) in spec]
+    b = api.Batch(solver, cloud, groups)
+    e0, e1 = _events()
+    e0.record()
+    b.init()
+    while b.run(1 << 20) > 0:
+        pass
+    e1.record()
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    cells = b.cell_steps()
+    b.qoi(allow_bad=True)
+    out = [g.qoi_dicts(len(sp.sensors)) for g in groups]
+    b.close()
+    return out, secs, cells
+
+
+def level_ids(l, lo, hi):
+    return [(l << ID_SHIFT) | i for i in range(lo, hi)]
+
+
+def pairs_from(qf, qc, which):
+    rows, bad = [], 0
+    for i in range(len(qf)):
+        ok = qf[i]["status"] == 0 and (qc is None or qc[i]["status"] == 0)
+        if not ok:
+            bad += 1
+            continue
+        rows.append((_qoi(qf[i], which), _qoi(qc[i], which) if qc is not None else 0.0))
+    return np.array(rows), bad
+
+
+def run_levels(solver, cloud, levels, counts, which=QOI, separate=False):
+    """Pairs of every level (fine members on levels[l], coarse on levels[l-1])."""
+    spec, owner = [], []
+    for l, (N, M) in enumerate(zip(levels, counts)):
+        ids = level_ids(l, 0, M)
+        spec.append((N, ids))
+        owner.append((l, "fine"))
+        if l > 0:
+            spec.append((levels[l - 1], ids))
+            owner.append((l, "coarse"))
+    if separate:
+        res, secs, cells = [], 0.0, 0.0
+        for sg in spec:
+            r, s, c = solve_groups(solver, cloud, [sg])
+            res += r
+            secs += s
+            cells += c
+    else:
+        res, secs, cells = solve_groups(solver, cloud, spec)
+    L = len(levels) - 1
+    fine = {l: res[k] for k, (l, role) in enumerate(owner) if role == "fine"}
+    coarse = {l: res[k] for k, (l, role) in enumerate(owner) if role == "coarse"}
+    pairs, W_cells, failed = [], [], 0
+    for l in range(L + 1):
+        p, bad = pairs_from(fine[l], coarse.get(l), which)
+        pairs.append(p)
+        failed += bad
+        cs = sum(levels[l] ** 3 * q["n_steps"] for q in fine[l])
+        if l > 0:
+            cs += sum(levels[l - 1] ** 3 * q["n_steps"] for q in coarse[l])
+        W_cells.append(cs / len(fine[l]))
+    return dict(pairs=pairs, W_cells=W_cells, secs=secs, cells=cells, failed=failed, fine=fine, coarse=coarse)
+
+
+def features_for(cloud, ids, seed=W.BASE_SEED):
+    import torch
+    bub = np.stack([api.sample_cloud(cloud, seed, int(i)) for i in ids])
+    return S.cloud_features(torch.from_numpy(bub).cuda(), cloud.n_bubbles, cloud.domain_L, cloud.cloud_radius)
+
+
+def train_surrogate(X, y, steps, lr=1e-3, hidden=256, seed=0):
+    """Train the MLP on (X rows, y); returns (net, training seconds)."""
+    import torch
+    n, d = X.shape
+    net = S.MLP(d, hidden, 3, 1, max_rows=n)
+    rng = np.random.default_rng(seed)
+    sizes = net.sizes
+    vec = np.concatenate([np.concatenate([(rng.normal(size=(a, b)) * math.sqrt(2.0 / a)).ravel(), np.zeros(b)])
+                          for a, b in zip(sizes[:-1], sizes[1:])]).astype(np.float32)
+    net.set_params(vec)
+    m, s = S.column_moments(X)
+    net.set_scaling(m.cpu().numpy(), s.cpu().numpy(), np.array([y.mean()]), np.array([max(y.std(), 1e-30)]))
+    T = torch.from_numpy(y[:, None].astype(np.float32)).cuda()
+    e0, e1 = _events()
+    e0.record()
+    hist = net.train(X, T, steps=steps, lr=lr)
+    e1.record()
+    torch.cuda.synchronize()
+    return net, e0.elapsed_time(e1) / 1e3, hist
+
+
+def infer(net, X):
+    import torch
+    e0, e1 = _events()
+    e0.record()
+    Y = net.forward(X)
+    e1.record()
+    torch.cuda.synchronize()
+    return Y.cpu().numpy().ravel().astype(np.float64), e0.elapsed_time(e1) / 1e3
+
+
+# ------------------------------------------------------------------------------ uneven3
+
+def cmd_uneven3(quick):
+    w = W.cfg3()
+    counts = (128, 16, 2) if quick else (1024, 128, 16)
+    solver = api.Solver(w.solver, "fp32")
+    r = run_levels(solver, w.cloud, w.levels, counts)
+    rs = run_levels(solver, w.cloud, w.levels, counts, separate=True)
+    est = api.estimate(r["pairs"], r["W_cells"])
+    return dict(experiment="uneven3", levels=list(w.levels), counts=list(counts), precision="fp32",
+                bubbles=w.cloud.n_bubbles, qoi="centre sensor peak pressure [Pa]",
+                device_seconds=r["secs"], cell_steps=r["cells"], cell_updates_per_s=r["cells"] / r["secs"],
+                separate_batches_seconds=rs["secs"], speedup_one_batch=rs["secs"] / r["secs"],
+                identical_to_separate=bool(all(np.array_equal(a, b) for a, b in zip(r["pairs"], rs["pairs"]))),
+                W_cell_steps_per_pair=r["W_cells"], failed=r["failed"],
+                estimator={k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in est.items()})
+
+
+# ------------------------------------------------------------------------------ surrogate
+
+def cmd_surrogate(quick):
+    import torch
+    w = W.cfg3()
+    cloud = w.cloud
+    counts = (256, 32, 4) if quick else (1024, 128, 16)
+    N_extra = 8192 if quick else 65536
+    steps = 300 if quick else 600
+    solver = api.Solver(w.solver, "fp32")
+    r = run_levels(solver, cloud, w.levels, counts)
+    pairs = r["pairs"]
+    sec_per_cell = r["secs"] / r["cells"]
+    Wsec = [c * sec_per_cell for c in r["W_cells"]]
+    est = api.estimate(pairs, Wsec)
+    alpha, st2 = est["alpha"], est["sigma_tilde2"]
+    M = [len(p) for p in pairs]
+    L = len(w.levels) - 1
+    out = dict(experiment="surrogate", levels=list(w.levels), counts=list(counts), N_extra=N_extra,
+               plain=dict(mean=est["mean"], eps2=est["eps2"], sigma_tilde2=st2.tolist(), alpha=alpha.tolist(),
+                          solve_seconds=r["secs"]))
+    # (a) level-0 term, geometry only; trained on half of the level-0 samples, CV on the other half
+    ids0 = level_ids(0, 0, counts[0])
+    X0 = features_for(cloud, ids0)
+    q0 = pairs[0][:, 0]
+    n_tr = len(q0) // 2
+    net, t_train, hist = train_surrogate(X0[:n_tr], q0[:n_tr], steps)
+    s_pair, t_inf0 = infer(net, X0[n_tr:])
+    Xe = features_for(cloud, level_ids(7, 0, N_extra))     # independent extra clouds
+    s_extra, t_inf = infer(net, Xe)
+    D0 = alpha[0] * q0[n_tr:]
+    cv = S.surrogate_cv(D0, alpha[0] * s_pair, alpha[0] * s_extra)
+    plain_var0 = np.var(D0, ddof=1) / len(D0)
+    sur_seconds = t_train + t_inf0 + t_inf
+    # equal GPU-seconds: the plain estimator spends sur_seconds on more level-0 samples instead
+    extra_plain = sur_seconds / Wsec[0]
+    plain_var0_eq = np.var(D0, ddof=1) / (len(D0) + extra_plain)
+    out["level0_geometry"] = dict(train_rows=n_tr, cv_rows=len(D0), loss_first_last=[float(hist[0]), float(hist[-1])],
+                                  corr=float(np.corrcoef(s_pair, q0[n_tr:])[0, 1]), beta=cv["beta"],
+                                  var_plain=plain_var0, var_with_surrogate=cv["var"],
+                                  var_plain_equal_gpu_seconds=plain_var0_eq,
+                                  variance_ratio=cv["var"] / plain_var0,
+                                  variance_ratio_equal_gpu_seconds=cv["var"] / plain_var0_eq,
+                                  surrogate_seconds=dict(train=t_train, infer=t_inf0 + t_inf),
+                                  level0_pair_seconds=Wsec[0])
+    net.close()
+    # (b) top term, geometry + coarse QoI, trained on the lower pairs' (coarse -> fine) relation
+    Xs, ys = [], []
+    for l in range(1, L):
+        Xl = features_for(cloud, level_ids(l, 0, M[l]))
+        qc = torch.from_numpy(pairs[l][:, 1:2].astype(np.float32)).cuda()
+        Xs.append(torch.cat([Xl, qc], dim=1))
+        ys.append(pairs[l][:, 0])
+    Xtr = torch.cat(Xs, 0)
+    ytr = np.concatenate(ys)
+    net, t_train_b, hist_b = train_surrogate(Xtr, ytr, steps)
+    XL = features_for(cloud, level_ids(L, 0, M[L]))
+    XLc = torch.cat([XL, torch.from_numpy(pairs[L][:, 1:2].astype(np.float32)).cuda()], dim=1)
+    sL, _ = infer(net, XLc)
+    DL = alpha[L] * pairs[L][:, 0] - alpha[L - 1] * pairs[L][:, 1]
+    out["top_geometry_coarse"] = dict(train_rows=len(ytr), top_pairs=M[L],
+                                      loss_first_last=[float(hist_b[0]), float(hist_b[-1])],
+                                      corr_with_D_L=float(np.corrcoef(sL, DL)[0, 1]) if M[L] > 2 else None,
+                                      note="its expectation over extra clouds needs one level-(L-1) solve per "
+                                           "extra cloud (charged to GPU-seconds)")
+    net.close()
+    return out
+
+
+# ------------------------------------------------------------------------------ rmse
+
+def cmd_rmse(quick):
+    import torch
+    w = W.tiny(16, 20)
+    cloud = W.cloud_uniform(20)
+    sp = w.solver
+    levels = [16, 32, 64]
+    tau = 2.0e5 if quick else 1.0e5
+    cap64 = 3e9 if quick else 8e9
+    s64 = api.Solver(sp, "fp64")
+    s32 = api.Solver(sp, "fp32")
+    t0 = time.time()
+    r64, p64, i64 = api.run_ofmlmc(s64, cloud, levels, target=tau, qoi=QOI, max_iterations=6,
+                                   max_cell_steps=cap64)
+    wall64 = time.time() - t0
+    # FP32 bias on common samples: the FP64 run's pairs, solved again in FP32
+    common = run_levels(s32, cloud, levels, [len(p) for p in p64])
+    Wc = r64["W"]
+    e64 = api.estimate(p64, Wc)
+    e32c = api.estimate(common["pairs"], Wc)
+    bias = abs(e32c["mean"] - e64["mean"])
+    tau32 = math.sqrt(max(tau ** 2 - bias ** 2, 0.25 * tau ** 2))
+    t0 = time.time()
+    r32, p32, i32 = api.run_ofmlmc(s32, cloud, levels, target=tau32, qoi=QOI, max_iterations=6,
+                                   max_cell_steps=10 * cap64)
+    wall32 = time.time() - t0
+    out = dict(experiment="rmse", levels=levels, bubbles=20, qoi="centre sensor peak pressure [Pa]",
+               tau=tau, fp32_bias=bias,
+               fp64=dict(gpu_seconds=r64["gpu_seconds"], wall_seconds=wall64, M=r64["M"], eps=math.sqrt(r64["est"]["eps2"]),
+                         mean=r64["est"]["mean"], iterations=r64["iterations"], capped=r64["capped"]),
+               fp32=dict(gpu_seconds=r32["gpu_seconds"], wall_seconds=wall32, M=r32["M"], eps=math.sqrt(r32["est"]["eps2"]),
+                         rmse=math.sqrt(r32["est"]["eps2"] + bias ** 2), mean=r32["est"]["mean"],
+                         iterations=r32["iterations"], capped=r32["capped"]))
+    # level-0 surrogate on the FP32 run: the variance it removes from the level-0 term
+    q0 = p32[0][:, 0]
+    if len(q0) >= 64:
+        X0 = features_for(cloud, [int(i) for i in i32[0]])
+        n_tr = len(q0) // 2
+        net, t_train, hist = train_surrogate(X0[:n_tr], q0[:n_tr], 400)
+        s_pair, t1 = infer(net, X0[n_tr:])
+        s_extra, t2 = infer(net, features_for(cloud, level_ids(7, 0, 65536)))
+        a0 = r32["est"]["alpha"][0]
+        cv = S.surrogate_cv(a0 * q0[n_tr:], a0 * s_pair, a0 * s_extra)
+        ratio = cv["var"] / (np.var(a0 * q0[n_tr:], ddof=1) / (len(q0) - n_tr))
+        st2 = np.array(r32["est"]["sigma_tilde2"])
+        Wsec32 = np.array(r32["W"]) * r32["gpu_seconds"] / r32["cell_steps"]
+        def cost(st):
+            return float(np.sum(np.sqrt(st * Wsec32)) ** 2 / tau32 ** 2)
+        st_sur = st2.copy()
+        st_sur[0] *= ratio
+        out["fp32_surrogate"] = dict(level0_variance_ratio=ratio, corr=float(np.corrcoef(s_pair, q0[n_tr:])[0, 1]),
+                                     train_seconds=t_train, infer_seconds=t1 + t2,
+                                     model_gpu_seconds_plain=cost(st2),
+                                     model_gpu_seconds_with_surrogate=cost(st_sur) + t_train + t1 + t2)
+        net.close()
+    out["gpu_seconds_ratio_fp64_over_fp32"] = r64["gpu_seconds"] / max(r32["gpu_seconds"], 1e-30)
+    return out
+
+
+def main():
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["uneven3", "surrogate", "rmse"])
+    ap.add_argument("--quick", action="store_true")
+    a = ap.parse_args()
+    torch.cuda.set_device(0)
+    fn = {"uneven3": cmd_uneven3, "surrogate": cmd_surrogate, "rmse": cmd_rmse}[a.what]
+    print(json.dumps(fn(a.quick)), flush=True)
+
+
+if __name__ == "__main__":
+    main()
