@@ -179,6 +179,15 @@ class Batch:
     def set_profiling(self, on: bool):
         nv.check(nv.lib().ofm_batch_set_profiling(self.h, int(on)), "ofm_batch_set_profiling")
 
+    def set_variant(self, variant: int):
+        nv.check(nv.lib().ofm_batch_set_variant(self.h, variant), "ofm_batch_set_variant")
+
+    def variant(self):
+        v = C.c_int()
+        t = (C.c_float * 2)()
+        nv.check(nv.lib().ofm_batch_get_variant(self.h, C.byref(v), t), "ofm_batch_get_variant")
+        return v.value, (t[0], t[1])
+
     def stage_time(self):
         ms = C.c_double()
         n = C.c_int64()

@@ -609,32 +609,35 @@ __device__ __forceinline__ void prefetch_l2(const void* gmem, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
 }
 
-// One RK stage.  parity 0: read Q_a, write Q_b; parity 1: the reverse.
-template <typename T, int STAGE>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
-    stage_kernel(const __grid_constant__ Params<T> P, int parity) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sW = reinterpret_cast<T*>(smem_raw);  // [7][NCROSS] primitives, compact layout
-    T* sF = sW + 7 * NCROSS;                 // [8][NFACE] face fluxes + face velocity
-    int* sRow = reinterpret_cast<int*>(sF + 8 * NFACE);  // [BX][BX] row offsets
-
+// Per-tile context of one RK stage.  parity 0: read Q_a, write Q_b; 1: the reverse.
+template <typename T>
+struct TileCtx {
     BlockWork<T> bw;
-    decode_block(P, blockIdx.x, bw);
-    if (P.s.done[bw.slot]) return;
-    const GroupDev& G = *bw.G;
-    const int N = G.N;
-    const size_t n3 = (size_t)N * N * N;
-    const size_t soff = (size_t)bw.s_local * 7 * n3;
-    const T* __restrict__ Qin = (const T*)(parity ? G.QB : G.QA) + soff;
-    T* __restrict__ Qout = (T*)(parity ? G.QA : G.QB) + soff;
-    T* __restrict__ dQ = (T*)G.dQ + soff;
-    const T dt = (T)P.s.dt[bw.slot];
-    const T invh = T(1) / (T)G.h;  // 1/h, formed as the FP64 reference forms it
-    const Eos<T> e = P.eos;
-    const int bc = P.bc;
+    const T* Qin;
+    T* Qout;
+    T* dQ;
+};
 
-    // 1. stage the tile and its halo: raw Q by asynchronous copies (all in
-    //    flight at once), then primitives in place
+template <typename T>
+__device__ __forceinline__ void tile_ctx(const Params<T>& P, long long b, int parity, TileCtx<T>& c) {
+    decode_block(P, b, c.bw);
+    const GroupDev& G = *c.bw.G;
+    const size_t n3 = (size_t)G.N * G.N * G.N;
+    const size_t soff = (size_t)c.bw.s_local * 7 * n3;
+    c.Qin = (const T*)(parity ? G.QB : G.QA) + soff;
+    c.Qout = (T*)(parity ? G.QA : G.QB) + soff;
+    c.dQ = (T*)G.dQ + soff;
+}
+
+// Asynchronous copies of a tile's raw Q (tile and halo, boundary ghosts by
+// index mapping) into sBuf, all in flight at once; for stages that read dQ,
+// an L2 prefetch of the tile's own dQ rows.
+template <typename T, int STAGE>
+__device__ __forceinline__ void tile_issue(const Params<T>& P, const TileCtx<T>& c, T* sBuf) {
+    const BlockWork<T>& bw = c.bw;
+    const int N = bw.G->N;
+    const size_t n3 = (size_t)N * N * N;
+    const int bc = P.bc;
     for (int i = threadIdx.x; i < NCROSS; i += NT) {
         int bx, by, bz;
         cross_decode(i, bx, by, bz);
@@ -644,23 +647,28 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
         const size_t gi = ((size_t)gz * N + gy) * N + gx;
         const int si = row_off(by, bz) + bx;
 #pragma unroll
-        for (int v = 0; v < 7; ++v) cp_async(sW + v * NCROSS + si, Qin + v * n3 + gi);
+        for (int v = 0; v < 7; ++v) cp_async(sBuf + v * NCROSS + si, c.Qin + v * n3 + gi);
     }
     if (STAGE > 0) {
-        // the update reads dQ of the tile's own cells: pull those rows into L2 now
         for (int r = threadIdx.x; r < 7 * TS * TS; r += NT) {
             const int v = r / (TS * TS), yz = r % (TS * TS);
             const size_t gi = ((size_t)(bw.z0 + yz / TS) * N + (bw.y0 + yz % TS)) * N + bw.x0;
-            prefetch_l2(dQ + v * n3 + gi, TS * sizeof(T));
+            prefetch_l2(c.dQ + v * n3 + gi, TS * sizeof(T));
         }
     }
+}
+
+__device__ __forceinline__ void fill_rows(int* sRow) {
     for (int i = threadIdx.x; i < BX * BX; i += NT) {
         const int y = i % BX - HALO, z = i / BX - HALO;
         const bool yi = (unsigned)y < (unsigned)TS, zi = (unsigned)z < (unsigned)TS;
         sRow[i] = (yi || zi) ? row_off(y, z) : -1;
     }
-    cp_async_wait_all();
-    __syncthreads();
+}
+
+// Raw Q of every staged cell -> primitives, in place.
+template <typename T>
+__device__ __forceinline__ void tile_convert(const Eos<T>& e, T* sW) {
     for (int i = threadIdx.x; i < NCROSS; i += NT) {
         T q[7], w[7];
 #pragma unroll
@@ -669,7 +677,24 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
 #pragma unroll
         for (int v = 0; v < 7; ++v) sW[v * NCROSS + i] = w[v];
     }
-    __syncthreads();
+}
+
+// Faces (direction by direction), per-cell right-hand sides, alpha2 source,
+// 2N update and, in the last stage, the new state's per-tile reductions, for
+// one tile whose primitives are staged in sW.
+template <typename T, int STAGE>
+__device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& c, const T* __restrict__ sW,
+                                          T* __restrict__ sF, const int* __restrict__ sRow) {
+    const BlockWork<T>& bw = c.bw;
+    const GroupDev& G = *bw.G;
+    const int N = G.N;
+    const size_t n3 = (size_t)N * N * N;
+    const T* __restrict__ Qin = c.Qin;
+    T* __restrict__ Qout = c.Qout;
+    T* __restrict__ dQ = c.dQ;
+    const T dt = (T)P.s.dt[bw.slot];
+    const T invh = T(1) / (T)G.h;  // 1/h, formed as the FP64 reference forms it
+    const Eos<T> e = P.eos;
 
     T rhs[CELLS_PER_THREAD][7];
     T divu[CELLS_PER_THREAD];
@@ -776,6 +801,88 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
         const long long tile = blockIdx.x - G.block0 - (long long)bw.s_local * G.tps;
         block_reduce_write(red, G.part + (size_t)bw.s_local * G.tps + tile);
     }
+}
+
+// One RK stage, one block per tile.
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
+    stage_kernel(const __grid_constant__ Params<T> P, int parity) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sW = reinterpret_cast<T*>(smem_raw);  // [7][NCROSS] primitives, compact layout
+    T* sF = sW + 7 * NCROSS;                 // [8][NFACE] face fluxes + face velocity
+    int* sRow = reinterpret_cast<int*>(sF + 8 * NFACE);  // [BX][BX] row offsets
+    TileCtx<T> c;
+    tile_ctx(P, blockIdx.x, parity, c);
+    if (P.s.done[c.bw.slot]) return;
+    tile_issue<T, STAGE>(P, c, sW);
+    fill_rows(sRow);
+    cp_async_wait_all();
+    __syncthreads();
+    tile_convert(P.eos, sW);
+    __syncthreads();
+    tile_body<T, STAGE>(P, c, sW, sF, sRow);
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// First tile at or after t (stepping by stride) whose sample is not finished.
+template <typename T>
+__device__ __forceinline__ long long next_active(const Params<T>& P, long long t, long long stride) {
+    while (t < P.total_blocks) {
+        int gi = 0;
+        while (gi + 1 < P.n_groups && t >= P.g[gi + 1].block0) ++gi;
+        const GroupDev& G = P.g[gi];
+        const int slot = G.slot0 + (int)((t - G.block0) / G.tps);
+        if (!P.s.done[slot]) return t;
+        t += stride;
+    }
+    return t;
+}
+
+// One RK stage, persistent blocks: each block walks tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ... (finished samples skipped without a launch),
+// copying the next tile's raw Q into a second shared buffer while it computes
+// the current one.  Same arithmetic, same results as stage_kernel.
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    stage_kernel_pp(const __grid_constant__ Params<T> P, int parity) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sW0 = reinterpret_cast<T*>(smem_raw);
+    T* sW1 = sW0 + 7 * NCROSS;
+    T* sF = sW1 + 7 * NCROSS;
+    int* sRow = reinterpret_cast<int*>(sF + 8 * NFACE);
+    fill_rows(sRow);
+    const long long stride = gridDim.x;
+    long long t = next_active(P, (long long)blockIdx.x, stride);
+    TileCtx<T> c;
+    if (t < P.total_blocks) {
+        tile_ctx(P, t, parity, c);
+        tile_issue<T, STAGE>(P, c, sW0);
+    }
+    cp_async_commit();
+    int i = 0;
+    while (t < P.total_blocks) {
+        const long long tn = next_active(P, t + stride, stride);
+        TileCtx<T> cn;
+        T* cur = (i & 1) ? sW1 : sW0;
+        T* nxt = (i & 1) ? sW0 : sW1;
+        if (tn < P.total_blocks) {
+            tile_ctx(P, tn, parity, cn);
+            tile_issue<T, STAGE>(P, cn, nxt);
+        }
+        cp_async_commit();
+        cp_async_wait_one();   // everything but the copies just issued has landed
+        __syncthreads();
+        tile_convert(P.eos, cur);
+        __syncthreads();
+        tile_body<T, STAGE>(P, c, cur, sF, sRow);
+        __syncthreads();
+        t = tn;
+        c = cn;
+        ++i;
+    }
+    cp_async_wait_all();
 }
 
 // Pressure at one cell of a stored state (sensor evaluation).
@@ -950,19 +1057,40 @@ __global__ void __launch_bounds__(256) totals_kernel(const __grid_constant__ Par
 template <typename T>
 int set_smem_attrs() {
     const int bytes = (int)smem_bytes(sizeof(T));
+    const int bytes_pp = (int)smem_bytes_pp(sizeof(T));
     CUDA_TRY(cudaFuncSetAttribute(stage_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     CUDA_TRY(cudaFuncSetAttribute(stage_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     CUDA_TRY(cudaFuncSetAttribute(stage_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_pp<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_pp));
+    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_pp<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_pp));
+    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_pp<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_pp));
     return OFM_OK;
 }
 
+// Grid of the persistent variant: resident blocks per SM times the SM count,
+// never more than the number of tiles.
 template <typename T>
-int launch_step(const Params<T>& P, int parity, cudaStream_t st, long long* launches) {
-    const size_t sm = smem_bytes(sizeof(T));
-    const dim3 grid((unsigned)P.total_blocks);
-    stage_kernel<T, 0><<<grid, NT, sm, st>>>(P, parity);
-    stage_kernel<T, 1><<<grid, NT, sm, st>>>(P, 1 - parity);
-    stage_kernel<T, 2><<<grid, NT, sm, st>>>(P, parity);
+unsigned pp_grid(const Params<T>& P) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (long long)sms * (sizeof(T) == 4 ? 2 : 1);
+    return (unsigned)(P.total_blocks < want ? P.total_blocks : want);
+}
+
+template <typename T, int STAGE>
+void launch_one_stage(const Params<T>& P, int variant, int parity, cudaStream_t st) {
+    if (variant == OFM_VARIANT_PERSISTENT)
+        stage_kernel_pp<T, STAGE><<<pp_grid(P), NT, smem_bytes_pp(sizeof(T)), st>>>(P, parity);
+    else
+        stage_kernel<T, STAGE><<<(unsigned)P.total_blocks, NT, smem_bytes(sizeof(T)), st>>>(P, parity);
+}
+
+template <typename T>
+int launch_step(const Params<T>& P, int variant, int parity, cudaStream_t st, long long* launches) {
+    launch_one_stage<T, 0>(P, variant, parity, st);
+    launch_one_stage<T, 1>(P, variant, 1 - parity, st);
+    launch_one_stage<T, 2>(P, variant, parity, st);
     finalize_kernel<T><<<P.total_slots, 256, 0, st>>>(P, 0, 1 - parity);
     *launches += 4;
     CUDA_TRY(cudaGetLastError());
@@ -970,15 +1098,13 @@ int launch_step(const Params<T>& P, int parity, cudaStream_t st, long long* laun
 }
 
 template <typename T>
-int launch_stage(const Params<T>& P, int stage, int parity, cudaStream_t st, long long* launches) {
-    const size_t sm = smem_bytes(sizeof(T));
-    const dim3 grid((unsigned)P.total_blocks);
+int launch_stage(const Params<T>& P, int variant, int stage, int parity, cudaStream_t st, long long* launches) {
     if (stage == 0)
-        stage_kernel<T, 0><<<grid, NT, sm, st>>>(P, parity);
+        launch_one_stage<T, 0>(P, variant, parity, st);
     else if (stage == 1)
-        stage_kernel<T, 1><<<grid, NT, sm, st>>>(P, parity);
+        launch_one_stage<T, 1>(P, variant, parity, st);
     else if (stage == 2)
-        stage_kernel<T, 2><<<grid, NT, sm, st>>>(P, parity);
+        launch_one_stage<T, 2>(P, variant, parity, st);
     else
         finalize_kernel<T><<<P.total_slots, 256, 0, st>>>(P, 0, parity);
     *launches += 1;

@@ -91,6 +91,8 @@ struct ofm_batch {
     cudaGraphExec_t chunk;
     bool chunk_ready;
     bool initialised;
+    int variant;              // stage-kernel variant; -1 = pick by timing at the first run
+    float tune_ms[2];         // autotuning times of the two variants (two steps each)
     bool profiling;           // steps without graphs, CUDA events around each stage kernel
     cudaEvent_t pev[4];
     double stage_ms;
@@ -198,7 +200,7 @@ int build_chunk(ofm_batch* b, const Params<T>& P) {
     CUDA_TRY(cudaStreamBeginCapture(b->priv, cudaStreamCaptureModeThreadLocal));
     const long long saved = b->launches;
     for (int k = 0; k < CHUNK_STEPS; ++k) {
-        int rc = launch_step(P, k & 1, b->priv, &b->launches);
+        int rc = launch_step(P, b->variant < 0 ? OFM_VARIANT_TILES : b->variant, k & 1, b->priv, &b->launches);
         if (rc != OFM_OK) {
             cudaStreamEndCapture(b->priv, &graph);
             return rc;
@@ -347,6 +349,8 @@ extern "C" int ofm_batch_create(ofm_batch** out, ofm_solver* s, const ofm_cloud_
     b->chunk_ready = false;
     b->initialised = false;
     b->profiling = false;
+    b->variant = -1;
+    b->tune_ms[0] = b->tune_ms[1] = 0.f;
     for (int k = 0; k < 4; ++k) b->pev[k] = nullptr;
     b->stage_ms = 0.0;
     b->stage_launches = 0;
@@ -455,18 +459,42 @@ extern "C" int ofm_batch_run(ofm_batch* b, int max_steps, int* n_active) {
     if (rc != OFM_OK) return rc;
     int done_steps = 0;
     int active = 1;
+    if (b->variant < 0 && !b->profiling && max_steps >= 4 && (b->global_steps & 1) == 0) {
+        // autotune: the two stage-kernel variants give identical results; time
+        // two steps of each (alternating) and keep the faster
+        float t[2] = {0.f, 0.f};
+        for (int k = 0; k < 4; ++k) {
+            const int var = k & 1;
+            CUDA_TRY(cudaEventRecord(b->pev[0], b->priv));
+            rc = b->precision == OFM_FP64 ? launch_step(b->pd, var, (int)(b->global_steps & 1), b->priv, &b->launches)
+                                          : launch_step(b->pf, var, (int)(b->global_steps & 1), b->priv, &b->launches);
+            if (rc != OFM_OK) return rc;
+            CUDA_TRY(cudaEventRecord(b->pev[1], b->priv));
+            CUDA_TRY(cudaEventSynchronize(b->pev[1]));
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, b->pev[0], b->pev[1]));
+            t[var] += ms;
+            b->global_steps += 1;
+            done_steps += 1;
+        }
+        b->variant = t[1] < t[0] ? OFM_VARIANT_PERSISTENT : OFM_VARIANT_TILES;
+        b->tune_ms[0] = t[0];
+        b->tune_ms[1] = t[1];
+    }
+    const int variant = b->variant < 0 ? OFM_VARIANT_TILES : b->variant;
     while (done_steps < max_steps) {
         if (b->profiling) {
             const int parity = (int)(b->global_steps & 1);
             for (int k = 0; k < 4; ++k) {
                 CUDA_TRY(cudaEventRecord(b->pev[k], b->priv));
                 if (k == 3) break;
-                rc = b->precision == OFM_FP64 ? launch_stage(b->pd, k, k == 1 ? 1 - parity : parity, b->priv, &b->launches)
-                                              : launch_stage(b->pf, k, k == 1 ? 1 - parity : parity, b->priv, &b->launches);
+                rc = b->precision == OFM_FP64
+                         ? launch_stage(b->pd, variant, k, k == 1 ? 1 - parity : parity, b->priv, &b->launches)
+                         : launch_stage(b->pf, variant, k, k == 1 ? 1 - parity : parity, b->priv, &b->launches);
                 if (rc != OFM_OK) return rc;
             }
-            rc = b->precision == OFM_FP64 ? launch_stage(b->pd, 3, 1 - parity, b->priv, &b->launches)
-                                          : launch_stage(b->pf, 3, 1 - parity, b->priv, &b->launches);
+            rc = b->precision == OFM_FP64 ? launch_stage(b->pd, variant, 3, 1 - parity, b->priv, &b->launches)
+                                          : launch_stage(b->pf, variant, 3, 1 - parity, b->priv, &b->launches);
             if (rc != OFM_OK) return rc;
             CUDA_TRY(cudaEventSynchronize(b->pev[3]));
             for (int k = 0; k < 3; ++k) {
@@ -488,8 +516,8 @@ extern "C" int ofm_batch_run(ofm_batch* b, int max_steps, int* n_active) {
             done_steps += CHUNK_STEPS;
         } else {
             const int parity = (int)(b->global_steps & 1);
-            rc = b->precision == OFM_FP64 ? launch_step(b->pd, parity, b->priv, &b->launches)
-                                          : launch_step(b->pf, parity, b->priv, &b->launches);
+            rc = b->precision == OFM_FP64 ? launch_step(b->pd, variant, parity, b->priv, &b->launches)
+                                          : launch_step(b->pf, variant, parity, b->priv, &b->launches);
             if (rc != OFM_OK) return rc;
             b->global_steps += 1;
             done_steps += 1;
@@ -649,6 +677,28 @@ extern "C" int ofm_batch_set_profiling(ofm_batch* b, int on) {
     ofm::clear_error();
     if (!b) return fail(OFM_EINVAL, "NULL batch");
     b->profiling = on != 0;
+    return OFM_OK;
+}
+
+extern "C" int ofm_batch_set_variant(ofm_batch* b, int variant) {
+    ofm::clear_error();
+    if (!b || variant < -1 || variant > OFM_VARIANT_PERSISTENT) return fail(OFM_EINVAL, "bad batch or variant");
+    if (variant != b->variant && b->chunk_ready) {
+        cudaGraphExecDestroy(b->chunk);
+        b->chunk_ready = false;
+    }
+    b->variant = variant;
+    return OFM_OK;
+}
+
+extern "C" int ofm_batch_get_variant(ofm_batch* b, int* variant, float* tune_ms) {
+    ofm::clear_error();
+    if (!b || !variant) return fail(OFM_EINVAL, "NULL argument");
+    *variant = b->variant;
+    if (tune_ms) {
+        tune_ms[0] = b->tune_ms[0];
+        tune_ms[1] = b->tune_ms[1];
+    }
     return OFM_OK;
 }
 

@@ -178,7 +178,7 @@ int run_static(const ofm_solver* s, int N, int M, int nb, unsigned char* ws, con
     long long step = 0;
     for (;;) {
         for (int k = 0; k < CHUNK_STEPS; ++k, ++step) {
-            rc = launch_step(P, (int)(step & 1), st, &launches);
+            rc = launch_step(P, OFM_VARIANT_TILES, (int)(step & 1), st, &launches);
             if (rc != OFM_OK) return rc;
         }
         int active = 0;  // pageable host int: no pinned allocation

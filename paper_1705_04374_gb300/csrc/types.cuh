@@ -19,11 +19,10 @@ constexpr int NCELL = TS * TS * TS;      // 512 cells per tile
 constexpr int NSLAB = HALO * TS * TS;    // 192 cells per halo slab
 constexpr int NCROSS = NCELL + 6 * NSLAB;  // 1664 staged cells
 constexpr int NFACE = (TS + 1) * TS * TS;  // 576 faces per direction
-constexpr int NT = 192;                  // threads per block: 3 faces each per direction
-constexpr int CELLS_PER_THREAD = (NCELL + NT - 1) / NT;  // 3
+constexpr int NT = 256;                  // threads per block (measured better than 192 and 256x2)
+constexpr int CELLS_PER_THREAD = (NCELL + NT - 1) / NT;  // 2
 constexpr int CHUNK_STEPS = 8;           // steps per captured graph (even)
 
-static_assert(NFACE % NT == 0, "each thread computes the same number of faces");
 
 template <typename T>
 struct Eos {
@@ -99,6 +98,13 @@ constexpr double RK_B[3] = {0.924574, 0.287713063186749, 0.626538109512740};
 // Stage-kernel dynamic shared memory: primitives of the staged cells, face
 // fluxes of one direction, and the staging layout's row-offset table.
 constexpr size_t smem_bytes(size_t elem) { return elem * (7 * NCROSS + 8 * NFACE) + sizeof(int) * BX * BX; }
+// The persistent variant double-buffers the staged primitives.
+constexpr size_t smem_bytes_pp(size_t elem) { return elem * (14 * NCROSS + 8 * NFACE) + sizeof(int) * BX * BX; }
+
+// Stage-kernel variants: one block per tile, or persistent blocks that copy
+// the next tile while computing the current one.
+constexpr int OFM_VARIANT_TILES = 0;
+constexpr int OFM_VARIANT_PERSISTENT = 1;
 
 // Launch wrappers, instantiated for double in kernels_fp64.cu (compiled
 // without FMA contraction, in the oracle's operation order) and for float in
@@ -106,12 +112,12 @@ constexpr size_t smem_bytes(size_t elem) { return elem * (7 * NCROSS + 8 * NFACE
 template <typename T>
 int set_smem_attrs();
 template <typename T>
-int launch_step(const Params<T>& P, int parity, cudaStream_t st, long long* launches);
+int launch_step(const Params<T>& P, int variant, int parity, cudaStream_t st, long long* launches);
 template <typename T>
 int launch_init(const Params<T>& P, cudaStream_t st, bool fill_ic, long long* launches);
 // stage 0..2: one RK stage kernel; stage 3: the step's finalize kernel.
 template <typename T>
-int launch_stage(const Params<T>& P, int stage, int parity, cudaStream_t st, long long* launches);
+int launch_stage(const Params<T>& P, int variant, int stage, int parity, cudaStream_t st, long long* launches);
 template <typename T>
 int launch_totals(const Params<T>& P, cudaStream_t st, int which, long long* launches);
 

@@ -96,6 +96,8 @@ SIGNATURES = {
     "ofm_batch_cell_steps": (C.c_int, [_vp, _P(C.c_double)]),
     "ofm_batch_kernel_launches": (C.c_int, [_vp, _P(C.c_int64)]),
     "ofm_batch_set_profiling": (C.c_int, [_vp, C.c_int]),
+    "ofm_batch_set_variant": (C.c_int, [_vp, C.c_int]),
+    "ofm_batch_get_variant": (C.c_int, [_vp, _P(C.c_int), _P(C.c_float)]),
     "ofm_batch_stage_time": (C.c_int, [_vp, _P(C.c_double), _P(C.c_int64)]),
     "ofm_batch_transfer_bytes": (C.c_int, [_vp, _P(C.c_int64), _P(C.c_int64)]),
     "ofm_batch_destroy": (None, [_vp]),
