@@ -1,7 +1,7 @@
 """A small, fixed solver workload for profiler captures.
 
     python -m paper_1705_04374_gb300.profile_case [--samples 64] [--steps 2]
-                                                   [--precision fp32|fp64] [--N 64]
+                                                   [--precision fp32|fp64] [--N 64] [--variant 0|1]
 
 Runs the ensemble workload's clouds (20 bubbles) on a reduced number of
 samples: initial condition, then `steps` RK3 steps in profiling mode (one
@@ -31,6 +31,7 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--N", type=int, default=64)
+    ap.add_argument("--variant", type=int, default=0, help="0: one block per tile, 1: persistent")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     w = W.cfg2(a.precision)
@@ -38,11 +39,12 @@ def main() -> None:
     g = api.make_group(w.solver, a.N, list(range(a.samples)), W.BASE_SEED)
     b = api.Batch(s, w.cloud, [g])
     b.init()
+    b.set_variant(a.variant)
     b.set_profiling(True)
     b.run(a.steps)
     torch.cuda.synchronize()
     ms, n = b.stage_time()
-    print(f"profile_case: {a.samples} x {a.N}^3 {a.precision}, {a.steps} steps, "
+    print(f"profile_case: {a.samples} x {a.N}^3 {a.precision}, variant {a.variant}, {a.steps} steps, "
           f"stage kernel avg {ms / max(n, 1):.3f} ms over {n} launches")
     b.close()
 
