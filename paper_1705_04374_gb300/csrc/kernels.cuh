@@ -683,8 +683,9 @@ __device__ __forceinline__ void tile_convert(const Eos<T>& e, T* sW) {
 // 2N update and, in the last stage, the new state's per-tile reductions, for
 // one tile whose primitives are staged in sW.
 template <typename T, int STAGE>
-__device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& c, const T* __restrict__ sW,
-                                          T* __restrict__ sF, const int* __restrict__ sRow) {
+__device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& c, long long tile_index,
+                                          const T* __restrict__ sW, T* __restrict__ sF,
+                                          const int* __restrict__ sRow) {
     const BlockWork<T>& bw = c.bw;
     const GroupDev& G = *bw.G;
     const int N = G.N;
@@ -798,7 +799,7 @@ __device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& 
         }
     }
     if (STAGE == 2) {
-        const long long tile = blockIdx.x - G.block0 - (long long)bw.s_local * G.tps;
+        const long long tile = tile_index - G.block0 - (long long)bw.s_local * G.tps;
         block_reduce_write(red, G.part + (size_t)bw.s_local * G.tps + tile);
     }
 }
@@ -820,7 +821,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
     __syncthreads();
     tile_convert(P.eos, sW);
     __syncthreads();
-    tile_body<T, STAGE>(P, c, sW, sF, sRow);
+    tile_body<T, STAGE>(P, c, (long long)blockIdx.x, sW, sF, sRow);
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -876,7 +877,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
         __syncthreads();
         tile_convert(P.eos, cur);
         __syncthreads();
-        tile_body<T, STAGE>(P, c, cur, sF, sRow);
+        tile_body<T, STAGE>(P, c, t, cur, sF, sRow);
         __syncthreads();
         t = tn;
         c = cn;
