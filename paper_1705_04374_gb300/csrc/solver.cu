@@ -349,7 +349,7 @@ extern "C" int ofm_batch_create(ofm_batch** out, ofm_solver* s, const ofm_cloud_
     b->chunk_ready = false;
     b->initialised = false;
     b->profiling = false;
-    b->variant = -1;
+    b->variant = OFM_VARIANT_TILES;
     b->tune_ms[0] = b->tune_ms[1] = 0.f;
     for (int k = 0; k < 4; ++k) b->pev[k] = nullptr;
     b->stage_ms = 0.0;
