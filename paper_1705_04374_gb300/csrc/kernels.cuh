@@ -363,7 +363,10 @@ __device__ void block_reduce_write(Red r, Partial* out) {
 template <typename T>
 __global__ void reset_kernel(const __grid_constant__ Params<T> P) {
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot == 0) *P.s.n_active = P.total_slots;
+    if (slot == 0) {
+        *P.s.n_active = P.total_slots;
+        for (int g = 0; g < P.n_groups; ++g) P.s.g_active[g] = P.g[g].n_samples;
+    }
     if (slot >= P.total_slots) return;
     P.s.t[slot] = 0.0;
     P.s.dt[slot] = 0.0;
@@ -1005,6 +1008,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ P
         q.t_final = t;
         q.n_steps = nsteps;
         atomicSub(P.s.n_active, 1);
+        atomicSub(P.s.g_active + gi, 1);
     }
 }
 
@@ -1081,6 +1085,7 @@ unsigned pp_grid(const Params<T>& P) {
 
 template <typename T, int STAGE>
 void launch_one_stage(const Params<T>& P, int variant, int parity, cudaStream_t st) {
+    if (P.total_blocks <= 0) return;  // every group finished
     if (variant == OFM_VARIANT_PERSISTENT)
         stage_kernel_pp<T, STAGE><<<pp_grid(P), NT, smem_bytes_pp(sizeof(T)), st>>>(P, parity);
     else
@@ -1088,26 +1093,28 @@ void launch_one_stage(const Params<T>& P, int variant, int parity, cudaStream_t 
 }
 
 template <typename T>
-int launch_step(const Params<T>& P, int variant, int parity, cudaStream_t st, long long* launches) {
-    launch_one_stage<T, 0>(P, variant, parity, st);
-    launch_one_stage<T, 1>(P, variant, 1 - parity, st);
-    launch_one_stage<T, 2>(P, variant, parity, st);
-    finalize_kernel<T><<<P.total_slots, 256, 0, st>>>(P, 0, 1 - parity);
+int launch_step(const Params<T>& Ps, const Params<T>& Pf, int variant, int parity, cudaStream_t st,
+                long long* launches) {
+    launch_one_stage<T, 0>(Ps, variant, parity, st);
+    launch_one_stage<T, 1>(Ps, variant, 1 - parity, st);
+    launch_one_stage<T, 2>(Ps, variant, parity, st);
+    finalize_kernel<T><<<Pf.total_slots, 256, 0, st>>>(Pf, 0, 1 - parity);
     *launches += 4;
     CUDA_TRY(cudaGetLastError());
     return OFM_OK;
 }
 
 template <typename T>
-int launch_stage(const Params<T>& P, int variant, int stage, int parity, cudaStream_t st, long long* launches) {
+int launch_stage(const Params<T>& Ps, const Params<T>& Pf, int variant, int stage, int parity, cudaStream_t st,
+                 long long* launches) {
     if (stage == 0)
-        launch_one_stage<T, 0>(P, variant, parity, st);
+        launch_one_stage<T, 0>(Ps, variant, parity, st);
     else if (stage == 1)
-        launch_one_stage<T, 1>(P, variant, parity, st);
+        launch_one_stage<T, 1>(Ps, variant, parity, st);
     else if (stage == 2)
-        launch_one_stage<T, 2>(P, variant, parity, st);
+        launch_one_stage<T, 2>(Ps, variant, parity, st);
     else
-        finalize_kernel<T><<<P.total_slots, 256, 0, st>>>(P, 0, parity);
+        finalize_kernel<T><<<Pf.total_slots, 256, 0, st>>>(Pf, 0, parity);
     *launches += 1;
     CUDA_TRY(cudaGetLastError());
     return OFM_OK;

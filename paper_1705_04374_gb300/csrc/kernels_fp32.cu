@@ -5,9 +5,9 @@
 namespace ofm {
 namespace gpu {
 template int set_smem_attrs<float>();
-template int launch_step<float>(const Params<float>&, int, int, cudaStream_t, long long*);
+template int launch_step<float>(const Params<float>&, const Params<float>&, int, int, cudaStream_t, long long*);
 template int launch_init<float>(const Params<float>&, cudaStream_t, bool, long long*);
-template int launch_stage<float>(const Params<float>&, int, int, int, cudaStream_t, long long*);
+template int launch_stage<float>(const Params<float>&, const Params<float>&, int, int, int, cudaStream_t, long long*);
 template int launch_totals<float>(const Params<float>&, cudaStream_t, int, long long*);
 }  // namespace gpu
 }  // namespace ofm

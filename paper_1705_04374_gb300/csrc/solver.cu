@@ -98,8 +98,11 @@ struct ofm_batch {
     double stage_ms;
     long long stage_launches;
     long long h2d_bytes, d2h_bytes;
-    Params<double> pd;
+    Params<double> pd;        // full group table
     Params<float> pf;
+    Params<double> pd_s;      // table the stage kernels walk: groups with unfinished samples
+    Params<float> pf_s;
+    unsigned active_mask;     // groups in the stage table
     size_t off_t, off_dt, off_last, off_done, off_nsteps, off_kout, off_qoi, off_sold, off_hist,
         off_active, off_bub;
 };
@@ -165,6 +168,7 @@ void fill_params(ofm_batch* b, Params<T>& P) {
     P.s.sens_old = (double*)(b->ws + b->off_sold);
     P.s.hist = (double*)(b->ws + b->off_hist);
     P.s.n_active = (int*)(b->ws + b->off_active);
+    P.s.g_active = (int*)(b->ws + b->off_active + 16);
     P.s.bubbles = (const double*)(b->ws + b->off_bub);
     const double g1 = c.gamma[0], g2 = c.gamma[1];
     const double pc1 = c.pc[0] / pref, pc2 = c.pc[1] / pref;
@@ -194,13 +198,42 @@ void fill_params(ofm_batch* b, Params<T>& P) {
     P.rho2 = c.rho0[1] / 1000.0;
 }
 
+// Stage-kernel table with only the groups in `mask`: same pointers and sample
+// slots, tile ranges (block0) re-packed so finished groups launch no blocks.
 template <typename T>
-int build_chunk(ofm_batch* b, const Params<T>& P) {
+void stage_table(const Params<T>& full, unsigned mask, Params<T>& out) {
+    out = full;
+    int n = 0;
+    long long blk = 0;
+    for (int g = 0; g < full.n_groups; ++g) {
+        if (!(mask & (1u << g))) continue;
+        out.g[n] = full.g[g];
+        out.g[n].block0 = blk;
+        blk += (long long)full.g[g].tps * full.g[g].n_samples;
+        ++n;
+    }
+    out.n_groups = n;
+    out.total_blocks = blk;
+}
+
+void set_active_mask(ofm_batch* b, unsigned mask) {
+    if (mask == b->active_mask) return;
+    b->active_mask = mask;
+    stage_table(b->pd, mask, b->pd_s);
+    stage_table(b->pf, mask, b->pf_s);
+    if (b->chunk_ready) {
+        cudaGraphExecDestroy(b->chunk);
+        b->chunk_ready = false;
+    }
+}
+
+template <typename T>
+int build_chunk(ofm_batch* b, const Params<T>& Ps, const Params<T>& P) {
     cudaGraph_t graph;
     CUDA_TRY(cudaStreamBeginCapture(b->priv, cudaStreamCaptureModeThreadLocal));
     const long long saved = b->launches;
     for (int k = 0; k < CHUNK_STEPS; ++k) {
-        int rc = launch_step(P, b->variant < 0 ? OFM_VARIANT_TILES : b->variant, k & 1, b->priv, &b->launches);
+        int rc = launch_step(Ps, P, b->variant < 0 ? OFM_VARIANT_TILES : b->variant, k & 1, b->priv, &b->launches);
         if (rc != OFM_OK) {
             cudaStreamEndCapture(b->priv, &graph);
             return rc;
@@ -306,7 +339,7 @@ static void layout(const ofm_solver* s, const ofm_cloud_params* cloud, const ofm
     b->off_qoi = Lo.take(S * sizeof(DevQoi));
     b->off_sold = Lo.take(S * OFM_MAX_SENSORS * 8);
     b->off_hist = Lo.take(std::max<size_t>(1, S * s->cfg.n_sensors * s->cfg.n_out_times) * 8);
-    b->off_active = Lo.take(16);
+    b->off_active = Lo.take(16 + sizeof(int) * OFM_MAX_GROUPS);
     b->off_bub = Lo.take(std::max<size_t>(1, S * cloud->n_bubbles * 4) * 8);
 }
 
@@ -385,14 +418,17 @@ extern "C" int ofm_batch_create(ofm_batch** out, ofm_solver* s, const ofm_cloud_
     }
     if (cudaStreamCreateWithFlags(&b->priv, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost((void**)&b->h_active, sizeof(int)) != cudaSuccess)
+        cudaMallocHost((void**)&b->h_active, 16 + sizeof(int) * OFM_MAX_GROUPS) != cudaSuccess)
         return bail(fail(OFM_ECUDA, "stream / event / pinned allocation failed"));
+    b->active_mask = 0;
     if (b->precision == OFM_FP64) {
         fill_params(b, b->pd);
+        b->pd_s = b->pd;
         b->total_blocks = b->pd.total_blocks;
         if ((rc = set_smem_attrs<double>()) != OFM_OK) return bail(rc);
     } else {
         fill_params(b, b->pf);
+        b->pf_s = b->pf;
         b->total_blocks = b->pf.total_blocks;
         if ((rc = set_smem_attrs<float>()) != OFM_OK) return bail(rc);
     }
@@ -446,6 +482,8 @@ extern "C" int ofm_batch_init(ofm_batch* b) {
     if (rc != OFM_OK) return rc;
     rc = b->precision == OFM_FP64 ? launch_init(b->pd, b->priv, true, &b->launches) : launch_init(b->pf, b->priv, true, &b->launches);
     if (rc != OFM_OK) return rc;
+    b->active_mask = 0;
+    set_active_mask(b, (1u << b->n_groups) - 1u);
     b->global_steps = 0;
     b->initialised = true;
     return leave(b);
@@ -466,8 +504,9 @@ extern "C" int ofm_batch_run(ofm_batch* b, int max_steps, int* n_active) {
         for (int k = 0; k < 4; ++k) {
             const int var = k & 1;
             CUDA_TRY(cudaEventRecord(b->pev[0], b->priv));
-            rc = b->precision == OFM_FP64 ? launch_step(b->pd, var, (int)(b->global_steps & 1), b->priv, &b->launches)
-                                          : launch_step(b->pf, var, (int)(b->global_steps & 1), b->priv, &b->launches);
+            rc = b->precision == OFM_FP64
+                     ? launch_step(b->pd_s, b->pd, var, (int)(b->global_steps & 1), b->priv, &b->launches)
+                     : launch_step(b->pf_s, b->pf, var, (int)(b->global_steps & 1), b->priv, &b->launches);
             if (rc != OFM_OK) return rc;
             CUDA_TRY(cudaEventRecord(b->pev[1], b->priv));
             CUDA_TRY(cudaEventSynchronize(b->pev[1]));
@@ -489,12 +528,12 @@ extern "C" int ofm_batch_run(ofm_batch* b, int max_steps, int* n_active) {
                 CUDA_TRY(cudaEventRecord(b->pev[k], b->priv));
                 if (k == 3) break;
                 rc = b->precision == OFM_FP64
-                         ? launch_stage(b->pd, variant, k, k == 1 ? 1 - parity : parity, b->priv, &b->launches)
-                         : launch_stage(b->pf, variant, k, k == 1 ? 1 - parity : parity, b->priv, &b->launches);
+                         ? launch_stage(b->pd_s, b->pd, variant, k, k == 1 ? 1 - parity : parity, b->priv, &b->launches)
+                         : launch_stage(b->pf_s, b->pf, variant, k, k == 1 ? 1 - parity : parity, b->priv, &b->launches);
                 if (rc != OFM_OK) return rc;
             }
-            rc = b->precision == OFM_FP64 ? launch_stage(b->pd, variant, 3, 1 - parity, b->priv, &b->launches)
-                                          : launch_stage(b->pf, variant, 3, 1 - parity, b->priv, &b->launches);
+            rc = b->precision == OFM_FP64 ? launch_stage(b->pd_s, b->pd, variant, 3, 1 - parity, b->priv, &b->launches)
+                                          : launch_stage(b->pf_s, b->pf, variant, 3, 1 - parity, b->priv, &b->launches);
             if (rc != OFM_OK) return rc;
             CUDA_TRY(cudaEventSynchronize(b->pev[3]));
             for (int k = 0; k < 3; ++k) {
@@ -507,7 +546,7 @@ extern "C" int ofm_batch_run(ofm_batch* b, int max_steps, int* n_active) {
             done_steps += 1;
         } else if ((b->global_steps & 1) == 0 && max_steps - done_steps >= CHUNK_STEPS) {
             if (!b->chunk_ready) {
-                rc = b->precision == OFM_FP64 ? build_chunk(b, b->pd) : build_chunk(b, b->pf);
+                rc = b->precision == OFM_FP64 ? build_chunk(b, b->pd_s, b->pd) : build_chunk(b, b->pf_s, b->pf);
                 if (rc != OFM_OK) return rc;
             }
             CUDA_TRY(cudaGraphLaunch(b->chunk, b->priv));
@@ -516,18 +555,22 @@ extern "C" int ofm_batch_run(ofm_batch* b, int max_steps, int* n_active) {
             done_steps += CHUNK_STEPS;
         } else {
             const int parity = (int)(b->global_steps & 1);
-            rc = b->precision == OFM_FP64 ? launch_step(b->pd, variant, parity, b->priv, &b->launches)
-                                          : launch_step(b->pf, variant, parity, b->priv, &b->launches);
+            rc = b->precision == OFM_FP64 ? launch_step(b->pd_s, b->pd, variant, parity, b->priv, &b->launches)
+                                          : launch_step(b->pf_s, b->pf, variant, parity, b->priv, &b->launches);
             if (rc != OFM_OK) return rc;
             b->global_steps += 1;
             done_steps += 1;
         }
-        const size_t off = b->off_active;
-        CUDA_TRY(cudaMemcpyAsync(b->h_active, b->ws + off, sizeof(int), cudaMemcpyDeviceToHost, b->priv));
-        b->d2h_bytes += (long long)sizeof(int);
+        const size_t cnt_bytes = 16 + sizeof(int) * b->n_groups;
+        CUDA_TRY(cudaMemcpyAsync(b->h_active, b->ws + b->off_active, cnt_bytes, cudaMemcpyDeviceToHost, b->priv));
+        b->d2h_bytes += (long long)cnt_bytes;
         CUDA_TRY(cudaStreamSynchronize(b->priv));
         active = *b->h_active;
         if (active == 0) break;
+        unsigned mask = 0;
+        for (int g = 0; g < b->n_groups; ++g)
+            if (b->h_active[4 + g] > 0) mask |= 1u << g;
+        set_active_mask(b, mask);
     }
     if (n_active) *n_active = active;
     return leave(b);

@@ -63,7 +63,7 @@ int scratch_address(unsigned char** out) {
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct StaticLayout {
-    size_t QA, QB, dQ, part, sens, t, dt, last, done, nsteps, kout, qoi, sold, hist, active, bub, total;
+    size_t QA, QB, dQ, part, sens, t, dt, last, done, nsteps, kout, qoi, sold, hist, active, gact, bub, total;
 };
 
 StaticLayout static_layout(const ofm_solver* s, int N, int M, int nb, size_t n_sens_cells) {
@@ -91,6 +91,7 @@ StaticLayout static_layout(const ofm_solver* s, int N, int M, int nb, size_t n_s
     L.sold = take(Ms * OFM_MAX_SENSORS * 8);
     L.hist = take((Ms * s->cfg.n_sensors * s->cfg.n_out_times ? Ms * s->cfg.n_sensors * s->cfg.n_out_times : 1) * 8);
     L.active = take(16);
+    L.gact = take(16);
     L.bub = take((Ms * nb ? Ms * nb : 1) * 32);
     L.total = at;
     return L;
@@ -129,6 +130,7 @@ void static_params(const ofm_solver* s, int N, int M, int nb, unsigned char* ws,
     P.s.sens_old = (double*)(ws + L.sold);
     P.s.hist = (double*)(ws + L.hist);
     P.s.n_active = (int*)(ws + L.active);
+    P.s.g_active = (int*)(ws + L.gact);
     P.s.bubbles = (const double*)(ws + L.bub);
     const double g1 = c.gamma[0], g2 = c.gamma[1];
     const double pc1 = c.pc[0] / pref, pc2 = c.pc[1] / pref;
@@ -178,7 +180,7 @@ int run_static(const ofm_solver* s, int N, int M, int nb, unsigned char* ws, con
     long long step = 0;
     for (;;) {
         for (int k = 0; k < CHUNK_STEPS; ++k, ++step) {
-            rc = launch_step(P, OFM_VARIANT_TILES, (int)(step & 1), st, &launches);
+            rc = launch_step(P, P, OFM_VARIANT_TILES, (int)(step & 1), st, &launches);
             if (rc != OFM_OK) return rc;
         }
         int active = 0;  // pageable host int: no pinned allocation

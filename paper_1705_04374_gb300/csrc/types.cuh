@@ -75,6 +75,7 @@ struct SampleDev {
     double* sens_old;     // [slot][OFM_MAX_SENSORS]
     double* hist;         // [slot][n_sens][n_out]
     int* n_active;
+    int* g_active;          // [group] samples not yet finished
     const double* bubbles;  // [slot][nb][4], non-dimensional
 };
 
@@ -111,13 +112,17 @@ constexpr int OFM_VARIANT_PERSISTENT = 1;
 // kernels_fp32.cu.  Each returns OFM_OK or OFM_ECUDA and counts its launches.
 template <typename T>
 int set_smem_attrs();
+// Ps: the table the stage kernels walk (finished groups may be left out);
+// Pf: the full table (finalize and reductions index samples by slot).
 template <typename T>
-int launch_step(const Params<T>& P, int variant, int parity, cudaStream_t st, long long* launches);
+int launch_step(const Params<T>& Ps, const Params<T>& Pf, int variant, int parity, cudaStream_t st,
+                long long* launches);
 template <typename T>
 int launch_init(const Params<T>& P, cudaStream_t st, bool fill_ic, long long* launches);
 // stage 0..2: one RK stage kernel; stage 3: the step's finalize kernel.
 template <typename T>
-int launch_stage(const Params<T>& P, int variant, int stage, int parity, cudaStream_t st, long long* launches);
+int launch_stage(const Params<T>& Ps, const Params<T>& Pf, int variant, int stage, int parity, cudaStream_t st,
+                 long long* launches);
 template <typename T>
 int launch_totals(const Params<T>& P, cudaStream_t st, int which, long long* launches);
 
