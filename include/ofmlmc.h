@@ -374,8 +374,9 @@ int ofm_mlp_train(ofm_mlp* mlp, const float* X, const float* T, int n, int steps
 /* Column mean and standard deviation (M-1) of a device matrix, into device
  * FP64 arrays, fixed summation order. */
 int ofm_column_moments(const float* X, int rows, int cols, double* mean_dev, double* std_dev, void* stream);
-/* Surrogate inputs: per cloud, its bubbles sorted by the distance of the
- * centre from the domain centre (ties by index), each as
+/* Surrogate inputs: per cloud, its bubbles ordered by the gap between the
+ * bubble's surface and the domain centre, |x_b - L/2| - r_b (ties by index),
+ * each as
  * ((x - L/2)/scale, (y - L/2)/scale, (z - L/2)/scale, r/scale).
  * bubbles_dev: device [n_clouds][n_bubbles][4] doubles (metres);
  * X_dev: device [n_clouds][4 n_bubbles] floats. */

@@ -132,12 +132,13 @@ def unflatten(vec: np.ndarray, sizes) -> list:
 
 
 def cloud_features(bubbles: np.ndarray, domain_L: float, scale: float) -> np.ndarray:
-    """Bubbles (nb, 4) in metres -> features sorted by distance of the centre
-    from the domain centre (ties by index): ((x-c)/s, (y-c)/s, (z-c)/s, r/s)."""
+    """Bubbles (nb, 4) in metres -> features ordered by the gap between each
+    bubble's surface and the domain centre, |x_b - c| - r_b (ties by index):
+    ((x-c)/s, (y-c)/s, (z-c)/s, r/s)."""
     c = 0.5 * domain_L
     inv = 1.0 / scale
     d = bubbles[:, :3] - c
-    key = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]
+    key = np.sqrt(d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]) - bubbles[:, 3]
     order = np.lexsort((np.arange(len(key)), key))
     f = np.empty((len(key), 4))
     f[:, :3] = (bubbles[order, :3] - c) * inv

@@ -239,9 +239,9 @@ __global__ void column_moments_kernel(int rows, int cols, const float* __restric
     sdev[c] = rows > 1 ? sqrt(q / (rows - 1)) : 0.0;
 }
 
-// Features of one cloud per block: bubbles ordered by distance of the centre
-// from the domain centre (ties by bubble index), each as
-// ((x - c)/s, (y - c)/s, (z - c)/s, r/s).
+// Features of one cloud per block: bubbles ordered by the gap between the
+// bubble's surface and the domain centre, |x_b - c| - r_b (ties by bubble
+// index), each as ((x - c)/s, (y - c)/s, (z - c)/s, r/s).
 __global__ void features_kernel(int n_clouds, int nb, const double* __restrict__ bub, double centre, double inv_scale,
                                 float* __restrict__ X) {
     extern __shared__ double skey[];
@@ -250,7 +250,7 @@ __global__ void features_kernel(int n_clouds, int nb, const double* __restrict__
     const double* b = bub + (size_t)cl * nb * 4;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         const double dx = b[4 * i] - centre, dy = b[4 * i + 1] - centre, dz = b[4 * i + 2] - centre;
-        skey[i] = dx * dx + dy * dy + dz * dz;
+        skey[i] = sqrt(dx * dx + dy * dy + dz * dz) - b[4 * i + 3];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {

@@ -3,6 +3,7 @@
     python -m paper_1705_04374_gb300.experiments uneven3 [--quick]
     python -m paper_1705_04374_gb300.experiments surrogate [--quick]
     python -m paper_1705_04374_gb300.experiments rmse [--quick]
+    python -m paper_1705_04374_gb300.experiments cfg5 [--quick]
 
 uneven3   three levels 32^3 / 64^3 / 128^3 with 1024 / 128 / 16 pairs of 50-bubble
           clouds (FP32 stencil, FP64 reductions) in one uneven batch; device time,
@@ -16,6 +17,9 @@ surrogate the MLP surrogate trained on the solver's own samples and used as the
 rmse      GPU-seconds to a fixed OF-MLMC RMSE: the adaptive loop in plain FP64
           against FP32 (+ the level-0 surrogate), with the FP32 bias measured on
           common samples and included in the RMSE.
+cfg5      500-bubble clouds, four levels 32^3..256^3, sample numbers from the
+          OF-MLMC allocation at 1 % of the mean peak pressure, FP32, with the
+          level-0 surrogate.
 
 Every computation runs in the library's kernels and host code (C ABI); this
 module only orders the calls and times them with CUDA events.
@@ -130,25 +134,38 @@ def features_for(cloud, ids, seed=W.BASE_SEED):
     return S.cloud_features(torch.from_numpy(bub).cuda(), cloud.n_bubbles, cloud.domain_L, cloud.cloud_radius)
 
 
-def train_surrogate(X, y, steps, lr=1e-3, hidden=256, seed=0):
-    """Train the MLP on (X rows, y); returns (net, training seconds)."""
+def train_surrogate(X, y, steps, lr=1e-3, hidden=256, seed=0, chunk=25):
+    """Train the MLP on (X rows, y) with early stopping: 80 % of the rows train,
+    20 % validate after every `chunk` Adam steps; the parameters with the
+    lowest validation error are kept.  Returns (net, device seconds, loss history)."""
     import torch
     n, d = X.shape
-    net = S.MLP(d, hidden, 3, 1, max_rows=n)
+    n_tr = max(2, int(0.8 * n))
+    net = S.MLP(d, hidden, 3, 1, max_rows=n_tr)
     rng = np.random.default_rng(seed)
     sizes = net.sizes
     vec = np.concatenate([np.concatenate([(rng.normal(size=(a, b)) * math.sqrt(2.0 / a)).ravel(), np.zeros(b)])
                           for a, b in zip(sizes[:-1], sizes[1:])]).astype(np.float32)
     net.set_params(vec)
-    m, s = S.column_moments(X)
-    net.set_scaling(m.cpu().numpy(), s.cpu().numpy(), np.array([y.mean()]), np.array([max(y.std(), 1e-30)]))
-    T = torch.from_numpy(y[:, None].astype(np.float32)).cuda()
+    m, s = S.column_moments(X[:n_tr])
+    ytr = y[:n_tr]
+    net.set_scaling(m.cpu().numpy(), s.cpu().numpy(), np.array([ytr.mean()]), np.array([max(ytr.std(), 1e-30)]))
+    T = torch.from_numpy(ytr[:, None].astype(np.float32)).cuda()
+    yv = y[n_tr:]
     e0, e1 = _events()
     e0.record()
-    hist = net.train(X, T, steps=steps, lr=lr)
+    best, best_err, hist = net.get_params(), float("inf"), []
+    for _ in range(max(1, steps // chunk)):
+        hist.extend(net.train(X[:n_tr], T, steps=chunk, lr=lr).tolist())
+        if len(yv):
+            pv = net.forward(X[n_tr:]).cpu().numpy().ravel()
+            err = float(np.mean((pv - yv) ** 2))
+            if err < best_err:
+                best_err, best = err, net.get_params()
+    net.set_params(best)
     e1.record()
     torch.cuda.synchronize()
-    return net, e0.elapsed_time(e1) / 1e3, hist
+    return net, e0.elapsed_time(e1) / 1e3, np.array(hist)
 
 
 def infer(net, X):
@@ -256,8 +273,8 @@ def cmd_rmse(quick):
     cloud = W.cloud_uniform(20)
     sp = w.solver
     levels = [16, 32, 64]
-    tau = 2.0e5 if quick else 1.0e5
-    cap64 = 3e9 if quick else 8e9
+    tau = 6.0e5 if quick else 3.0e5
+    cap64 = 1e9 if quick else 3e9
     s64 = api.Solver(sp, "fp64")
     s32 = api.Solver(sp, "fp32")
     t0 = time.time()
@@ -308,14 +325,50 @@ def cmd_rmse(quick):
     return out
 
 
+# ------------------------------------------------------------------------------ cfg5
+
+def cmd_cfg5(quick):
+    """500-bubble clouds, 4 levels 32^3..256^3, sample numbers from the OF-MLMC
+    allocation at a tolerance of 1 % of the mean peak pressure (FP32 stencil,
+    memory-admitted batches), and the level-0 surrogate on top."""
+    cloud = W.cloud_uniform(500)
+    sp = W.SolverParams(sensors=W.centre_sensor())
+    levels = [16, 32, 64, 128] if quick else [32, 64, 128, 256]
+    s32 = api.Solver(sp, "fp32")
+    warm, _, _ = api.run_ofmlmc(s32, cloud, levels, target=1.0, qoi=0, max_iterations=1)
+    tau = 0.01 * abs(warm["est"]["mean"])
+    res, pairs, ids = api.run_ofmlmc(s32, cloud, levels, target=tau, qoi=0, max_iterations=4,
+                                     max_cell_steps=(2e10 if quick else 2.5e11))
+    out = dict(experiment="cfg5", levels=levels, bubbles=500, qoi="peak pressure [Pa]", tau=tau,
+               warmup_M=warm["M"], M=res["M"], W_cell_steps=res["W"], iterations=res["iterations"],
+               capped=res["capped"], failed=res["failed"], gpu_seconds=res["gpu_seconds"],
+               cell_steps=res["cell_steps"], cell_updates_per_s=res["cell_steps"] / max(res["gpu_seconds"], 1e-30),
+               eps=math.sqrt(res["est"]["eps2"]), mean=res["est"]["mean"],
+               alpha=res["est"]["alpha"].tolist(), sigma_tilde2=res["est"]["sigma_tilde2"].tolist())
+    q0 = pairs[0][:, 0]
+    if len(q0) >= 40:
+        X0 = features_for(cloud, [int(i) for i in ids[0]])
+        n_tr = len(q0) // 2
+        net, t_train, hist = train_surrogate(X0[:n_tr], q0[:n_tr], 400)
+        s_pair, t1 = infer(net, X0[n_tr:])
+        s_extra, t2 = infer(net, features_for(cloud, level_ids(7, 0, 65536 if not quick else 4096)))
+        a0 = res["est"]["alpha"][0]
+        cv = S.surrogate_cv(a0 * q0[n_tr:], a0 * s_pair, a0 * s_extra)
+        out["level0_surrogate"] = dict(corr=float(np.corrcoef(s_pair, q0[n_tr:])[0, 1]), beta=cv["beta"],
+                                       variance_ratio=cv["var"] / (np.var(a0 * q0[n_tr:], ddof=1) / (len(q0) - n_tr)),
+                                       train_seconds=t_train, infer_seconds=t1 + t2)
+        net.close()
+    return out
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["uneven3", "surrogate", "rmse"])
+    ap.add_argument("what", choices=["uneven3", "surrogate", "rmse", "cfg5"])
     ap.add_argument("--quick", action="store_true")
     a = ap.parse_args()
     torch.cuda.set_device(0)
-    fn = {"uneven3": cmd_uneven3, "surrogate": cmd_surrogate, "rmse": cmd_rmse}[a.what]
+    fn = {"uneven3": cmd_uneven3, "surrogate": cmd_surrogate, "rmse": cmd_rmse, "cfg5": cmd_cfg5}[a.what]
     print(json.dumps(fn(a.quick)), flush=True)
 
 
