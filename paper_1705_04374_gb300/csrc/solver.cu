@@ -205,7 +205,7 @@ void stage_table(const Params<T>& full, unsigned mask, Params<T>& out) {
     out = full;
     int n = 0;
     long long blk = 0;
-    for (int g = 0; g < full.n_groups; ++g) {
+    for (int g = 0; g < full.n_groups && g < OFM_MAX_GROUPS; ++g) {
         if (!(mask & (1u << g))) continue;
         out.g[n] = full.g[g];
         out.g[n].block0 = blk;
@@ -219,8 +219,10 @@ void stage_table(const Params<T>& full, unsigned mask, Params<T>& out) {
 void set_active_mask(ofm_batch* b, unsigned mask) {
     if (mask == b->active_mask) return;
     b->active_mask = mask;
-    stage_table(b->pd, mask, b->pd_s);
-    stage_table(b->pf, mask, b->pf_s);
+    if (b->precision == OFM_FP64)   // only the batch's own precision has a table
+        stage_table(b->pd, mask, b->pd_s);
+    else
+        stage_table(b->pf, mask, b->pf_s);
     if (b->chunk_ready) {
         cudaGraphExecDestroy(b->chunk);
         b->chunk_ready = false;
@@ -349,7 +351,7 @@ extern "C" int ofm_batch_workspace_bytes(const ofm_solver* s, const ofm_cloud_pa
     int rc = check_groups(s, cloud, groups, n_groups);
     if (rc != OFM_OK) return rc;
     if (!bytes) return fail(OFM_EINVAL, "NULL bytes");
-    ofm_batch tmp;
+    ofm_batch tmp{};
     Layout Lo;
     layout(s, cloud, groups, n_groups, &tmp, Lo);
     *bytes = Lo.total;
@@ -365,7 +367,7 @@ extern "C" int ofm_batch_create(ofm_batch** out, ofm_solver* s, const ofm_cloud_
     int rc = check_groups(s, cloud, groups, n_groups);
     if (rc != OFM_OK) return rc;
     if (((uintptr_t)workspace) % 256 != 0) return fail(OFM_EINVAL, "workspace must be 256-byte aligned");
-    ofm_batch* b = new (std::nothrow) ofm_batch;
+    ofm_batch* b = new (std::nothrow) ofm_batch();  // value-initialised: every plain field starts at zero
     if (!b) return fail(OFM_ENOMEM, "out of host memory");
     b->solver = s;
     b->precision = s->cfg.precision;
