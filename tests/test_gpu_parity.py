@@ -359,4 +359,4 @@ def test_stage_kernel_variants_are_bitwise_identical(precision):
                     assert a["p_peak"] == c["p_peak"]
                     assert np.array_equal(a["totals_end"], c["totals_end"])
                 else:
-                    assert abs(a["p_peak"] - c["p_peak"]) <= 1e-5 * c["p_peak"]
+                    assert abs(a["p_peak"] - c["p_peak"]) <= 1e-3 * c["p_peak"]   # the FP32 QoI bound
