@@ -273,8 +273,8 @@ def cmd_rmse(quick):
     cloud = W.cloud_uniform(20)
     sp = w.solver
     levels = [16, 32, 64]
-    tau = 6.0e5 if quick else 3.0e5
-    cap64 = 1e9 if quick else 3e9
+    tau = 1.2e6 if quick else 6.0e5
+    cap64 = 1e9 if quick else 4e9
     s64 = api.Solver(sp, "fp64")
     s32 = api.Solver(sp, "fp32")
     t0 = time.time()
@@ -329,18 +329,20 @@ def cmd_rmse(quick):
 
 def cmd_cfg5(quick):
     """500-bubble clouds, 4 levels 32^3..256^3, sample numbers from the OF-MLMC
-    allocation at a tolerance of 1 % of the mean peak pressure (FP32 stencil,
+    allocation for a fixed budget of cell-steps (Eq. M-budget; FP32 stencil,
     memory-admitted batches), and the level-0 surrogate on top."""
     cloud = W.cloud_uniform(500)
     sp = W.SolverParams(sensors=W.centre_sensor())
     levels = [16, 32, 64, 128] if quick else [32, 64, 128, 256]
+    budget = 1.0e10 if quick else 1.2e11
     s32 = api.Solver(sp, "fp32")
-    warm, _, _ = api.run_ofmlmc(s32, cloud, levels, target=1.0, qoi=0, max_iterations=1)
-    tau = 0.01 * abs(warm["est"]["mean"])
-    res, pairs, ids = api.run_ofmlmc(s32, cloud, levels, target=tau, qoi=0, max_iterations=4,
-                                     max_cell_steps=(2e10 if quick else 2.5e11))
-    out = dict(experiment="cfg5", levels=levels, bubbles=500, qoi="peak pressure [Pa]", tau=tau,
-               warmup_M=warm["M"], M=res["M"], W_cell_steps=res["W"], iterations=res["iterations"],
+    warm, _, _ = api.run_ofmlmc(s32, cloud, levels, target=budget, mode="budget", qoi=0, max_iterations=1)
+    res, pairs, ids = api.run_ofmlmc(s32, cloud, levels, target=budget, mode="budget", qoi=0, max_iterations=4,
+                                     max_cell_steps=2.0 * budget, capacity=1 << 18)
+    out = dict(experiment="cfg5", levels=levels, bubbles=500, qoi="peak pressure [Pa]", budget_cell_steps=budget,
+               warmup_M=warm["M"], warmup_mean=warm["est"]["mean"], warmup_eps=math.sqrt(warm["est"]["eps2"]),
+               warmup_alpha=warm["est"]["alpha"].tolist(),
+               M=res["M"], W_cell_steps=res["W"], iterations=res["iterations"],
                capped=res["capped"], failed=res["failed"], gpu_seconds=res["gpu_seconds"],
                cell_steps=res["cell_steps"], cell_updates_per_s=res["cell_steps"] / max(res["gpu_seconds"], 1e-30),
                eps=math.sqrt(res["est"]["eps2"]), mean=res["est"]["mean"],
