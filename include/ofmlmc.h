@@ -192,14 +192,16 @@ int ofm_batch_kernel_launches(ofm_batch* batch, int64_t* launches);
 int ofm_batch_set_profiling(ofm_batch* batch, int on);
 int ofm_batch_stage_time(ofm_batch* batch, double* total_ms, int64_t* n_launches);
 /* Stage-kernel variant: 0 (default) = one block per 8^3 tile; 1 = persistent
- * blocks (two per SM in FP32) that copy the next tile's halo while computing
- * the current one and skip finished samples without launching; -1 = autotune:
- * the first ofm_batch_run of at least 4 steps times two steps of each variant
- * and keeps the faster.  In FP64 both variants give identical bits; in FP32
- * they agree to round-off (the compiler may fuse multiply-adds differently in
- * the two kernels), so runs that must be bitwise reproducible keep a fixed
- * variant.  get_variant also returns the autotuning times (ms, two steps
- * each; may be NULL). */
+ * blocks (three per SM in FP32, one in FP64) with one staging buffer each,
+ * issuing the next tile's halo copies before the current tile's update and
+ * skipping finished samples without launching; -1 = autotune: the first
+ * ofm_batch_run of at least 4 steps times two steps of each variant and keeps
+ * the faster.  In FP64 both variants give identical bits; in FP32 they agree
+ * to round-off (the compiler may fuse multiply-adds differently in the two
+ * kernels), so runs that must be bitwise reproducible keep a fixed variant.
+ * get_variant also returns the autotuning times (ms, two steps of each
+ * variant; tune_ms holds 2 floats, may be NULL).  Errors: OFM_EINVAL for a
+ * variant outside -1..1. */
 int ofm_batch_set_variant(ofm_batch* batch, int variant);
 int ofm_batch_get_variant(ofm_batch* batch, int* variant, float* tune_ms);
 /* Bytes this batch has copied host->device and device->host so far. */

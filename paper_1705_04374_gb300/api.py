@@ -186,7 +186,7 @@ class Batch:
         v = C.c_int()
         t = (C.c_float * 2)()
         nv.check(nv.lib().ofm_batch_get_variant(self.h, C.byref(v), t), "ofm_batch_get_variant")
-        return v.value, (t[0], t[1])
+        return v.value, tuple(t)
 
     def stage_time(self):
         ms = C.c_double()

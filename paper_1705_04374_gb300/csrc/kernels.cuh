@@ -202,15 +202,21 @@ __device__ __forceinline__ void hllc(const Eos<T>& e, const T* wl, const T* wr, 
 // --------------------------------------------------------------------------
 // Tile geometry helpers
 // --------------------------------------------------------------------------
-// Compact staging layout of the tile and its halo (no corners): rows along x.
-// Rows whose (y, z) both lie in the tile hold x = -3..10 (14 cells); rows in a
-// y- or z-halo slab hold x = 0..7.  row_off(y, z) + x is the staged index.
-constexpr int ROWS_INT = TS * TS * BX;           // 896 cells in full-width rows
-constexpr int ROWS_Y = ROWS_INT + 2 * HALO * TS * TS;  // start of z-halo rows (1280)
+// Staging layout of the tile and its halo (no corners), rows along x, every
+// row starting on a 16-byte boundary so that rows are copied 16 bytes at a
+// time.  Rows whose (y, z) both lie in the tile have RW = 16 slots holding
+// x = -4..11 (the stencils read x = -3..10; slots 0 and 15 are padding); rows
+// of the y- and z-halo slabs hold x = 0..7.  row_off(y, z) + x is the staged
+// index.
+constexpr int RW = 16;                                 // slots of a full-width row
+constexpr int XOFF = 4;                                // slot of x = 0 in a full-width row
+constexpr int ROWS_INT = TS * TS * RW;                 // 1024 slots in full-width rows
+constexpr int ROWS_Y = ROWS_INT + 2 * HALO * TS * TS;  // start of z-halo rows (1408)
+static_assert(ROWS_Y + 2 * HALO * TS * TS == NCROSS, "staging layout size");
 
 __device__ __forceinline__ int row_off(int y, int z) {
     const bool yi = (unsigned)y < (unsigned)TS, zi = (unsigned)z < (unsigned)TS;
-    if (yi && zi) return (z * TS + y) * BX + HALO;
+    if (yi && zi) return (z * TS + y) * RW + XOFF;
     if (zi) {
         const int hy = y < 0 ? y + HALO : y - TS + HALO;  // 0..5
         return ROWS_INT + (hy * TS + z) * TS;
@@ -219,36 +225,9 @@ __device__ __forceinline__ int row_off(int y, int z) {
     return ROWS_Y + (hz * TS + y) * TS;
 }
 
-// Staged cell i in [0, NCROSS): the tile, then six 3-deep halo slabs
-// (x-, x+, y-, y+, z-, z+).  Box coordinates are tile-relative.
-__device__ __forceinline__ void cross_decode(int i, int& bx, int& by, int& bz) {
-    if (i < NCELL) {
-        bx = i & 7;
-        by = (i >> 3) & 7;
-        bz = i >> 6;
-        return;
-    }
-    const int j = i - NCELL;
-    const int slab = j / NSLAB;
-    const int r = j - slab * NSLAB;
-    const int hi = slab & 1;
-    if (slab < 2) {
-        const int hx = r % 3, q = r / 3;
-        by = q & 7;
-        bz = q >> 3;
-        bx = hi ? TS + hx : hx - HALO;
-    } else if (slab < 4) {
-        bx = r & 7;
-        const int q = r >> 3;
-        const int hy = q % 3;
-        bz = q / 3;
-        by = hi ? TS + hy : hy - HALO;
-    } else {
-        bx = r & 7;
-        by = (r >> 3) & 7;
-        const int hz = r >> 6;
-        bz = hi ? TS + hz : hz - HALO;
-    }
+// Staged slot i in [0, NCROSS) that holds no stencil cell (row padding).
+__device__ __forceinline__ bool pad_slot(int i) {
+    return i < ROWS_INT && ((i & (RW - 1)) == 0 || (i & (RW - 1)) == RW - 1);
 }
 
 __device__ __forceinline__ int bc_map(int g, int N, int bc) {
@@ -595,7 +574,7 @@ __device__ __forceinline__ void face_fp64(const Eos<double>& e, const double* __
     hllc<double, DIR>(e, wl, wr, F);
 }
 
-// Asynchronous global -> shared copies (cp.async) of 4 or 8 bytes, and an L2
+// Asynchronous global -> shared copies (cp.async) of one element, and an L2
 // prefetch of a contiguous global range (bulk, no registers or shared memory).
 template <typename T>
 __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
@@ -604,6 +583,12 @@ __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// 16 bytes, both addresses 16-byte aligned, cached in L2 only.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
@@ -632,25 +617,62 @@ __device__ __forceinline__ void tile_ctx(const Params<T>& P, long long b, int pa
     c.dQ = (T*)G.dQ + soff;
 }
 
-// Asynchronous copies of a tile's raw Q (tile and halo, boundary ghosts by
-// index mapping) into sBuf, all in flight at once; for stages that read dQ,
-// an L2 prefetch of the tile's own dQ rows.
+// Asynchronous copies of a tile's raw Q (tile and halo) into sBuf, all in
+// flight at once, in segments of four cells of one row: 16-byte copies (two
+// in double precision) wherever the four cells lie in the domain, else one
+// copy per halo cell through the boundary map (x halos of tiles on the
+// domain's x faces; rows of y and z halos are mapped as a whole).  For stages
+// that read dQ, an L2 prefetch of the tile's own dQ rows.
+constexpr int NSEG_INT = TS * TS * 4;                 // full-width rows: 4 segments each
+constexpr int NSEG = NSEG_INT + 4 * HALO * TS * 2;     // + y and z halo rows: 2 each (448)
+
 template <typename T, int STAGE>
 __device__ __forceinline__ void tile_issue(const Params<T>& P, const TileCtx<T>& c, T* sBuf) {
     const BlockWork<T>& bw = c.bw;
     const int N = bw.G->N;
     const size_t n3 = (size_t)N * N * N;
     const int bc = P.bc;
-    for (int i = threadIdx.x; i < NCROSS; i += NT) {
-        int bx, by, bz;
-        cross_decode(i, bx, by, bz);
-        const int gx = bc_map(bw.x0 + bx, N, bc);
+    for (int u = threadIdx.x; u < NSEG; u += NT) {
+        int by, bz, bx0;   // tile-relative row and first x of the segment
+        if (u < NSEG_INT) {
+            const int row = u >> 2, seg = u & 3;
+            by = row & 7;
+            bz = row >> 3;
+            bx0 = 4 * seg - 4;
+        } else {
+            constexpr int NSEG_SLAB = 2 * HALO * TS * 2;        // units of the y (then z) halo rows
+            const int v = u - NSEG_INT, zs = v >= NSEG_SLAB;
+            const int row = (v - zs * NSEG_SLAB) >> 1, h = row % (2 * HALO), r = row / (2 * HALO);
+            const int off = h < HALO ? h - HALO : TS + h - HALO;   // -3..-1, 8..10
+            bx0 = 4 * (v & 1);
+            if (!zs) {
+                by = off;
+                bz = r;
+            } else {
+                by = r;
+                bz = off;
+            }
+        }
         const int gy = bc_map(bw.y0 + by, N, bc);
         const int gz = bc_map(bw.z0 + bz, N, bc);
-        const size_t gi = ((size_t)gz * N + gy) * N + gx;
-        const int si = row_off(by, bz) + bx;
+        const size_t grow = ((size_t)gz * N + gy) * N;
+        const int si = row_off(by, bz) + bx0;
+        const int gx0 = bw.x0 + bx0;
+        if (gx0 >= 0 && gx0 + 4 <= N) {
 #pragma unroll
-        for (int v = 0; v < 7; ++v) cp_async(sBuf + v * NCROSS + si, c.Qin + v * n3 + gi);
+            for (int v = 0; v < 7; ++v)
+#pragma unroll
+                for (int h = 0; h < (int)sizeof(T) / 4; ++h)
+                    cp_async16(sBuf + v * NCROSS + si + 2 * h, c.Qin + v * n3 + grow + gx0 + 2 * h);
+        } else {
+            // a 4-cell x-halo segment crossing the domain face: its 3 stencil cells
+            const int k0 = bx0 < 0 ? 1 : 0, k1 = bx0 < 0 ? 4 : 3;
+            for (int k = k0; k < k1; ++k) {
+                const int gx = bc_map(gx0 + k, N, bc);
+#pragma unroll
+                for (int v = 0; v < 7; ++v) cp_async(sBuf + v * NCROSS + si + k, c.Qin + v * n3 + grow + gx);
+            }
+        }
     }
     if (STAGE > 0) {
         for (int r = threadIdx.x; r < 7 * TS * TS; r += NT) {
@@ -673,6 +695,7 @@ __device__ __forceinline__ void fill_rows(int* sRow) {
 template <typename T>
 __device__ __forceinline__ void tile_convert(const Eos<T>& e, T* sW) {
     for (int i = threadIdx.x; i < NCROSS; i += NT) {
+        if (pad_slot(i)) continue;
         T q[7], w[7];
 #pragma unroll
         for (int v = 0; v < 7; ++v) q[v] = sW[v * NCROSS + i];
@@ -682,26 +705,22 @@ __device__ __forceinline__ void tile_convert(const Eos<T>& e, T* sW) {
     }
 }
 
-// Faces (direction by direction), per-cell right-hand sides, alpha2 source,
-// 2N update and, in the last stage, the new state's per-tile reductions, for
-// one tile whose primitives are staged in sW.
-template <typename T, int STAGE>
-__device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& c, long long tile_index,
-                                          const T* __restrict__ sW, T* __restrict__ sF,
-                                          const int* __restrict__ sRow) {
-    const BlockWork<T>& bw = c.bw;
-    const GroupDev& G = *bw.G;
-    const int N = G.N;
-    const size_t n3 = (size_t)N * N * N;
-    const T* __restrict__ Qin = c.Qin;
-    T* __restrict__ Qout = c.Qout;
-    T* __restrict__ dQ = c.dQ;
-    const T dt = (T)P.s.dt[bw.slot];
-    const T invh = T(1) / (T)G.h;  // 1/h, formed as the FP64 reference forms it
-    const Eos<T> e = P.eos;
-
+// Right-hand sides of one tile's cells (faces direction by direction,
+// per-cell flux differences and the face-velocity divergence), from the
+// primitives staged in sW.  Cell k of this thread is threadIdx.x + k * NT.
+template <typename T>
+struct TileRhs {
     T rhs[CELLS_PER_THREAD][7];
     T divu[CELLS_PER_THREAD];
+};
+
+template <typename T>
+__device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>& c, const T* __restrict__ sW,
+                                           T* __restrict__ sF, const int* __restrict__ sRow, TileRhs<T>& R) {
+    const T invh = T(1) / (T)c.bw.G->h;  // 1/h, formed as the FP64 reference forms it
+    const Eos<T> e = P.eos;
+    T (&rhs)[CELLS_PER_THREAD][7] = R.rhs;
+    T (&divu)[CELLS_PER_THREAD] = R.divu;
 #pragma unroll
     for (int k = 0; k < CELLS_PER_THREAD; ++k) {
         divu[k] = T(0);
@@ -709,7 +728,7 @@ __device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& 
         for (int v = 0; v < 7; ++v) rhs[k][v] = T(0);
     }
 
-    // 2. faces, direction by direction
+    // faces, direction by direction
 #pragma unroll 1
     for (int dir = 0; dir < 3; ++dir) {
         for (int f = threadIdx.x; f < NFACE; f += NT) {
@@ -768,8 +787,42 @@ __device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& 
         }
         __syncthreads();
     }
+}
 
-    // 3. alpha2 source, 2N update, and (last stage) the new state's reductions
+// Pressure and raw alpha2 of this thread's cells (the alpha2 source term).
+template <typename T>
+__device__ __forceinline__ void tile_cell_pa(const T* __restrict__ sW, T (&pc)[CELLS_PER_THREAD],
+                                             T (&ac)[CELLS_PER_THREAD]) {
+#pragma unroll
+    for (int k = 0; k < CELLS_PER_THREAD; ++k) {
+        const int c = threadIdx.x + k * NT;
+        if (c < NCELL) {
+            const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+            const int si = (z * TS + y) * RW + XOFF + x;   // row_off(y, z) + x for tile cells
+            pc[k] = sW[5 * NCROSS + si];
+            ac[k] = sW[6 * NCROSS + si];
+        }
+    }
+}
+
+// alpha2 source, 2N update and, in the last stage, the new state's per-tile
+// reductions (reads Q and dQ from global memory; shared memory is not used
+// except by the block reduction).
+template <typename T, int STAGE>
+__device__ __forceinline__ void tile_update(const Params<T>& P, const TileCtx<T>& c, long long tile_index,
+                                            TileRhs<T>& R, const T (&pc)[CELLS_PER_THREAD],
+                                            const T (&ac)[CELLS_PER_THREAD]) {
+    const BlockWork<T>& bw = c.bw;
+    const GroupDev& G = *bw.G;
+    const int N = G.N;
+    const size_t n3 = (size_t)N * N * N;
+    const T* __restrict__ Qin = c.Qin;
+    T* __restrict__ Qout = c.Qout;
+    T* __restrict__ dQ = c.dQ;
+    const T dt = (T)P.s.dt[bw.slot];
+    const Eos<T> e = P.eos;
+    T (&rhs)[CELLS_PER_THREAD][7] = R.rhs;
+    T (&divu)[CELLS_PER_THREAD] = R.divu;
     const T A = (T)P.rkA[STAGE], B = (T)P.rkB[STAGE];
     Red red;
     red_init(red);
@@ -778,9 +831,8 @@ __device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& 
         const int c = threadIdx.x + k * NT;
         if (c < NCELL) {
             const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-            const int si = (z * TS + y) * BX + HALO + x;   // row_off(y, z) + x for tile cells
-            const T p = sW[5 * NCROSS + si];
-            const T a2raw = sW[6 * NCROSS + si];
+            const T p = pc[k];
+            const T a2raw = ac[k];
             const T a2 = clamp01(a2raw);
             const T a1 = T(1) - a2;
             const T z1 = e.g1 * (p + e.pc1);  // rho_1 c_1^2
@@ -805,6 +857,19 @@ __device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& 
         const long long tile = tile_index - G.block0 - (long long)bw.s_local * G.tps;
         block_reduce_write(red, G.part + (size_t)bw.s_local * G.tps + tile);
     }
+}
+
+
+// One tile: faces, source, update.
+template <typename T, int STAGE>
+__device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& c, long long tile_index,
+                                          const T* __restrict__ sW, T* __restrict__ sF,
+                                          const int* __restrict__ sRow) {
+    TileRhs<T> R;
+    tile_faces<T>(P, c, sW, sF, sRow, R);
+    T pc[CELLS_PER_THREAD], ac[CELLS_PER_THREAD];
+    tile_cell_pa(sW, pc, ac);
+    tile_update<T, STAGE>(P, c, tile_index, R, pc, ac);
 }
 
 // One RK stage, one block per tile.
@@ -844,17 +909,19 @@ __device__ __forceinline__ long long next_active(const Params<T>& P, long long t
     return t;
 }
 
-// One RK stage, persistent blocks: each block walks tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ... (finished samples skipped without a launch),
-// copying the next tile's raw Q into a second shared buffer while it computes
-// the current one.  Same arithmetic, same results as stage_kernel.
+// One RK stage, persistent blocks (three per SM in single precision, one
+// staging buffer each): each block walks tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ... (finished samples skipped without a launch).  Once a tile's
+// faces are done and its pressure and alpha2 are in registers, the block
+// issues the next tile's halo copies and then performs the current tile's
+// update, so the update's global loads and the next tile's copies are in
+// flight together.  Same arithmetic as stage_kernel.
 template <typename T, int STAGE>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
-    stage_kernel_pp(const __grid_constant__ Params<T> P, int parity) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
+    stage_kernel_persistent(const __grid_constant__ Params<T> P, int parity) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sW0 = reinterpret_cast<T*>(smem_raw);
-    T* sW1 = sW0 + 7 * NCROSS;
-    T* sF = sW1 + 7 * NCROSS;
+    T* sW = reinterpret_cast<T*>(smem_raw);
+    T* sF = sW + 7 * NCROSS;
     int* sRow = reinterpret_cast<int*>(sF + 8 * NFACE);
     fill_rows(sRow);
     const long long stride = gridDim.x;
@@ -862,29 +929,27 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     TileCtx<T> c;
     if (t < P.total_blocks) {
         tile_ctx(P, t, parity, c);
-        tile_issue<T, STAGE>(P, c, sW0);
+        tile_issue<T, STAGE>(P, c, sW);
     }
-    cp_async_commit();
-    int i = 0;
     while (t < P.total_blocks) {
+        cp_async_wait_all();
+        __syncthreads();
+        tile_convert(P.eos, sW);
+        __syncthreads();
+        TileRhs<T> R;
+        tile_faces<T>(P, c, sW, sF, sRow, R);
+        T pc[CELLS_PER_THREAD], ac[CELLS_PER_THREAD];
+        tile_cell_pa(sW, pc, ac);
+        __syncthreads();   // every read of sW is done
         const long long tn = next_active(P, t + stride, stride);
         TileCtx<T> cn;
-        T* cur = (i & 1) ? sW1 : sW0;
-        T* nxt = (i & 1) ? sW0 : sW1;
         if (tn < P.total_blocks) {
             tile_ctx(P, tn, parity, cn);
-            tile_issue<T, STAGE>(P, cn, nxt);
+            tile_issue<T, STAGE>(P, cn, sW);
         }
-        cp_async_commit();
-        cp_async_wait_one();   // everything but the copies just issued has landed
-        __syncthreads();
-        tile_convert(P.eos, cur);
-        __syncthreads();
-        tile_body<T, STAGE>(P, c, t, cur, sF, sRow);
-        __syncthreads();
+        tile_update<T, STAGE>(P, c, t, R, pc, ac);
         t = tn;
         c = cn;
-        ++i;
     }
     cp_async_wait_all();
 }
@@ -1062,24 +1127,23 @@ __global__ void __launch_bounds__(256) totals_kernel(const __grid_constant__ Par
 template <typename T>
 int set_smem_attrs() {
     const int bytes = (int)smem_bytes(sizeof(T));
-    const int bytes_pp = (int)smem_bytes_pp(sizeof(T));
     CUDA_TRY(cudaFuncSetAttribute(stage_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     CUDA_TRY(cudaFuncSetAttribute(stage_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     CUDA_TRY(cudaFuncSetAttribute(stage_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_pp<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_pp));
-    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_pp<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_pp));
-    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_pp<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes_pp));
+    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_persistent<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_persistent<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_persistent<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     return OFM_OK;
 }
 
-// Grid of the persistent variant: resident blocks per SM times the SM count,
-// never more than the number of tiles.
+// Grid of the persistent variant: resident blocks per SM (three in single,
+// one in double precision) times the SM count, never more than the tiles.
 template <typename T>
-unsigned pp_grid(const Params<T>& P) {
+unsigned persistent_grid(const Params<T>& P) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long want = (long long)sms * (sizeof(T) == 4 ? 2 : 1);
+    const long long want = (long long)sms * (sizeof(T) == 4 ? 3 : 1);
     return (unsigned)(P.total_blocks < want ? P.total_blocks : want);
 }
 
@@ -1087,7 +1151,7 @@ template <typename T, int STAGE>
 void launch_one_stage(const Params<T>& P, int variant, int parity, cudaStream_t st) {
     if (P.total_blocks <= 0) return;  // every group finished
     if (variant == OFM_VARIANT_PERSISTENT)
-        stage_kernel_pp<T, STAGE><<<pp_grid(P), NT, smem_bytes_pp(sizeof(T)), st>>>(P, parity);
+        stage_kernel_persistent<T, STAGE><<<persistent_grid(P), NT, smem_bytes(sizeof(T)), st>>>(P, parity);
     else
         stage_kernel<T, STAGE><<<(unsigned)P.total_blocks, NT, smem_bytes(sizeof(T)), st>>>(P, parity);
 }

@@ -92,7 +92,7 @@ struct ofm_batch {
     bool chunk_ready;
     bool initialised;
     int variant;              // stage-kernel variant; -1 = pick by timing at the first run
-    float tune_ms[2];         // autotuning times of the two variants (two steps each)
+    float tune_ms[OFM_N_VARIANTS];  // autotuning times of the variants (two steps each)
     bool profiling;           // steps without graphs, CUDA events around each stage kernel
     cudaEvent_t pev[4];
     double stage_ms;
@@ -385,7 +385,7 @@ extern "C" int ofm_batch_create(ofm_batch** out, ofm_solver* s, const ofm_cloud_
     b->initialised = false;
     b->profiling = false;
     b->variant = OFM_VARIANT_TILES;
-    b->tune_ms[0] = b->tune_ms[1] = 0.f;
+    for (int v = 0; v < OFM_N_VARIANTS; ++v) b->tune_ms[v] = 0.f;
     for (int k = 0; k < 4; ++k) b->pev[k] = nullptr;
     b->stage_ms = 0.0;
     b->stage_launches = 0;
@@ -499,12 +499,12 @@ extern "C" int ofm_batch_run(ofm_batch* b, int max_steps, int* n_active) {
     if (rc != OFM_OK) return rc;
     int done_steps = 0;
     int active = 1;
-    if (b->variant < 0 && !b->profiling && max_steps >= 4 && (b->global_steps & 1) == 0) {
-        // autotune: the two stage-kernel variants give identical results; time
-        // two steps of each (alternating) and keep the faster
-        float t[2] = {0.f, 0.f};
-        for (int k = 0; k < 4; ++k) {
-            const int var = k & 1;
+    if (b->variant < 0 && !b->profiling && max_steps >= 2 * OFM_N_VARIANTS && (b->global_steps & 1) == 0) {
+        // autotune: time two steps of each stage-kernel variant (interleaved)
+        // and keep the fastest; the step count stays even
+        float t[OFM_N_VARIANTS] = {};
+        for (int k = 0; k < 2 * OFM_N_VARIANTS; ++k) {
+            const int var = k % OFM_N_VARIANTS;
             CUDA_TRY(cudaEventRecord(b->pev[0], b->priv));
             rc = b->precision == OFM_FP64
                      ? launch_step(b->pd_s, b->pd, var, (int)(b->global_steps & 1), b->priv, &b->launches)
@@ -518,9 +518,11 @@ extern "C" int ofm_batch_run(ofm_batch* b, int max_steps, int* n_active) {
             b->global_steps += 1;
             done_steps += 1;
         }
-        b->variant = t[1] < t[0] ? OFM_VARIANT_PERSISTENT : OFM_VARIANT_TILES;
-        b->tune_ms[0] = t[0];
-        b->tune_ms[1] = t[1];
+        int best = 0;
+        for (int v = 1; v < OFM_N_VARIANTS; ++v)
+            if (t[v] < t[best]) best = v;
+        b->variant = best;
+        for (int v = 0; v < OFM_N_VARIANTS; ++v) b->tune_ms[v] = t[v];
     }
     const int variant = b->variant < 0 ? OFM_VARIANT_TILES : b->variant;
     while (done_steps < max_steps) {
@@ -727,7 +729,7 @@ extern "C" int ofm_batch_set_profiling(ofm_batch* b, int on) {
 
 extern "C" int ofm_batch_set_variant(ofm_batch* b, int variant) {
     ofm::clear_error();
-    if (!b || variant < -1 || variant > OFM_VARIANT_PERSISTENT) return fail(OFM_EINVAL, "bad batch or variant");
+    if (!b || variant < -1 || variant >= OFM_N_VARIANTS) return fail(OFM_EINVAL, "bad batch or variant");
     if (variant != b->variant && b->chunk_ready) {
         cudaGraphExecDestroy(b->chunk);
         b->chunk_ready = false;
@@ -740,10 +742,8 @@ extern "C" int ofm_batch_get_variant(ofm_batch* b, int* variant, float* tune_ms)
     ofm::clear_error();
     if (!b || !variant) return fail(OFM_EINVAL, "NULL argument");
     *variant = b->variant;
-    if (tune_ms) {
-        tune_ms[0] = b->tune_ms[0];
-        tune_ms[1] = b->tune_ms[1];
-    }
+    if (tune_ms)
+        for (int v = 0; v < OFM_N_VARIANTS; ++v) tune_ms[v] = b->tune_ms[v];
     return OFM_OK;
 }
 

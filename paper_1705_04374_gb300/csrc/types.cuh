@@ -14,10 +14,9 @@ namespace gpu {
 constexpr int TS = 8;                    // tile edge (cells)
 constexpr int HALO = 3;                  // WENO5 needs three cells on each side
 constexpr int BX = TS + 2 * HALO;        // staged box edge (14)
-constexpr int BOX3 = BX * BX * BX;       // staged box cells (2744, corners unused)
 constexpr int NCELL = TS * TS * TS;      // 512 cells per tile
 constexpr int NSLAB = HALO * TS * TS;    // 192 cells per halo slab
-constexpr int NCROSS = NCELL + 6 * NSLAB;  // 1664 staged cells
+constexpr int NCROSS = TS * TS * 16 + 4 * NSLAB;  // 1792 staged slots (1664 cells + row padding)
 constexpr int NFACE = (TS + 1) * TS * TS;  // 576 faces per direction
 constexpr int NT = 256;                  // threads per block (measured better than 192 and 256x2)
 constexpr int CELLS_PER_THREAD = (NCELL + NT - 1) / NT;  // 2
@@ -95,17 +94,16 @@ struct Params {
 constexpr double RK_A[3] = {0.0, -2.915492524638791, -0.000000093517376};
 constexpr double RK_B[3] = {0.924574, 0.287713063186749, 0.626538109512740};
 
-
 // Stage-kernel dynamic shared memory: primitives of the staged cells, face
-// fluxes of one direction, and the staging layout's row-offset table.
+// fluxes of one direction, and the staging layout's row-offset table
+// (FP32: 69.4 KB, three blocks per SM; FP64: 137 KB, one).
 constexpr size_t smem_bytes(size_t elem) { return elem * (7 * NCROSS + 8 * NFACE) + sizeof(int) * BX * BX; }
-// The persistent variant double-buffers the staged primitives.
-constexpr size_t smem_bytes_pp(size_t elem) { return elem * (14 * NCROSS + 8 * NFACE) + sizeof(int) * BX * BX; }
 
-// Stage-kernel variants: one block per tile, or persistent blocks that copy
-// the next tile while computing the current one.
+// Stage-kernel variants: one block per tile, or persistent blocks that issue
+// the next tile's copies before the current tile's update.
 constexpr int OFM_VARIANT_TILES = 0;
 constexpr int OFM_VARIANT_PERSISTENT = 1;
+constexpr int OFM_N_VARIANTS = 2;
 
 // Launch wrappers, instantiated for double in kernels_fp64.cu (compiled
 // without FMA contraction, in the oracle's operation order) and for float in

@@ -324,10 +324,10 @@ def test_full_size_ensemble_one_step_sampled(precision, tol):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_stage_kernel_variants_are_bitwise_identical(precision):
-    """One block per tile, persistent double-buffered blocks and the autotuned
-    choice give the same bits in FP64 (round-off agreement in FP32), on an
-    uneven batch whose groups finish at different steps (the persistent
-    variant skips finished samples)."""
+    """One block per tile, persistent blocks and the autotuned choice give the
+    same bits in FP64 (round-off agreement in FP32), on an uneven batch whose
+    groups finish at different steps (the persistent variant skips finished
+    samples)."""
     w = W.tiny(16, 4)
     sp = w.solver
     spec = [(16, [0, 1, 2]), (32, [3, 4]), (8, [5])]
