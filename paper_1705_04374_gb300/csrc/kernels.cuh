@@ -117,6 +117,13 @@ __device__ __forceinline__ bool admissible(const Eos<T>& e, const T* w) {
     return w[5] + Pi / (G + T(1)) > T(0);
 }
 
+// The same test in single precision without the division ((Gamma+1) > 0),
+// also returning the state's closure for the Riemann solver.
+__device__ __forceinline__ bool admissible_f(const Eos<float>& e, const float* w, float& G, float& Pi) {
+    closure(e, w[6], G, Pi);
+    return w[6] >= 0.0f && w[6] <= 1.0f && w[0] > 0.0f && w[1] > 0.0f && (G + 1.0f) * w[5] + Pi > 0.0f;
+}
+
 // HLLC flux in direction DIR.  F[0..5]: mass 1, mass 2, momentum x/y/z,
 // energy; F[6]: alpha2 flux = alpha2 (upwind by the sign of s*) times the
 // face velocity; F[7]: the face velocity (for div u), i.e. the velocity that
@@ -474,13 +481,12 @@ __device__ __forceinline__ void weno5_pair(float m2, float m1, float c0, float p
 // HLLC in the face frame (un normal, ut1/ut2 tangential), single precision.
 // Output: F[0..1] masses, F[2] normal momentum, F[3..4] tangential momenta,
 // F[5] energy, F[6] alpha2 flux, F[7] face velocity.
-__device__ __forceinline__ void hllc_frame(const Eos<float>& e, const float* wl, const float* wr, float* F) {
+// (GL, PiL), (GR, PiR): the closure of each side.
+__device__ __forceinline__ void hllc_frame(const float* wl, const float* wr, float GL, float PiL, float GR, float PiR,
+                                           float* F) {
     const float rL = wl[0] + wl[1], rR = wr[0] + wr[1];
     const float uL = wl[2], uR = wr[2];
     const float pL = wl[5], pR = wr[5];
-    float GL, PiL, GR, PiR;
-    closure(e, wl[6], GL, PiL);
-    closure(e, wr[6], GR, PiR);
     const float EL = GL * pL + PiL + 0.5f * rL * (wl[2] * wl[2] + wl[3] * wl[3] + wl[4] * wl[4]);
     const float ER = GR * pR + PiR + 0.5f * rR * (wr[2] * wr[2] + wr[3] * wr[3] + wr[4] * wr[4]);
     const float cL = sqrtf(((GL + 1.0f) * pL + PiL) / (GL * rL));
@@ -532,13 +538,16 @@ __device__ __forceinline__ void face_fp32(const Eos<float>& e, const float* __re
         const float* P = sW + v * NCROSS;
         weno5_pair(P[i6[0]], P[i6[1]], P[i6[2]], P[i6[3]], P[i6[4]], P[i6[5]], 4.0f * e.eps, wl[v], wr[v]);
     }
-    if (!admissible(e, wl)) {
+    float GL, PiL, GR, PiR;
+    if (!admissible_f(e, wl, GL, PiL)) {
 #pragma unroll
         for (int v = 0; v < 7; ++v) wl[v] = sW[v * NCROSS + i6[2]];
+        closure(e, wl[6], GL, PiL);
     }
-    if (!admissible(e, wr)) {
+    if (!admissible_f(e, wr, GR, PiR)) {
 #pragma unroll
         for (int v = 0; v < 7; ++v) wr[v] = sW[v * NCROSS + i6[3]];
+        closure(e, wr[6], GR, PiR);
     }
     // rotate velocities into the face frame: slot 2 normal, 3 and 4 tangential
     const float lx = wl[2], ly = wl[3], lz = wl[4], rx = wr[2], ry = wr[3], rz = wr[4];
@@ -548,7 +557,7 @@ __device__ __forceinline__ void face_fp32(const Eos<float>& e, const float* __re
     wr[2] = dir == 0 ? rx : (dir == 1 ? ry : rz);
     wr[3] = dir == 0 ? ry : (dir == 1 ? rz : rx);
     wr[4] = dir == 0 ? rz : (dir == 1 ? rx : ry);
-    hllc_frame(e, wl, wr, F);
+    hllc_frame(wl, wr, GL, PiL, GR, PiR, F);
 }
 
 // One face in double precision, in the FP64 reference's operation order.
