@@ -43,7 +43,7 @@ M_SAMPLES = 512
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FLOPS_FILE = os.path.join(ROOT, "paper_1705_04374_gb300", "data", "flops_per_cell_step.json")
 TRAFFIC_FILE = os.path.join(ROOT, "paper_1705_04374_gb300", "data", "ncu_traffic.json")
-KERNEL_SRC = os.path.join(ROOT, "paper_1705_04374_gb300", "csrc", "kernels.cuh")
+KERNEL_SRC = [os.path.join(ROOT, "paper_1705_04374_gb300", "csrc", f) for f in ("kernels.cuh", "types.cuh")]
 
 # FP32 / FP64 non-tensor peaks from unit counts and the maximum SM clock:
 # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 at the nominal
@@ -217,8 +217,11 @@ def load_json(path):
 
 
 def kernel_hash():
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for path in KERNEL_SRC:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def run_ours(args):
