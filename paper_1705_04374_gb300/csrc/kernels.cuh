@@ -529,34 +529,28 @@ __device__ __forceinline__ void hllc_frame(const float* wl, const float* wr, flo
 }
 
 // One face in single precision: stencil of six staged cells (staged indices
-// i6), direction dir.  Returns F in the face frame (see hllc_frame).
+// i6); vo[v] is the staged offset of face-frame variable v (slot 2 the normal
+// velocity, 3 and 4 the tangential ones), so the states are reconstructed
+// directly in the face frame.  Returns F in the face frame (see hllc_frame).
 __device__ __forceinline__ void face_fp32(const Eos<float>& e, const float* __restrict__ sW, const int* i6,
-                                          int dir, float* F) {
+                                          const int (&vo)[7], float* F) {
     float wl[7], wr[7];
 #pragma unroll
     for (int v = 0; v < 7; ++v) {
-        const float* P = sW + v * NCROSS;
+        const float* P = sW + vo[v];
         weno5_pair(P[i6[0]], P[i6[1]], P[i6[2]], P[i6[3]], P[i6[4]], P[i6[5]], 4.0f * e.eps, wl[v], wr[v]);
     }
     float GL, PiL, GR, PiR;
     if (!admissible_f(e, wl, GL, PiL)) {
 #pragma unroll
-        for (int v = 0; v < 7; ++v) wl[v] = sW[v * NCROSS + i6[2]];
+        for (int v = 0; v < 7; ++v) wl[v] = sW[vo[v] + i6[2]];
         closure(e, wl[6], GL, PiL);
     }
     if (!admissible_f(e, wr, GR, PiR)) {
 #pragma unroll
-        for (int v = 0; v < 7; ++v) wr[v] = sW[v * NCROSS + i6[3]];
+        for (int v = 0; v < 7; ++v) wr[v] = sW[vo[v] + i6[3]];
         closure(e, wr[6], GR, PiR);
     }
-    // rotate velocities into the face frame: slot 2 normal, 3 and 4 tangential
-    const float lx = wl[2], ly = wl[3], lz = wl[4], rx = wr[2], ry = wr[3], rz = wr[4];
-    wl[2] = dir == 0 ? lx : (dir == 1 ? ly : lz);
-    wl[3] = dir == 0 ? ly : (dir == 1 ? lz : lx);
-    wl[4] = dir == 0 ? lz : (dir == 1 ? lx : ly);
-    wr[2] = dir == 0 ? rx : (dir == 1 ? ry : rz);
-    wr[3] = dir == 0 ? ry : (dir == 1 ? rz : rx);
-    wr[4] = dir == 0 ? rz : (dir == 1 ? rx : ry);
     hllc_frame(wl, wr, GL, PiL, GR, PiR, F);
 }
 
@@ -714,6 +708,38 @@ __device__ __forceinline__ void tile_convert(const Eos<T>& e, T* sW) {
     }
 }
 
+// One face of direction dir from the stencil i6, its 8 values (7 fluxes
+// and the face velocity) written to dst[v * stride] in the staged variable
+// order.
+template <typename T>
+__device__ __forceinline__ void face_store(const Eos<T>& e, const T* __restrict__ sW, const int* i6, int dir,
+                                           T* __restrict__ dst, int stride) {
+    T F[8];
+    if constexpr (std::is_same<T, double>::value) {
+        if (dir == 0)
+            face_fp64<0>(e, sW, i6, F);
+        else if (dir == 1)
+            face_fp64<1>(e, sW, i6, F);
+        else
+            face_fp64<2>(e, sW, i6, F);
+#pragma unroll
+        for (int v = 0; v < 8; ++v) dst[v * stride] = F[v];
+    } else {
+        const int r1 = dir == 0 ? 3 : (dir == 1 ? 4 : 2);   // staged row of the first tangential velocity
+        const int r2 = dir == 0 ? 4 : (dir == 1 ? 2 : 3);   // and of the second
+        const int vo[7] = {0, NCROSS, (2 + dir) * NCROSS, r1 * NCROSS, r2 * NCROSS, 5 * NCROSS, 6 * NCROSS};
+        face_fp32(e, sW, i6, vo, F);
+        dst[0] = F[0];
+        dst[stride] = F[1];
+        dst[(2 + dir) * stride] = F[2];
+        dst[r1 * stride] = F[3];
+        dst[r2 * stride] = F[4];
+        dst[5 * stride] = F[5];
+        dst[6 * stride] = F[6];
+        dst[7 * stride] = F[7];
+    }
+}
+
 // Right-hand sides of one tile's cells (faces direction by direction,
 // per-cell flux differences and the face-velocity divergence), from the
 // primitives staged in sW.  Cell k of this thread is threadIdx.x + k * NT.
@@ -737,48 +763,32 @@ __device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>&
         for (int v = 0; v < 7; ++v) rhs[k][v] = T(0);
     }
 
-    // faces, direction by direction
+    // The far face of every line (x = 8, y = 8 or z = 8; 64 per direction) for
+    // all three directions first, into sFb, then per direction the near face
+    // of every cell (512, two per thread) into sF, so that every barrier
+    // interval holds the same number of faces per thread.
+    T* __restrict__ sFb = sF + 8 * NCELL;   // [3][8][64]
+    for (int f = threadIdx.x; f < 3 * TS * TS; f += NT) {
+        const int dir = f >> 6, line = f & 63, a = line & 7, b = line >> 3;
+        int i6[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            i6[k] = dir == 0 ? sRow[(b + HALO) * BX + a + HALO] + TS - 3 + k
+                             : (dir == 1 ? sRow[(b + HALO) * BX + TS - 3 + k + HALO] + a
+                                         : sRow[(TS - 3 + k + HALO) * BX + b + HALO] + a);
+        face_store(e, sW, i6, dir, sFb + dir * 8 * TS * TS + line, TS * TS);
+    }
 #pragma unroll 1
     for (int dir = 0; dir < 3; ++dir) {
-        for (int f = threadIdx.x; f < NFACE; f += NT) {
+        for (int c = threadIdx.x; c < NCELL; c += NT) {
+            const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
             int i6[6];
-            if (dir == 0) {
-                const int fx = f % 9, q = f / 9;
-                const int base = sRow[((q >> 3) + HALO) * BX + (q & 7) + HALO] + fx - 1;
 #pragma unroll
-                for (int k = 0; k < 6; ++k) i6[k] = base + k - 2;
-            } else if (dir == 1) {
-                const int x = f & 7, q = f >> 3, ly = q % 9 - 1, z = q / 9;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) i6[k] = sRow[(z + HALO) * BX + ly + k - 2 + HALO] + x;
-            } else {
-                const int x = f & 7, y = (f >> 3) & 7, lz = (f >> 6) - 1;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) i6[k] = sRow[(lz + k - 2 + HALO) * BX + y + HALO] + x;
-            }
-            T F[8];
-            if constexpr (std::is_same<T, double>::value) {
-                if (dir == 0)
-                    face_fp64<0>(e, sW, i6, F);
-                else if (dir == 1)
-                    face_fp64<1>(e, sW, i6, F);
-                else
-                    face_fp64<2>(e, sW, i6, F);
-#pragma unroll
-                for (int v = 0; v < 8; ++v) sF[v * NFACE + f] = F[v];
-            } else {
-                face_fp32(e, sW, i6, dir, F);
-                const int r1 = dir == 0 ? 3 : (dir == 1 ? 4 : 2);   // first tangential row
-                const int r2 = dir == 0 ? 4 : (dir == 1 ? 2 : 3);   // second tangential row
-                sF[0 * NFACE + f] = F[0];
-                sF[1 * NFACE + f] = F[1];
-                sF[(2 + dir) * NFACE + f] = F[2];
-                sF[r1 * NFACE + f] = F[3];
-                sF[r2 * NFACE + f] = F[4];
-                sF[5 * NFACE + f] = F[5];
-                sF[6 * NFACE + f] = F[6];
-                sF[7 * NFACE + f] = F[7];
-            }
+            for (int k = 0; k < 6; ++k)
+                i6[k] = dir == 0 ? sRow[(z + HALO) * BX + y + HALO] + x - 3 + k
+                                 : (dir == 1 ? sRow[(z + HALO) * BX + y - 3 + k + HALO] + x
+                                             : sRow[(z - 3 + k + HALO) * BX + y + HALO] + x);
+            face_store(e, sW, i6, dir, sF + c, NCELL);
         }
         __syncthreads();
 #pragma unroll
@@ -786,12 +796,16 @@ __device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>&
             const int c = threadIdx.x + k * NT;
             if (c < NCELL) {
                 const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-                const int fl = dir == 0 ? x + 9 * (y + 8 * z) : (dir == 1 ? x + 8 * (y + 9 * z) : c);
+                const int cd = dir == 0 ? x : (dir == 1 ? y : z);
                 const int step = dir == 0 ? 1 : (dir == 1 ? 8 : 64);
+                const int line = dir == 0 ? c >> 3 : (dir == 1 ? x + 8 * z : c & 63);
+                // flux at the cell's far face: the next cell's near face, or the line's far face
+                const T* __restrict__ Fr = cd < TS - 1 ? sF + c + step : sFb + dir * 8 * TS * TS + line;
+                const int sr = cd < TS - 1 ? NCELL : TS * TS;
 #pragma unroll
                 for (int v = 0; v < 7; ++v)
-                    rhs[k][v] -= (sF[v * NFACE + fl + step] - sF[v * NFACE + fl]) * invh;
-                divu[k] += (sF[7 * NFACE + fl + step] - sF[7 * NFACE + fl]) * invh;
+                    rhs[k][v] -= (Fr[v * sr] - sF[v * NCELL + c]) * invh;
+                divu[k] += (Fr[7 * sr] - sF[7 * NCELL + c]) * invh;
             }
         }
         __syncthreads();
@@ -887,8 +901,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
     stage_kernel(const __grid_constant__ Params<T> P, int parity) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sW = reinterpret_cast<T*>(smem_raw);  // [7][NCROSS] primitives, compact layout
-    T* sF = sW + 7 * NCROSS;                 // [8][NFACE] face fluxes + face velocity
-    int* sRow = reinterpret_cast<int*>(sF + 8 * NFACE);  // [BX][BX] row offsets
+    T* sF = sW + 7 * NCROSS;                 // face fluxes + face velocities (NFLUX)
+    int* sRow = reinterpret_cast<int*>(sF + NFLUX);  // [BX][BX] row offsets
     TileCtx<T> c;
     tile_ctx(P, blockIdx.x, parity, c);
     if (P.s.done[c.bw.slot]) return;
@@ -931,7 +945,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sW = reinterpret_cast<T*>(smem_raw);
     T* sF = sW + 7 * NCROSS;
-    int* sRow = reinterpret_cast<int*>(sF + 8 * NFACE);
+    int* sRow = reinterpret_cast<int*>(sF + NFLUX);
     fill_rows(sRow);
     const long long stride = gridDim.x;
     long long t = next_active(P, (long long)blockIdx.x, stride);

@@ -17,7 +17,7 @@ constexpr int BX = TS + 2 * HALO;        // staged box edge (14)
 constexpr int NCELL = TS * TS * TS;      // 512 cells per tile
 constexpr int NSLAB = HALO * TS * TS;    // 192 cells per halo slab
 constexpr int NCROSS = TS * TS * 16 + 4 * NSLAB;  // 1792 staged slots (1664 cells + row padding)
-constexpr int NFACE = (TS + 1) * TS * TS;  // 576 faces per direction
+constexpr int NFLUX = 8 * NCELL + 3 * 8 * TS * TS;  // shared flux values: near faces of one direction + far faces of all three
 constexpr int NT = 256;                  // threads per block (measured better than 192 and 256x2)
 constexpr int CELLS_PER_THREAD = (NCELL + NT - 1) / NT;  // 2
 constexpr int CHUNK_STEPS = 8;           // steps per captured graph (even)
@@ -95,9 +95,10 @@ constexpr double RK_A[3] = {0.0, -2.915492524638791, -0.000000093517376};
 constexpr double RK_B[3] = {0.924574, 0.287713063186749, 0.626538109512740};
 
 // Stage-kernel dynamic shared memory: primitives of the staged cells, face
-// fluxes of one direction, and the staging layout's row-offset table
-// (FP32: 69.4 KB, three blocks per SM; FP64: 137 KB, one).
-constexpr size_t smem_bytes(size_t elem) { return elem * (7 * NCROSS + 8 * NFACE) + sizeof(int) * BX * BX; }
+// fluxes (near faces of one direction, far faces of all three) and the
+// staging layout's row-offset table
+// (FP32: 73.5 KB, three blocks per SM; FP64: 146 KB, one).
+constexpr size_t smem_bytes(size_t elem) { return elem * (7 * NCROSS + NFLUX) + sizeof(int) * BX * BX; }
 
 // Stage-kernel variants: one block per tile, or persistent blocks that issue
 // the next tile's copies before the current tile's update.
