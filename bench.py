@@ -230,6 +230,7 @@ def run_ours(args):
 
     from paper_1705_04374_gb300 import api
     from paper_1705_04374_gb300 import native as nv
+    from paper_1705_04374_gb300 import sharding
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -243,7 +244,7 @@ def run_ours(args):
 
     w, sp = workload(args.precision)
     M = args.samples
-    ids = list(range(rank * M, (rank + 1) * M))
+    ids = sharding.rank_sample_ids(rank, M)
     solver = api.Solver(sp, args.precision)
     group = api.make_group(sp, N_GRID, ids, W.BASE_SEED)
     batch = api.Batch(solver, w.cloud, [group])
@@ -274,14 +275,8 @@ def run_ours(args):
     launches = batch.launches() - launches0
     batch.qoi(allow_bad=True)
     statuses = [q.status for q in group.qoi]
-    t = torch.tensor([ms, cells], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        t[0] = tmax[0]
-    ms_all, cells_all = float(t[0]), float(t[1])
-    value = cells_all / (ms_all / 1e3)
+    ms_all, cells_all = sharding.aggregate(ms, cells, world, device="cuda")
+    value = sharding.job_rate(ms_all / 1e3, cells_all)
 
     # kernel timing: one more solve with CUDA events around every stage kernel
     batch.set_profiling(True)
@@ -334,13 +329,8 @@ def run_ours(args):
         e2e_cells += solve_e2e()
     barrier()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s, e2e_cells], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tm = te.clone()
-        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(te[1:2], op=dist.ReduceOp.SUM)
-        te[0] = tm[0]
-    e2e_value = float(te[1]) / float(te[0])
+    e2e_s_all, e2e_cells_all = sharding.aggregate(e2e_s, e2e_cells, world, device="cuda")
+    e2e_value = sharding.job_rate(e2e_s_all, e2e_cells_all)
 
     if rank != 0:
         if world > 1:

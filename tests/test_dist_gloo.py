@@ -1,0 +1,73 @@
+"""The multi-GPU ensemble's host logic with two gloo ranks on the CPU.
+
+Ranks solve disjoint blocks of sample ids with no data exchange; the job's
+throughput is all ranks' work over the slowest rank's time.  Checked here:
+the blocks are disjoint and cover the ensemble, a sample's random cloud does
+not depend on which rank (or how many ranks) draws it, and the MAX/SUM
+aggregation and throughput formula used by the benchmark."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+import workloads as W  # noqa: E402
+from paper_1705_04374_gb300 import sharding  # noqa: E402
+
+PER_RANK = 5
+WORLD = 2
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, port, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=WORLD)
+    try:
+        from paper_1705_04374_gb300 import api
+        ids = sharding.rank_sample_ids(rank, PER_RANK)
+        cloud = W.cfg2("fp32").cloud
+        clouds = np.stack([api.sample_cloud(cloud, W.BASE_SEED, sid) for sid in ids])
+        gathered = [None] * WORLD
+        dist.all_gather_object(gathered, (ids, clouds))
+        # rank r took (r + 1) s and did 10 (r + 1) units of work
+        elapsed, work = sharding.aggregate(1.0 + rank, 10.0 * (rank + 1), WORLD)
+        if rank == 0:
+            np.save(os.path.join(out_dir, "ids.npy"), np.array([g[0] for g in gathered]))
+            np.save(os.path.join(out_dir, "clouds.npy"), np.stack([g[1] for g in gathered]))
+            np.save(os.path.join(out_dir, "agg.npy"), np.array([elapsed, work, sharding.job_rate(elapsed, work)]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_partition_and_aggregate(tmp_path):
+    mp.start_processes(_rank_main, args=(_free_port(), str(tmp_path)), nprocs=WORLD, start_method="spawn")
+    ids = np.load(tmp_path / "ids.npy")
+    flat = ids.ravel().tolist()
+    assert len(set(flat)) == len(flat) == WORLD * PER_RANK          # disjoint
+    assert sorted(flat) == list(range(WORLD * PER_RANK))            # covering
+    # a sample's cloud is the same whichever rank draws it
+    from paper_1705_04374_gb300 import api
+    cloud = W.cfg2("fp32").cloud
+    single = np.stack([api.sample_cloud(cloud, W.BASE_SEED, sid) for sid in range(WORLD * PER_RANK)])
+    clouds = np.load(tmp_path / "clouds.npy").reshape(single.shape)
+    assert np.array_equal(clouds, single)
+    elapsed, work, rate = np.load(tmp_path / "agg.npy")
+    assert elapsed == 2.0 and work == 30.0 and rate == 15.0
+
+
+def test_single_rank_needs_no_process_group():
+    assert sharding.aggregate(3.0, 7.0, 1) == (3.0, 7.0)
+    assert sharding.rank_sample_ids(0, 3) == [0, 1, 2]
+    assert sharding.rank_sample_ids(2, 3) == [6, 7, 8]
+    with pytest.raises(ValueError):
+        sharding.job_rate(0.0, 1.0)
