@@ -9,7 +9,9 @@ Plain numpy in FP64, following Section 2.4 of the paper:
   - optimal sample numbers for a tolerance, Eq. (M-tol), or a budget,
     Eq. (M-budget), with the keep-computed-samples re-optimisation of step 7;
   - warm-up sample numbers, Eq. (warmup);
-  - the MC-equivalent cost, Eq. (speedup).
+  - the MC-equivalent cost, Eq. (speedup);
+  - the same estimator from per-level summaries (counts, means, squared
+    deviations, fine/coarse co-deviation) that combine across processes.
 
 Input convention: ``pairs[l]`` is an (M_l, 2) array; column 0 holds q_l and
 column 1 holds q_{l-1} evaluated on the same random input (column 1 unused
@@ -138,6 +140,70 @@ def estimate(pairs, W):
     M = [p.shape[0] for p in pairs]
     return dict(alpha=alpha, sigma2=sigma2, cov=cov, sigma_tilde2=st2,
                 mean=ofmlmc_mean(pairs, alpha), eps2=eps2(st2, M), M=M)
+
+
+# ---------------------------------------------------------------------------
+# The same estimator from per-level summaries, for samples spread over several
+# processes (Sec. 2.4: the estimator needs only per-level means, variances and
+# the fine/coarse covariance).  A summary is (n, mean_f, mean_c, m2_f, m2_c,
+# c_fc): pair count, means of the fine and coarse members, their sums of
+# squared deviations and the sum of products of deviations.  Two summaries of
+# disjoint sample sets combine exactly (pairwise update of Chan, Golub and
+# LeVeque, 1979).
+
+def level_moments(p: np.ndarray) -> tuple:
+    """Summary of one level's (M, 2) pairs, two passes."""
+    p = np.asarray(p, dtype=np.float64)
+    n = p.shape[0]
+    if n == 0:
+        return (0, 0.0, 0.0, 0.0, 0.0, 0.0)
+    mf, mc = float(np.mean(p[:, 0])), float(np.mean(p[:, 1]))
+    df, dc = p[:, 0] - mf, p[:, 1] - mc
+    return (n, mf, mc, float(np.sum(df * df)), float(np.sum(dc * dc)), float(np.sum(df * dc)))
+
+
+def merge_moments(a: tuple, b: tuple) -> tuple:
+    """Summary of the union of two disjoint sample sets."""
+    na, nb = a[0], b[0]
+    if na == 0:
+        return tuple(b)
+    if nb == 0:
+        return tuple(a)
+    n = na + nb
+    dfm, dcm = b[1] - a[1], b[2] - a[2]
+    w = na * nb / n
+    return (n, a[1] + dfm * nb / n, a[2] + dcm * nb / n,
+            a[3] + b[3] + dfm * dfm * w, a[4] + b[4] + dcm * dcm * w, a[5] + b[5] + dfm * dcm * w)
+
+
+def estimate_from_moments(moms, W):
+    """estimate() from per-level summaries: the pooled variances of step 3
+    (fine members of pair l with coarse members of pair l+1), the covariances,
+    alpha, sigma~^2 = V[alpha_l q_l - alpha_{l-1} q_{l-1}], the mean and eps^2."""
+    L = len(moms) - 1
+    sigma2 = np.zeros(L + 1)
+    cov = np.zeros(L + 1)
+    for l in range(L + 1):
+        n, mf, _, m2f = moms[l][0], moms[l][1], moms[l][2], moms[l][3]
+        pooled = (n, mf, 0.0, m2f, 0.0, 0.0)
+        if l < L:
+            nx = moms[l + 1]
+            pooled = merge_moments(pooled, (nx[0], nx[2], 0.0, nx[4], 0.0, 0.0))
+        sigma2[l] = pooled[3] / (pooled[0] - 1)
+        cov[l] = moms[l][5] / (n - 1) if l > 0 else 0.0
+    alpha = alpha_optimal(sigma2, cov, W)
+    st2 = np.zeros(L + 1)
+    mean = 0.0
+    for l in range(L + 1):
+        n, mf, mc, m2f, m2c, cfc = moms[l]
+        if l == 0:
+            st2[0] = alpha[0] ** 2 * m2f / (n - 1)
+            mean += alpha[0] * mf
+        else:
+            st2[l] = (alpha[l] ** 2 * m2f + alpha[l - 1] ** 2 * m2c - 2.0 * alpha[l] * alpha[l - 1] * cfc) / (n - 1)
+            mean += alpha[l] * mf - alpha[l - 1] * mc
+    M = [m[0] for m in moms]
+    return dict(alpha=alpha, sigma2=sigma2, cov=cov, sigma_tilde2=st2, mean=mean, eps2=eps2(st2, M), M=M)
 
 
 def optimal_M(sig_t2, W, target: float, mode: str) -> np.ndarray:

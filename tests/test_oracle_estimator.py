@@ -166,3 +166,41 @@ def test_adaptive_loop_reaches_tolerance_on_toy():
 def test_zero_variance_needs_no_samples():
     assert list(E.optimal_M([0.0, 0.0], [1.0, 16.0], 0.1, "tol")) == [0, 0]
     assert list(E.optimal_M([0.0, 0.0], [1.0, 16.0], 1e3, "budget")) == [0, 0]
+
+
+def test_merged_summaries_equal_the_summary_of_the_union():
+    """Pairwise combination of per-process summaries is exact: any split of a
+    sample set, merged in any order, gives the two-pass summary of the whole
+    (including empty parts and single samples)."""
+    rng = np.random.default_rng(7)
+    p = rng.normal(3.0e6, 4.0e5, (37, 2))
+    p[:, 1] = 0.8 * p[:, 0] + rng.normal(0, 1e5, 37)
+    whole = E.level_moments(p)
+    for cuts in ([0, 37], [1, 36], [5, 20, 12], [0, 0, 37], [13, 1, 1, 22]):
+        parts, at = [], 0
+        for c in cuts:
+            parts.append(E.level_moments(p[at:at + c]))
+            at += c
+        for order in (parts, parts[::-1]):
+            acc = (0, 0.0, 0.0, 0.0, 0.0, 0.0)
+            for q in order:
+                acc = E.merge_moments(acc, q)
+            assert acc[0] == whole[0]
+            assert np.allclose(acc[1:], whole[1:], rtol=1e-12, atol=0.0)
+    # two single samples: m2 = (x1 - x2)^2 / 2, the textbook two-point variance
+    m = E.merge_moments(E.level_moments(np.array([[1.0, 4.0]])), E.level_moments(np.array([[3.0, 1.0]])))
+    assert m == (2, 2.0, 2.5, 2.0, 4.5, -3.0)
+
+
+def test_estimate_from_summaries_equals_estimate_from_pairs():
+    """The summary path is the pair path re-associated: same alpha, indicators,
+    mean and error to round-off on a three-level toy."""
+    L, a, b = 2, 0.5, 1.0
+    pairs = Wk.toy_levels([300, 40, 9], L, a, b, seed=11)
+    W = np.array([1.0, 17.0, 272.0])
+    ref = E.estimate(pairs, W)
+    got = E.estimate_from_moments([E.level_moments(p) for p in pairs], W)
+    for k in ("alpha", "sigma2", "cov", "sigma_tilde2"):
+        assert np.allclose(got[k], ref[k], rtol=1e-11, atol=1e-14), k
+    assert abs(got["mean"] - ref["mean"]) <= 1e-12 * abs(ref["mean"])
+    assert abs(got["eps2"] - ref["eps2"]) <= 1e-11 * ref["eps2"]
