@@ -270,6 +270,31 @@ typedef struct {
 int ofm_estimate(int L, const int64_t* M, const double* const* q, const double* W,
                  ofm_estimate_out* out);
 
+/* The same estimator from per-level summaries, for pairs spread over several
+ * processes (one process per GPU).  Section 2.4 needs only per-level means,
+ * pooled variances and the fine/coarse covariance, so each process
+ * summarises its own pairs, the summaries are exchanged (a few hundred
+ * bytes per level) and combined, and every process evaluates Eqs.
+ * (alpha-matvec), (ocv-mlmc) and (ocv-mlmc-err) on the combined summaries.
+ *   ofm_level_moments_of: summary of one level's M pairs (row-major (M, 2):
+ *     fine, coarse member), two passes over the data; M = 0 gives n = 0.
+ *   ofm_merge_moments: summary of the union of two disjoint pair sets
+ *     (pairwise update of Chan, Golub and LeVeque); out may alias a or b.
+ *   ofm_estimate_moments: ofm_estimate from L+1 summaries (n >= 2 each);
+ *     equal to ofm_estimate on the union of the pairs up to round-off.
+ * Errors: OFM_EINVAL for NULL pointers, negative counts, n < 2 or W <= 0;
+ * OFM_ENUMERIC for a singular coefficient system. */
+typedef struct {
+    int64_t n;            /* pairs */
+    double mean_f, mean_c; /* means of the fine and coarse members */
+    double m2_f, m2_c;    /* sums of squared deviations from those means */
+    double c_fc;          /* sum of products of the fine and coarse deviations */
+} ofm_level_moments;
+
+int ofm_level_moments_of(const double* pairs, int64_t M, ofm_level_moments* out);
+int ofm_merge_moments(const ofm_level_moments* a, const ofm_level_moments* b, ofm_level_moments* out);
+int ofm_estimate_moments(int L, const ofm_level_moments* moments, const double* W, ofm_estimate_out* out);
+
 /* Eq. (M-tol) (mode OFM_MODE_TOL, target = tau, constraint eps_OF <= tau) or
  * Eq. (M-budget) (OFM_MODE_BUDGET, target = budget) with the step-7 rule that
  * keeps already computed samples (M_done may be NULL = none). */

@@ -240,6 +240,38 @@ def estimate(pairs: Sequence[np.ndarray], W: Sequence[float]) -> dict:
                 sigma_tilde2=np.array(out.sigma_tilde2[:n]), mean=out.mean, eps2=out.eps2)
 
 
+def level_moments(pairs: np.ndarray) -> tuple:
+    """ofm_level_moments_of on one level's (M, 2) pairs: (n, mean_f, mean_c, m2_f, m2_c, c_fc)."""
+    arr = np.ascontiguousarray(pairs, dtype=np.float64).reshape(-1, 2)
+    out = nv.ofm_level_moments()
+    nv.check(nv.lib().ofm_level_moments_of(arr.ctypes.data_as(C.POINTER(C.c_double)), arr.shape[0], C.byref(out)),
+             "ofm_level_moments_of")
+    return (out.n, out.mean_f, out.mean_c, out.m2_f, out.m2_c, out.c_fc)
+
+
+def _moments_c(m) -> "nv.ofm_level_moments":
+    return nv.ofm_level_moments(int(m[0]), *[float(x) for x in m[1:]])
+
+
+def merge_moments(a, b) -> tuple:
+    """ofm_merge_moments: summary of the union of two disjoint pair sets."""
+    x, y, out = _moments_c(a), _moments_c(b), nv.ofm_level_moments()
+    nv.check(nv.lib().ofm_merge_moments(C.byref(x), C.byref(y), C.byref(out)), "ofm_merge_moments")
+    return (out.n, out.mean_f, out.mean_c, out.m2_f, out.m2_c, out.c_fc)
+
+
+def estimate_moments(moments, W) -> dict:
+    """ofm_estimate_moments on per-level summaries."""
+    L = len(moments) - 1
+    arr = (nv.ofm_level_moments * (L + 1))(*[_moments_c(m) for m in moments])
+    Wc = (C.c_double * (L + 1))(*W)
+    out = nv.ofm_estimate_out()
+    nv.check(nv.lib().ofm_estimate_moments(L, arr, Wc, C.byref(out)), "ofm_estimate_moments")
+    n = L + 1
+    return dict(alpha=np.array(out.alpha[:n]), sigma2=np.array(out.sigma2[:n]), cov=np.array(out.cov[:n]),
+                sigma_tilde2=np.array(out.sigma_tilde2[:n]), mean=out.mean, eps2=out.eps2)
+
+
 def optimal_samples(sigma_tilde2, W, target: float, mode: str = "tol", M_done=None) -> np.ndarray:
     L = len(W) - 1
     s = (C.c_double * (L + 1))(*sigma_tilde2)

@@ -185,6 +185,89 @@ extern "C" int ofm_estimate(int L, const int64_t* M, const double* const* q, con
     return OFM_OK;
 }
 
+// Per-level summaries (Section 2.4 needs only means, pooled variances and the
+// fine/coarse covariance); pairwise combination after Chan, Golub and LeVeque.
+extern "C" int ofm_level_moments_of(const double* pairs, int64_t M, ofm_level_moments* out) {
+    if (!out || M < 0 || (M > 0 && !pairs)) return fail(OFM_EINVAL, "ofm_level_moments_of: bad arguments");
+    std::memset(out, 0, sizeof(*out));
+    out->n = M;
+    if (M == 0) return OFM_OK;
+    double sf = 0.0, sc = 0.0;
+    for (int64_t i = 0; i < M; ++i) {
+        sf += pairs[2 * i];
+        sc += pairs[2 * i + 1];
+    }
+    out->mean_f = sf / (double)M;
+    out->mean_c = sc / (double)M;
+    for (int64_t i = 0; i < M; ++i) {
+        const double df = pairs[2 * i] - out->mean_f, dc = pairs[2 * i + 1] - out->mean_c;
+        out->m2_f += df * df;
+        out->m2_c += dc * dc;
+        out->c_fc += df * dc;
+    }
+    return OFM_OK;
+}
+
+extern "C" int ofm_merge_moments(const ofm_level_moments* a, const ofm_level_moments* b, ofm_level_moments* out) {
+    if (!a || !b || !out || a->n < 0 || b->n < 0) return fail(OFM_EINVAL, "ofm_merge_moments: bad arguments");
+    const ofm_level_moments x = *a, y = *b;
+    if (x.n == 0) {
+        *out = y;
+        return OFM_OK;
+    }
+    if (y.n == 0) {
+        *out = x;
+        return OFM_OK;
+    }
+    const double n = (double)(x.n + y.n);
+    const double df = y.mean_f - x.mean_f, dc = y.mean_c - x.mean_c;
+    const double w = (double)x.n * (double)y.n / n;
+    out->n = x.n + y.n;
+    out->mean_f = x.mean_f + df * (double)y.n / n;
+    out->mean_c = x.mean_c + dc * (double)y.n / n;
+    out->m2_f = x.m2_f + y.m2_f + df * df * w;
+    out->m2_c = x.m2_c + y.m2_c + dc * dc * w;
+    out->c_fc = x.c_fc + y.c_fc + df * dc * w;
+    return OFM_OK;
+}
+
+extern "C" int ofm_estimate_moments(int L, const ofm_level_moments* m, const double* W, ofm_estimate_out* out) {
+    if (L < 0 || L >= OFM_MAX_LEVELS || !m || !W || !out) return fail(OFM_EINVAL, "ofm_estimate_moments: bad arguments");
+    for (int l = 0; l <= L; ++l) {
+        if (m[l].n < 2) return fail(OFM_EINVAL, "ofm_estimate_moments: level %d needs >= 2 samples", l);
+        if (!(W[l] > 0.0)) return fail(OFM_EINVAL, "ofm_estimate_moments: W[%d] must be > 0", l);
+    }
+    std::memset(out, 0, sizeof(*out));
+    for (int l = 0; l <= L; ++l) {
+        // pooled: fine members of pair l with the coarse members of pair l+1
+        ofm_level_moments pooled{m[l].n, m[l].mean_f, 0.0, m[l].m2_f, 0.0, 0.0};
+        if (l < L) {
+            const ofm_level_moments up{m[l + 1].n, m[l + 1].mean_c, 0.0, m[l + 1].m2_c, 0.0, 0.0};
+            ofm_merge_moments(&pooled, &up, &pooled);
+        }
+        out->sigma2[l] = pooled.m2_f / (double)(pooled.n - 1);
+        out->cov[l] = l > 0 ? m[l].c_fc / (double)(m[l].n - 1) : 0.0;
+    }
+    int rc = solve_alpha(L, out->sigma2, out->cov, W, out->alpha);
+    if (rc != OFM_OK) return rc;
+    double mean = 0.0, eps2 = 0.0;
+    for (int l = 0; l <= L; ++l) {
+        const double n1 = (double)(m[l].n - 1), a = out->alpha[l];
+        if (l == 0) {
+            out->sigma_tilde2[0] = a * a * m[0].m2_f / n1;
+            mean += a * m[0].mean_f;
+        } else {
+            const double b = out->alpha[l - 1];
+            out->sigma_tilde2[l] = (a * a * m[l].m2_f + b * b * m[l].m2_c - 2.0 * a * b * m[l].c_fc) / n1;
+            mean += a * m[l].mean_f - b * m[l].mean_c;
+        }
+        eps2 += out->sigma_tilde2[l] / (double)m[l].n;
+    }
+    out->mean = mean;
+    out->eps2 = eps2;
+    return OFM_OK;
+}
+
 extern "C" int ofm_warmup_samples(int L, const double* W, int64_t* M_out) {
     if (L < 0 || L >= OFM_MAX_LEVELS || !W || !M_out) return fail(OFM_EINVAL, "ofm_warmup_samples: bad arguments");
     for (int l = 0; l <= L; ++l) {

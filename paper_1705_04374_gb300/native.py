@@ -56,6 +56,11 @@ class ofm_group(C.Structure):
                 ("qoi_out", C.POINTER(ofm_qoi)), ("sensor_hist", C.POINTER(C.c_double))]
 
 
+class ofm_level_moments(C.Structure):
+    _fields_ = [("n", C.c_int64), ("mean_f", C.c_double), ("mean_c", C.c_double), ("m2_f", C.c_double),
+                ("m2_c", C.c_double), ("c_fc", C.c_double)]
+
+
 class ofm_estimate_out(C.Structure):
     _fields_ = [("alpha", C.c_double * OFM_MAX_LEVELS), ("sigma2", C.c_double * OFM_MAX_LEVELS),
                 ("cov", C.c_double * OFM_MAX_LEVELS), ("sigma_tilde2", C.c_double * OFM_MAX_LEVELS),
@@ -125,6 +130,9 @@ SIGNATURES = {
     "ofm_cloud_features": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp]),
     "ofm_estimate": (C.c_int, [C.c_int, _P(C.c_int64), _P(_P(C.c_double)), _P(C.c_double),
                                _P(ofm_estimate_out)]),
+    "ofm_level_moments_of": (C.c_int, [_P(C.c_double), C.c_int64, _P(ofm_level_moments)]),
+    "ofm_merge_moments": (C.c_int, [_P(ofm_level_moments), _P(ofm_level_moments), _P(ofm_level_moments)]),
+    "ofm_estimate_moments": (C.c_int, [C.c_int, _P(ofm_level_moments), _P(C.c_double), _P(ofm_estimate_out)]),
     "ofm_optimal_samples": (C.c_int, [C.c_int, _P(C.c_double), _P(C.c_double), _P(C.c_int64),
                                       C.c_double, C.c_int, _P(C.c_int64)]),
     "ofm_warmup_samples": (C.c_int, [C.c_int, _P(C.c_double), _P(C.c_int64)]),

@@ -71,3 +71,32 @@ def test_single_rank_needs_no_process_group():
     assert sharding.rank_sample_ids(2, 3) == [6, 7, 8]
     with pytest.raises(ValueError):
         sharding.job_rate(0.0, 1.0)
+
+
+def _estimator_rank(rank, port, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=WORLD)
+    try:
+        pairs = W.toy_levels([301, 41, 9], 2, 0.5, 1.0, seed=23)
+        local = [p[list(sharding.pair_shard(len(p), rank, WORLD))] for p in pairs]
+        est = sharding.distributed_estimate(local, [1.0, 17.0, 272.0], WORLD)
+        np.save(os.path.join(out_dir, f"est{rank}.npy"),
+                np.concatenate([est["alpha"], est["sigma2"], est["cov"], est["sigma_tilde2"], [est["mean"], est["eps2"]]]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_estimate_equals_single_process(tmp_path):
+    """Each rank summarises its level-stratified share of the pairs; after one
+    all-gather of the summaries both ranks hold the single-process estimate."""
+    mp.start_processes(_estimator_rank, args=(_free_port(), str(tmp_path)), nprocs=WORLD, start_method="spawn")
+    from paper_1705_04374_gb300 import api
+    pairs = W.toy_levels([301, 41, 9], 2, 0.5, 1.0, seed=23)
+    ref = api.estimate(pairs, [1.0, 17.0, 272.0])
+    want = np.concatenate([ref["alpha"], ref["sigma2"], ref["cov"], ref["sigma_tilde2"], [ref["mean"], ref["eps2"]]])
+    e0, e1 = np.load(tmp_path / "est0.npy"), np.load(tmp_path / "est1.npy")
+    assert np.array_equal(e0, e1)                      # every rank holds the same numbers
+    assert np.allclose(e0, want, rtol=1e-11, atol=1e-14)
+    shards = [set(sharding.pair_shard(41, r, WORLD)) for r in range(WORLD)]
+    assert not (shards[0] & shards[1]) and shards[0] | shards[1] == set(range(41))

@@ -121,3 +121,28 @@ def test_surrogate_cv_host_matches_oracle():
 def test_zero_variance_needs_no_samples_in_the_library():
     assert list(api.optimal_samples([0.0, 0.0], [1.0, 16.0], 0.1, "tol", [5, 3])) == [5, 3]
     assert list(api.optimal_samples([0.0, 0.0], [1.0, 16.0], 1e3, "budget")) == [0, 0]
+
+
+def test_summary_estimator_matches_oracle_and_pair_estimator():
+    """ofm_level_moments_of / ofm_merge_moments / ofm_estimate_moments against
+    the oracle's summaries and against ofm_estimate on the union of the pairs."""
+    L, a, b = 2, 0.5, 1.0
+    pairs = W.toy_levels([300, 40, 9], L, a, b, seed=11)
+    Wl = [1.0, 17.0, 272.0]
+    for p in pairs:
+        got, ref = api.level_moments(p), E.level_moments(p)
+        assert got[0] == ref[0] and np.allclose(got[1:], ref[1:], rtol=1e-13, atol=0)
+        half = len(p) // 3
+        m = api.merge_moments(api.level_moments(p[:half]), api.level_moments(p[half:]))
+        r = E.merge_moments(E.level_moments(p[:half]), E.level_moments(p[half:]))
+        assert m[0] == r[0] and np.allclose(m[1:], r[1:], rtol=1e-13, atol=0)
+    assert api.level_moments(np.zeros((0, 2))) == (0, 0.0, 0.0, 0.0, 0.0, 0.0)
+    est = api.estimate_moments([api.level_moments(p) for p in pairs], Wl)
+    ref = E.estimate_from_moments([E.level_moments(p) for p in pairs], Wl)
+    whole = api.estimate(pairs, Wl)
+    for k in ("alpha", "sigma2", "cov", "sigma_tilde2"):
+        assert np.allclose(est[k], ref[k], rtol=1e-12, atol=1e-15), k
+        assert np.allclose(est[k], whole[k], rtol=1e-11, atol=1e-14), k
+    assert abs(est["mean"] - whole["mean"]) <= 1e-12 * abs(whole["mean"])
+    with pytest.raises(nv.OfmError):
+        api.estimate_moments([api.level_moments(pairs[0][:1])], [1.0])   # one sample: no variance
