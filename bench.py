@@ -337,6 +337,9 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
+    # the FP pipes' multiply-add rate measured now, at the clocks this GPU runs at
+    probe_tflops = api.probe_fma_tflops(args.precision)
+
     # roofline of the dominant kernel (the RK-stage kernel)
     flops = load_json(FLOPS_FILE) or {}
     f_stage = flops.get("flops_per_cell_stage")
@@ -370,7 +373,9 @@ def run_ours(args):
                     else "nominal FP64 of the part",
                     "kernel": "stage_kernel (fused WENO5 + HLLC + 2N update)",
                     "per_launch": {"cells": cells_per_launch, "flops_per_cell": f_stage,
-                                   "avg_ms": avg_stage_ms, "launches_timed": stage_n}}
+                                   "avg_ms": avg_stage_ms, "launches_timed": stage_n},
+                    "fma_probe": {"tflops": probe_tflops, "frac": achieved_tflops / probe_tflops,
+                                  "what": "ofm_probe_fma_tflops: register multiply-add chains, measured in this run"}}
     else:
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_gbs / hbm_peak, "traffic": traffic,

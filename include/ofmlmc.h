@@ -348,6 +348,15 @@ typedef struct {
 int ofm_run(ofm_solver* solver, const ofm_cloud_params* cloud, const ofm_run_config* config, double* pairs_out,
             uint64_t* ids_out, int64_t pairs_capacity, ofm_run_result* result, void* stream);
 
+/* Measured multiply-add rate [TFLOP/s, a multiply-add = 2 flops] of the
+ * current device's FP32 (precision OFM_FP32) or FP64 (OFM_FP64) pipes:
+ * eight independent register chains per thread, 8 blocks of 256 threads per
+ * SM, 3 untimed and 10 timed launches on the given stream, CUDA events.  The
+ * ceiling that the stencil kernels' ALU roofline is read against, measured at
+ * the clocks the GPU runs at.  The paper has no counterpart.  Errors:
+ * OFM_EINVAL for a bad precision or NULL tflops, OFM_ECUDA. */
+int ofm_probe_fma_tflops(int precision, double* tflops, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Surrogate control variate (not in the paper).  An MLP s(x) of the cloud
  * geometry x predicts the finest-level QoI; it enters the estimator only as

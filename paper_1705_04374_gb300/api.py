@@ -283,6 +283,14 @@ def optimal_samples(sigma_tilde2, W, target: float, mode: str = "tol", M_done=No
     return np.array(out[:])
 
 
+def probe_fma_tflops(precision: str = "fp32") -> float:
+    """ofm_probe_fma_tflops on the current device and torch stream."""
+    out = C.c_double()
+    prec = nv.OFM_FP32 if precision == "fp32" else nv.OFM_FP64
+    nv.check(nv.lib().ofm_probe_fma_tflops(prec, C.byref(out), _torch_stream_ptr()), "ofm_probe_fma_tflops")
+    return out.value
+
+
 def warmup_samples(W) -> np.ndarray:
     L = len(W) - 1
     Wc = (C.c_double * (L + 1))(*W)

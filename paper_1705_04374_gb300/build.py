@@ -2,7 +2,7 @@
 
 Translation units compiled in parallel: the solver kernels once per
 precision (``kernels_fp64.cu`` without FMA contraction, ``kernels_fp32.cu``),
-the device-facing C ABI (``solver.cu``, ``solver_static.cu``) with nvcc, and
+the device-facing C ABI (``solver.cu``, ``solver_static.cu``, ``probe.cu``) with nvcc, and
 ``host.cpp`` (sampler, estimator, errors) with g++ -ffp-contract=off.  The CUDA runtime is linked
 statically so the library has no run-time dependency beyond the driver.
 """
@@ -31,6 +31,7 @@ SOURCES = {
     "solver_static.o": _NV + ["-c", os.path.join(CSRC, "solver_static.cu")],
     "mlp.o": _NV + ["-c", os.path.join(CSRC, "mlp.cu")],
     "run.o": _NV + ["-c", os.path.join(CSRC, "run.cu")],
+    "probe.o": _NV + ["-c", os.path.join(CSRC, "probe.cu")],
     "host.o": ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I", INCLUDE,
                "-c", os.path.join(CSRC, "host.cpp")],
 }

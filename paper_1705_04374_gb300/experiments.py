@@ -363,15 +363,54 @@ def cmd_cfg5(quick):
     return out
 
 
+# ------------------------------------------------------------------------------ epsval
+
+def cmd_epsval(quick, min_samples=16):
+    """The error estimate of Eq. (ocv-mlmc-err) against the empirical error:
+    R independent seeded OF-MLMC runs (FP32, 3 levels 16^3/32^3/64^3, 20
+    bubbles, centre sensor peak pressure) to a tolerance tau, and one
+    reference run to tau/3 with another seed, every level starting from at
+    least min_samples pairs.  The empirical mean squared error of the R
+    estimates about the reference, less the reference's own estimated
+    variance, should match the mean of the estimated eps^2."""
+    w = W.tiny(16, 20)
+    cloud = W.cloud_uniform(20)
+    levels = [16, 32, 64]
+    R = 4 if quick else 8
+    tau = 6.0e5 if quick else 3.0e5
+    s32 = api.Solver(w.solver, "fp32")
+    ref, _, _ = api.run_ofmlmc(s32, cloud, levels, target=tau / 3.0, qoi=QOI, seed=W.BASE_SEED + 1000,
+                               max_iterations=8, max_cell_steps=6e10, capacity=1 << 18, min_samples=min_samples)
+    ests, eps2s, gsec, Ms, capped = [], [], [], [], []
+    for r in range(R):
+        res, _, _ = api.run_ofmlmc(s32, cloud, levels, target=tau, qoi=QOI, seed=W.BASE_SEED + 1 + r,
+                                   max_iterations=8, max_cell_steps=2e10, min_samples=min_samples)
+        capped.append(res["capped"])
+        ests.append(res["est"]["mean"])
+        eps2s.append(res["est"]["eps2"])
+        gsec.append(res["gpu_seconds"])
+        Ms.append(list(res["M"]))
+    ests = np.array(ests)
+    mse = float(np.mean((ests - ref["est"]["mean"]) ** 2))
+    return dict(experiment="epsval", levels=levels, bubbles=20, qoi="centre sensor peak pressure [Pa]", tau=tau,
+                repeats=R, min_samples=min_samples, capped=capped, reference=dict(mean=ref["est"]["mean"], eps=math.sqrt(ref["est"]["eps2"]), M=list(ref["M"]),
+                                          gpu_seconds=ref["gpu_seconds"], capped=ref["capped"]),
+                estimates=ests.tolist(), eps_estimated=[math.sqrt(e) for e in eps2s], M=Ms, gpu_seconds=gsec,
+                empirical_rmse=math.sqrt(mse), mean_estimated_eps=math.sqrt(float(np.mean(eps2s))),
+                empirical_rmse_less_reference=math.sqrt(max(mse - ref["est"]["eps2"], 0.0)))
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["uneven3", "surrogate", "rmse", "cfg5"])
+    ap.add_argument("what", choices=["uneven3", "surrogate", "rmse", "cfg5", "epsval"])
     ap.add_argument("--quick", action="store_true")
+    ap.add_argument("--min-samples", type=int, default=16, help="epsval: pairs every level starts with")
     a = ap.parse_args()
     torch.cuda.set_device(0)
-    fn = {"uneven3": cmd_uneven3, "surrogate": cmd_surrogate, "rmse": cmd_rmse, "cfg5": cmd_cfg5}[a.what]
-    print(json.dumps(fn(a.quick)), flush=True)
+    fn = {"uneven3": cmd_uneven3, "surrogate": cmd_surrogate, "rmse": cmd_rmse, "cfg5": cmd_cfg5,
+          "epsval": cmd_epsval}[a.what]
+    print(json.dumps(fn(a.quick, a.min_samples) if a.what == "epsval" else fn(a.quick)), flush=True)
 
 
 if __name__ == "__main__":
