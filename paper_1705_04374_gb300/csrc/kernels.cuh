@@ -554,6 +554,92 @@ __device__ __forceinline__ void face_fp32(const Eos<float>& e, const float* __re
     hllc_frame(wl, wr, GL, PiL, GR, PiR, F);
 }
 
+// Single precision: R consecutive faces of one line.  idx[i] (i = 0..R+4)
+// is the staged index of the line's cell j - 3 + i, where face j (between
+// cells j - 1 and j) is the run's first face.  Each variable's R + 5 staged
+// values are loaded once, and each of the cells j - 1 .. j + R - 1 forms its
+// three smoothness indicators once for the left state of the face to its
+// right and the right state of the face to its left (the operations of
+// weno5_pair, in its order).  vo as in face_fp32.  Face r's 8 values go to
+// dst[r * step + v * stride] in the staged variable order.
+template <int R>
+__device__ __forceinline__ void face_run_fp32(const Eos<float>& e, const float* __restrict__ sW,
+                                              const int (&idx)[R + 5], const int (&vo)[7], int dir,
+                                              float* __restrict__ dst, int step, int stride) {
+    float wl[R][7], wr[R][7];
+    const float eps4 = 4.0f * e.eps;
+    const float k = 13.0f / 3.0f;
+#pragma unroll
+    for (int v = 0; v < 7; ++v) {
+        const float* P = sW + vo[v];
+        float p[R + 5];
+#pragma unroll
+        for (int i = 0; i < R + 5; ++i) p[i] = P[idx[i]];
+        float d[R + 4], D[R + 3], sv[R + 3];
+#pragma unroll
+        for (int i = 0; i < R + 4; ++i) d[i] = p[i + 1] - p[i];
+#pragma unroll
+        for (int i = 0; i < R + 3; ++i) {
+            D[i] = d[i + 1] - d[i];
+            sv[i] = fmaf(k * D[i], D[i], eps4);
+        }
+#pragma unroll
+        for (int j = 2; j <= R + 2; ++j) {   // cell idx[j]
+            const float tl = fmaf(2.0f, d[j - 1], D[j - 2]);
+            const float tm = d[j - 1] + d[j];
+            const float th = fmaf(-2.0f, d[j], D[j]);
+            float El = fmaf(tl, tl, sv[j - 2]), Em = fmaf(tm, tm, sv[j - 1]), Eh = fmaf(th, th, sv[j]);
+            El *= El;
+            Em *= Em;
+            Eh *= Eh;
+            const float X = Em * Eh, Y6 = 6.0f * (El * Eh), Z = El * Em;
+            if (j <= R + 1) {   // left state of face j - 2 of the run
+                const float hd = 0.5f * d[j];
+                const float a2 = 3.0f * Z;
+                const float q0 = fmaf(D[j - 2], 1.0f / 3.0f, 0.5f * d[j - 1]);
+                const float q1 = fmaf(D[j - 1], -1.0f / 6.0f, hd);
+                const float q2 = fmaf(D[j], -1.0f / 6.0f, hd);
+                wl[j - 2][v] = p[j] + fmaf(X, q0, fmaf(Y6, q1, a2 * q2)) / (X + Y6 + a2);
+            }
+            if (j >= 3) {       // right state of face j - 3 of the run
+                const float hd = 0.5f * d[j - 1];
+                const float a2 = 3.0f * X;
+                const float q0 = fmaf(D[j], 1.0f / 3.0f, -0.5f * d[j]);
+                const float q1 = fmaf(D[j - 1], -1.0f / 6.0f, -hd);
+                const float q2 = fmaf(D[j - 2], -1.0f / 6.0f, -hd);
+                wr[j - 3][v] = p[j] + fmaf(Z, q0, fmaf(Y6, q1, a2 * q2)) / (Z + Y6 + a2);
+            }
+        }
+    }
+    const int r1 = dir == 0 ? 3 : (dir == 1 ? 4 : 2);
+    const int r2 = dir == 0 ? 4 : (dir == 1 ? 2 : 3);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float GL, PiL, GR, PiR;
+        if (!admissible_f(e, wl[r], GL, PiL)) {
+#pragma unroll
+            for (int v = 0; v < 7; ++v) wl[r][v] = sW[vo[v] + idx[r + 2]];
+            closure(e, wl[r][6], GL, PiL);
+        }
+        if (!admissible_f(e, wr[r], GR, PiR)) {
+#pragma unroll
+            for (int v = 0; v < 7; ++v) wr[r][v] = sW[vo[v] + idx[r + 3]];
+            closure(e, wr[r][6], GR, PiR);
+        }
+        float F[8];
+        hllc_frame(wl[r], wr[r], GL, PiL, GR, PiR, F);
+        float* o = dst + r * step;
+        o[0] = F[0];
+        o[stride] = F[1];
+        o[(2 + dir) * stride] = F[2];
+        o[r1 * stride] = F[3];
+        o[r2 * stride] = F[4];
+        o[5 * stride] = F[5];
+        o[6 * stride] = F[6];
+        o[7 * stride] = F[7];
+    }
+}
+
 // One face in double precision, in the FP64 reference's operation order.
 template <int DIR>
 __device__ __forceinline__ void face_fp64(const Eos<double>& e, const double* __restrict__ sW, const int* i6,
@@ -754,8 +840,8 @@ __device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>&
                                            T* __restrict__ sF, const int* __restrict__ sRow, TileRhs<T>& R) {
     const T invh = T(1) / (T)c.bw.G->h;  // 1/h, formed as the FP64 reference forms it
     const Eos<T> e = P.eos;
-    T (&rhs)[CELLS_PER_THREAD][7] = R.rhs;
     T (&divu)[CELLS_PER_THREAD] = R.divu;
+    T (&rhs)[CELLS_PER_THREAD][7] = R.rhs;
 #pragma unroll
     for (int k = 0; k < CELLS_PER_THREAD; ++k) {
         divu[k] = T(0);
@@ -780,7 +866,36 @@ __device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>&
     }
 #pragma unroll 1
     for (int dir = 0; dir < 3; ++dir) {
-        for (int c = threadIdx.x; c < NCELL; c += NT) {
+        bool by_runs = false;
+        if constexpr (std::is_same<T, float>::value && NEAR_RUN > 1) {
+            // runs of NEAR_RUN consecutive near faces along each line, one per thread
+            constexpr int NR = TS / NEAR_RUN;   // runs per line
+            for (int t = threadIdx.x; t < TS * TS * NR; t += NT) {
+                int a, b, j;   // the line's two other coordinates and the run's first face
+                if (dir == 0) {
+                    j = NEAR_RUN * (t % NR);
+                    a = (t / NR) & 7;
+                    b = (t / NR) >> 3;
+                } else {
+                    a = t & 7;
+                    j = NEAR_RUN * ((t >> 3) % NR);
+                    b = (t >> 3) / NR;
+                }
+                int idx[NEAR_RUN + 5];
+#pragma unroll
+                for (int i = 0; i < NEAR_RUN + 5; ++i)
+                    idx[i] = dir == 0 ? sRow[(b + HALO) * BX + a + HALO] + j - 3 + i
+                                      : (dir == 1 ? sRow[(b + HALO) * BX + j - 3 + i + HALO] + a
+                                                  : sRow[(j - 3 + i + HALO) * BX + b + HALO] + a);
+                const int r1 = dir == 0 ? 3 : (dir == 1 ? 4 : 2);
+                const int r2 = dir == 0 ? 4 : (dir == 1 ? 2 : 3);
+                const int vo[7] = {0, NCROSS, (2 + dir) * NCROSS, r1 * NCROSS, r2 * NCROSS, 5 * NCROSS, 6 * NCROSS};
+                const int c0 = dir == 0 ? j + 8 * a + 64 * b : (dir == 1 ? a + 8 * j + 64 * b : a + 8 * b + 64 * j);
+                face_run_fp32<NEAR_RUN>(e, sW, idx, vo, dir, sF + c0, dir == 0 ? 1 : (dir == 1 ? 8 : 64), NCELL);
+            }
+            by_runs = true;
+        }
+        for (int c = by_runs ? NCELL : threadIdx.x; c < NCELL; c += NT) {
             const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
             int i6[6];
 #pragma unroll

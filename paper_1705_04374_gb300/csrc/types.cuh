@@ -20,6 +20,7 @@ constexpr int NCROSS = TS * TS * 16 + 4 * NSLAB;  // 1792 staged slots (1664 cel
 constexpr int NFLUX = 8 * NCELL + 3 * 8 * TS * TS;  // shared flux values: near faces of one direction + far faces of all three
 constexpr int NT = 256;                  // threads per block (measured better than 192 and 256x2)
 constexpr int CELLS_PER_THREAD = (NCELL + NT - 1) / NT;  // 2
+constexpr int NEAR_RUN = 2;             // FP32: consecutive near faces per thread task (1: one face per task)
 constexpr int CHUNK_STEPS = 8;           // steps per captured graph (even)
 
 
