@@ -554,11 +554,15 @@ void orc_totals(const orc_grid* g, const double* Q, double* tot) {
 /*   H(x) = max_b 1/2 (1 - tanh((|x - x_b| - r_b)/h)),                   */
 /*   alpha2 = clamp(H, 1e-6, 1 - 1e-6),                                  */
 /*   a1r1 = (1 - alpha2) rho1,  a2r2 = alpha2 rho2,                      */
-/*   p = p_liq + (p_gas - p_liq) H,  u = 0,  E = Gamma p + Pi.           */
+/*   p = p_l(x) + (p_gas - p_l(x)) H,  u = 0,  E = Gamma p + Pi,          */
+/* with the liquid pressure p_l = p_liq, or, with the cloud ramp of       */
+/* Sec. 3.1 (r0 > 0, distance r from the domain centre): p_l = p_cloud    */
+/* for r <= r0 and p_liq + (p_cloud - p_liq) r0 / r beyond (the pressure  */
+/* field of a liquid at rest around a sphere, continuous at r0).          */
 /* Cell centres x_c = (i + 1/2) h.  bub = nb x (x, y, z, r).             */
 /* ------------------------------------------------------------------ */
 void orc_init_cloud(const orc_grid* g, const double* bub, int nb, double rho1, double rho2,
-                    double p_gas, double p_liq, double* Q) {
+                    double p_gas, double p_liq, double p_cloud, double r0, double* Q) {
     const long n = cells(g);
     for (int k = 0; k < g->nz; ++k)
         for (int j = 0; j < g->ny; ++j)
@@ -579,7 +583,13 @@ void orc_init_cloud(const orc_grid* g, const double* bub, int nb, double rho1, d
                 w[0] = (1.0 - a2) * rho1;
                 w[1] = a2 * rho2;
                 w[2] = w[3] = w[4] = 0.0;
-                w[5] = p_liq + (p_gas - p_liq) * H;
+                double pl = p_liq;
+                if (r0 > 0.0) {
+                    double cx = x - 0.5 * g->nx * g->h, cy = y - 0.5 * g->ny * g->h, cz = z - 0.5 * g->nz * g->h;
+                    double r = sqrt(cx * cx + cy * cy + cz * cz);
+                    pl = r <= r0 ? p_cloud : p_liq + (p_cloud - p_liq) * r0 / r;
+                }
+                w[5] = pl + (p_gas - pl) * H;
                 w[6] = a2;
                 orc_cons_from_prim(g, w, q);
                 for (int v = 0; v < NV; ++v) Q[v * n + c] = q[v];

@@ -64,7 +64,7 @@ def _lib(count: bool = False) -> C.CDLL:
         lib.orc_max_speed.restype = C.c_double
         lib.orc_totals.argtypes = [G, _D, _D]
         lib.orc_init_cloud.argtypes = [G, _D, C.c_int, C.c_double, C.c_double, C.c_double,
-                                       C.c_double, _D]
+                                       C.c_double, C.c_double, C.c_double, _D]
         lib.orc_sensor_cell_count.argtypes = [G, _D]
         lib.orc_sensor_cell_count.restype = C.c_int
         lib.orc_solve.argtypes = [G, _D, C.c_double, C.c_int, C.c_int, _D, C.c_int, _D,
@@ -214,7 +214,8 @@ def init_cloud(sp, N: int, bubbles_si: np.ndarray) -> np.ndarray:
     nb = b.size // 4
     Q = np.zeros((NV, N, N, N))
     _lib().orc_init_cloud(C.byref(g), _p(b) if nb else None, nb, sp.rho0[0] / RHO_REF,
-                          sp.rho0[1] / RHO_REF, sp.p_gas / u.p_ref, sp.p_liq / u.p_ref, _p(Q))
+                          sp.rho0[1] / RHO_REF, sp.p_gas / u.p_ref, sp.p_liq / u.p_ref,
+                          sp.p_cloud / u.p_ref, sp.ramp_radius / sp.domain_L, _p(Q))
     return Q
 
 

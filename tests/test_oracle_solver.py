@@ -407,3 +407,47 @@ def test_splitmix64_reference_values():
     assert g.next_u64() == 0xE220A8397B1DCDAF
     assert g.next_u64() == 0x6E789E6AA1B965F4
     assert g.next_u64() == 0x06C45D188009454F
+
+
+def test_cloud_pressure_ramp_is_harmonic_and_continuous():
+    """Sec. 3.1 ramp (no bubbles, so the field is the liquid's alone): the
+    cloud pressure inside r0, continuity across r0, a harmonic field beyond it
+    (a liquid at rest around a sphere: the 7-point Laplacian is a small
+    fraction of the size |b| h^2 / r^3 of the second differences of b/r, which
+    a linear or 1/r^2 profile would not give), rising monotonically towards
+    p_inf."""
+    sp = W.solver_paper500()
+    N = 64
+    g = S.grid_from_params(sp, N)
+    Q = S.init_cloud(sp, N, np.zeros((0, 4)))
+    p = S.cons_to_prim(g, Q.reshape(7, -1))[5].reshape(N, N, N) * sp.p_liq     # Pa
+    h = sp.domain_L / N
+    x = (np.arange(N) + 0.5) * h - 0.5 * sp.domain_L
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    r0 = sp.ramp_radius
+    inside = r <= r0
+    assert np.allclose(p[inside], sp.p_cloud, rtol=1e-12, atol=0)
+    # continuity: cells within half a cell of r0 differ from p_cloud by at most one cell's rise
+    rise = (sp.p_liq - sp.p_cloud) * h / r0        # |dp/dr| at r0 times h
+    near = np.abs(r - r0) < 0.5 * h
+    assert near.any() and np.max(np.abs(p[near] - sp.p_cloud)) <= rise
+    # harmonic beyond r0 (all 7 stencil cells in the ramp region)
+    core = (slice(1, -1),) * 3
+    d2 = [p[2:, 1:-1, 1:-1] - 2 * p[core] + p[:-2, 1:-1, 1:-1],
+          p[1:-1, 2:, 1:-1] - 2 * p[core] + p[1:-1, :-2, 1:-1],
+          p[1:-1, 1:-1, 2:] - 2 * p[core] + p[1:-1, 1:-1, :-2]]
+    lap = d2[0] + d2[1] + d2[2]
+    b = abs(sp.p_cloud - sp.p_liq) * r0
+    ramp = r[core] > r0 + 2 * h
+    scale = b * h * h / r[core] ** 3
+    assert np.all(np.abs(lap[ramp]) <= 0.05 * scale[ramp])
+    assert np.max(np.abs(d2[0][ramp]) / scale[ramp]) > 0.5     # the scale is the size of the terms
+    # monotone rise with r, below p_inf
+    order = np.argsort(r[core][ramp])
+    pr = p[core][ramp][order]
+    assert np.all(np.diff(pr) >= -1e-9 * sp.p_liq) and pr[-1] < sp.p_liq and pr[0] > sp.p_cloud
+    # off by default: the uniform liquid pressure
+    q0 = S.init_cloud(W.SolverParams(), N, np.zeros((0, 4)))
+    p0 = S.cons_to_prim(g, q0.reshape(7, -1))[5]
+    assert np.allclose(p0, 1.0, rtol=1e-13)

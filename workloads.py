@@ -58,6 +58,11 @@ class SolverParams:
     domain_L: float = DOMAIN_L
     sensors: Tuple[Tuple[float, float, float, float], ...] = ()   # (x, y, z, r) in m
     n_out_times: int = 65
+    # Cloud pressure ramp (Sec. 3.1; off when ramp_radius == 0): the liquid is at
+    # p_cloud within ramp_radius of the domain centre and rises as 1/r towards
+    # p_liq beyond it.
+    p_cloud: float = 0.0
+    ramp_radius: float = 0.0
 
 
 def centre_sensor() -> Tuple[Tuple[float, float, float, float], ...]:
@@ -117,6 +122,13 @@ def cfg3() -> Workload:
     """3-level OF-MLMC 32^3/64^3/128^3, M = 1024/128/16, 50 bubbles, FP32 stencil."""
     return Workload("cfg3-3level-50bubbles", cloud_uniform(50),
                     SolverParams(sensors=centre_sensor()), (32, 64, 128), (1024, 128, 16), "fp32")
+
+
+def solver_paper500(**kw) -> SolverParams:
+    """Section 3.1 pressures: bubbles and the liquid around them at 0.5 MPa, rising
+    from 1 mm beyond the 20 mm cloud surface towards p_inf = 10 MPa."""
+    return SolverParams(p_gas=0.5e6, p_liq=1.0e7, p_cloud=0.5e6, ramp_radius=0.021,
+                        sensors=centre_sensor(), **kw)
 
 
 def tiny(n: int = 16, n_bubbles: int = 4, samples: int = 2) -> Workload:
