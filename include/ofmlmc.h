@@ -92,6 +92,12 @@ typedef struct {
     int n_sensors;    /* <= OFM_MAX_SENSORS */
     double sensors[OFM_MAX_SENSORS][4]; /* centre (x, y, z) and radius [m], Eq. (sensor) */
     int n_out_times;  /* sensor history samples on t_k = k t_end/(n_out_times-1) */
+    /* Cloud pressure ramp of the initial condition (Sec. 3.1): with ramp_radius > 0
+     * [m] the liquid is at p_cloud [Pa] within ramp_radius of the domain centre and
+     * at p_liq + (p_cloud - p_liq) ramp_radius / r at distance r beyond it (the
+     * pressure of a liquid at rest around a sphere); 0 = uniform p_liq. */
+    double p_cloud;
+    double ramp_radius;
 } ofm_solver_config;
 
 /* Per-sample quantities of interest (Section 3.2). */

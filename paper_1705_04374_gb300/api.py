@@ -21,6 +21,8 @@ def solver_config(sp, precision: str = "fp64") -> nv.ofm_solver_config:
     c.rho0[0], c.rho0[1] = sp.rho0
     c.p_gas = sp.p_gas
     c.p_liq = sp.p_liq
+    c.p_cloud = getattr(sp, "p_cloud", 0.0)
+    c.ramp_radius = getattr(sp, "ramp_radius", 0.0)
     c.cfl = sp.cfl
     c.t_end = sp.t_end
     c.weno_eps = sp.weno_eps

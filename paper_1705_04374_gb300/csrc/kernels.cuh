@@ -373,8 +373,11 @@ __global__ void reset_kernel(const __grid_constant__ Params<T> P) {
 
 // Initial condition (reading of the smoothing): H = max_b 1/2 (1 - tanh((|x - x_b| - r_b)/h))
 // = 1/2 (1 - tanh(min_b (|x - x_b| - r_b)/h)); alpha2 = clamp(H, 1e-6, 1 - 1e-6);
-// a1r1 = (1 - alpha2) rho1; a2r2 = alpha2 rho2; p = p_liq + (p_gas - p_liq) H;
-// u = 0; E = Gamma p + Pi.  Evaluated in FP64, stored in T.
+// a1r1 = (1 - alpha2) rho1; a2r2 = alpha2 rho2; p = p_l + (p_gas - p_l) H with the
+// liquid pressure p_l = p_liq, or with the cloud ramp of Sec. 3.1 (ramp_r0 > 0, r the
+// distance from the domain centre) p_l = p_cloud for r <= ramp_r0 and
+// p_liq + (p_cloud - p_liq) ramp_r0 / r beyond; u = 0; E = Gamma p + Pi.
+// Evaluated in FP64, stored in T.
 template <typename T>
 __global__ void __launch_bounds__(NT) ic_kernel(const __grid_constant__ Params<T> P) {
     BlockWork<T> bw;
@@ -399,7 +402,13 @@ __global__ void __launch_bounds__(NT) ic_kernel(const __grid_constant__ Params<T
         const double H = P.nb > 0 ? 0.5 * (1.0 - tanh(m / h)) : 0.0;
         const double a2 = fmin(fmax(H, 1e-6), 1.0 - 1e-6);
         const double a1 = 1.0 - a2;
-        const double p = P.p_liq + (P.p_gas - P.p_liq) * H;
+        double pl = P.p_liq;
+        if (P.ramp_r0 > 0.0) {
+            const double cx = xc - 0.5 * N * h, cy = yc - 0.5 * N * h, cz = zc - 0.5 * N * h;
+            const double r = sqrt(cx * cx + cy * cy + cz * cz);
+            pl = r <= P.ramp_r0 ? P.p_cloud : P.p_liq + (P.p_cloud - P.p_liq) * P.ramp_r0 / r;
+        }
+        const double p = pl + (P.p_gas - pl) * H;
         const size_t gi = ((size_t)z * N + y) * N + x;
         Q[0 * n3 + gi] = (T)(a1 * P.rho1);
         Q[1 * n3 + gi] = (T)(a2 * P.rho2);

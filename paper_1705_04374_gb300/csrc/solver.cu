@@ -194,6 +194,8 @@ void fill_params(ofm_batch* b, Params<T>& P) {
     P.cfl = c.cfl;
     P.p_gas = c.p_gas / pref;
     P.p_liq = c.p_liq / pref;
+    P.p_cloud = c.p_cloud / pref;
+    P.ramp_r0 = c.ramp_radius / c.domain_L;
     P.rho1 = c.rho0[0] / 1000.0;
     P.rho2 = c.rho0[1] / 1000.0;
 }
@@ -273,7 +275,8 @@ extern "C" int ofm_solver_create(ofm_solver** out, const ofm_solver_config* c) {
     *out = nullptr;
     if (!(c->gamma[0] > 1.0) || !(c->gamma[1] > 1.0) || !(c->pc[0] >= 0.0) || !(c->pc[1] >= 0.0) ||
         !(c->rho0[0] > 0.0) || !(c->rho0[1] > 0.0) || !(c->p_liq > 0.0) || !(c->p_gas > 0.0) ||
-        !(c->cfl > 0.0) || !(c->t_end > 0.0) || !(c->weno_eps > 0.0) || !(c->domain_L > 0.0))
+        !(c->cfl > 0.0) || !(c->t_end > 0.0) || !(c->weno_eps > 0.0) || !(c->domain_L > 0.0) ||
+        !(c->ramp_radius >= 0.0) || !(c->p_cloud >= 0.0) || (c->ramp_radius > 0.0 && !(c->p_cloud > 0.0)))
         return fail(OFM_EINVAL, "ofm_solver_create: non-physical configuration");
     if (c->precision != OFM_FP64 && c->precision != OFM_FP32)
         return fail(OFM_EINVAL, "ofm_solver_create: precision must be OFM_FP64 or OFM_FP32");

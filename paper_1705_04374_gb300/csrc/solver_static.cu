@@ -156,6 +156,8 @@ void static_params(const ofm_solver* s, int N, int M, int nb, unsigned char* ws,
     P.cfl = c.cfl;
     P.p_gas = c.p_gas / pref;
     P.p_liq = c.p_liq / pref;
+    P.p_cloud = c.p_cloud / pref;
+    P.ramp_r0 = c.ramp_radius / c.domain_L;
     P.rho1 = c.rho0[0] / 1000.0;
     P.rho2 = c.rho0[1] / 1000.0;
 }

@@ -89,6 +89,7 @@ struct Params {
     double rkA[3], rkB[3];
     int bc, nb, n_sens, n_out, max_steps, total_slots;
     double t_end, cfl, p_gas, p_liq, rho1, rho2;
+    double p_cloud, ramp_r0;   // cloud pressure ramp of the initial condition (ramp_r0 = 0: off)
 };
 
 // Low-storage TVD RK3 (Gottlieb & Shu 1998), Williamson 2N form.

@@ -39,7 +39,7 @@ class ofm_solver_config(C.Structure):
                 ("t_end", C.c_double), ("weno_eps", C.c_double), ("domain_L", C.c_double),
                 ("precision", C.c_int), ("bc", C.c_int), ("max_steps", C.c_int),
                 ("n_sensors", C.c_int), ("sensors", (C.c_double * 4) * OFM_MAX_SENSORS),
-                ("n_out_times", C.c_int)]
+                ("n_out_times", C.c_int), ("p_cloud", C.c_double), ("ramp_radius", C.c_double)]
 
 
 class ofm_qoi(C.Structure):

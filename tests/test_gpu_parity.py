@@ -84,6 +84,29 @@ def test_one_step_fp64_relative_l1(N):
     b.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_STEP_FP64), ("fp32", TOL_STEP_FP32)])
+def test_one_step_with_cloud_pressure_ramp(precision, tol):
+    """Sec. 3.1 pressures (bubbles and the liquid around them at 0.5 MPa, 1/r rise to
+    10 MPa from 1 mm beyond the cloud surface) on 24^3: the initial state and one
+    step against the oracle."""
+    N = 24
+    sp = W.solver_paper500()
+    cloud = W.cloud_uniform(20)
+    ids = [0, 3]
+    s, groups, b = gpu_batch(sp, precision, [(N, ids)], cloud)
+    b.init()
+    for i, sid in enumerate(ids):
+        bub = ocloud.sample_cloud(cloud, W.BASE_SEED, sid)
+        q0 = osolver.init_cloud(sp, N, bub)
+        assert np.all(rel_l1(b.state(0, i), q0) <= (1e-13 if precision == "fp64" else 1e-7)), sid
+    b.run(1)
+    for i, sid in enumerate(ids):
+        bub = ocloud.sample_cloud(cloud, W.BASE_SEED, sid)
+        r = rel_l1(b.state(0, i), oracle_one_step(sp, N, bub))
+        assert np.all(r <= tol), (sid, r)
+    b.close()
+
+
 def test_one_step_fp64_periodic_smooth_field():
     N = 16
     sp = W.with_solver(W.tiny(N), bc=1).solver

@@ -81,6 +81,9 @@ def test_invalid_arguments_are_rejected_on_the_host():
     h = C.c_void_p()
     assert L.ofm_solver_create(C.byref(h), C.byref(cfg)) == nv.OFM_EINVAL
     assert b"non-physical" in L.ofm_last_error()
+    cfg = api.solver_config(W.SolverParams(), "fp64")
+    cfg.ramp_radius, cfg.p_cloud = 0.02, 0.0          # a ramp needs a cloud pressure
+    assert L.ofm_solver_create(C.byref(h), C.byref(cfg)) == nv.OFM_EINVAL
     # estimator needs two samples per level
     with pytest.raises(nv.OfmError):
         api.estimate([np.zeros((1, 2)), np.zeros((5, 2))], [1.0, 2.0])
