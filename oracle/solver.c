@@ -492,6 +492,7 @@ enum { ORC_ST_NONFINITE = 1, ORC_ST_NEGATIVE = 2, ORC_ST_MAXSTEPS = 4 };
 
 typedef struct {
     double smax;
+    double cmax;   /* max over cells of the mixture sound speed */
     double pmax;
     long argmax;
     int status;
@@ -500,6 +501,7 @@ typedef struct {
 static void reduce_state(const orc_grid* g, const double* Q, orc_reduce* r) {
     const long n = cells(g);
     r->smax = 0.0;
+    r->cmax = 0.0;
     r->pmax = -INFINITY;
     r->argmax = 0;
     r->status = 0;
@@ -520,6 +522,7 @@ static void reduce_state(const orc_grid* g, const double* Q, orc_reduce* r) {
         double s = fmax(fabs(w[2]) + c0, fmax(fabs(w[3]) + c0, fabs(w[4]) + c0));
         FL(1 + 3 + 1);
         if (s > r->smax) r->smax = s;
+        if (c0 > r->cmax) r->cmax = c0;
         if (w[5] > r->pmax) {
             r->pmax = w[5];
             r->argmax = c;
@@ -640,7 +643,11 @@ static double sensor_value(const orc_grid* g, const double* Q, const long* idx, 
 /*   exactly on t_end);                                                  */
 /*   p_peak = max over t = 0 and every step of max_cells p, first index; */
 /*   sensor histories on t_k = k t_end/(K-1), linear in time between     */
-/*   steps; sensor peaks = max over steps of the sensor value.           */
+/*   steps; sensor peaks = max over steps of the sensor value;           */
+/*   c_max = max over t = 0 and every step of max_cells c (Sec. 3.2 maximum */
+/*   speed of sound); gas-fraction sensors (Sec. 3.2 alpha sensors): mean   */
+/*   alpha2 over the same cells as the pressure sensor, its value at t = 0, */
+/*   its minimum over the recorded steps and the first time of that minimum. */
 /* ------------------------------------------------------------------ */
 typedef struct {
     double p_peak;
@@ -652,7 +659,18 @@ typedef struct {
     int n_steps;
     int status;
     double t_final;
+    double c_max;
+    double sensor_alpha0[8];
+    double sensor_alpha_min[8];
+    double sensor_alpha_min_t[8];
 } orc_qoi;
+
+static double sensor_alpha(const orc_grid* g, const double* Q, const long* idx, int m) {
+    const long n = cells(g);
+    double acc = 0.0;
+    for (int a = 0; a < m; ++a) acc += Q[6 * n + idx[a]];
+    return m > 0 ? acc / m : NAN;
+}
 
 int orc_solve(const orc_grid* g, double* Q, double t_end, int max_steps, int n_sensors,
               const double* sensors, int n_out, double* hist, orc_qoi* out) {
@@ -672,10 +690,13 @@ int orc_solve(const orc_grid* g, double* Q, double t_end, int max_steps, int n_s
     out->peak_index = r.argmax;
     out->p_peak_t = 0.0;
     orc_totals(g, Q, out->totals0);
+    out->c_max = r.cmax;
     for (int s = 0; s < n_sensors; ++s) {
         sv_old[s] = sensor_value(g, Q, sidx[s], scount[s]);
         out->sensor_peak[s] = sv_old[s];
         if (hist && n_out > 0) hist[s * n_out + 0] = sv_old[s];
+        out->sensor_alpha0[s] = out->sensor_alpha_min[s] = sensor_alpha(g, Q, sidx[s], scount[s]);
+        out->sensor_alpha_min_t[s] = 0.0;
     }
     double t = 0.0;
     int nsteps = 0;
@@ -701,9 +722,15 @@ int orc_solve(const orc_grid* g, double* Q, double t_end, int max_steps, int n_s
             out->peak_index = r.argmax;
             out->p_peak_t = t_new;
         }
+        if (r.cmax > out->c_max) out->c_max = r.cmax;
         for (int s = 0; s < n_sensors; ++s) {
             sv_new[s] = sensor_value(g, Q, sidx[s], scount[s]);
             if (sv_new[s] > out->sensor_peak[s]) out->sensor_peak[s] = sv_new[s];
+            double a = sensor_alpha(g, Q, sidx[s], scount[s]);
+            if (a < out->sensor_alpha_min[s]) {
+                out->sensor_alpha_min[s] = a;
+                out->sensor_alpha_min_t[s] = t_new;
+            }
         }
         if (hist && n_out > 1) {
             while (kout < n_out) {

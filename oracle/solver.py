@@ -35,7 +35,8 @@ class OrcQoi(C.Structure):
     _fields_ = [("p_peak", C.c_double), ("peak_index", C.c_long), ("p_peak_t", C.c_double),
                 ("sensor_peak", C.c_double * 8), ("totals0", C.c_double * 6),
                 ("totals_end", C.c_double * 6), ("n_steps", C.c_int), ("status", C.c_int),
-                ("t_final", C.c_double)]
+                ("t_final", C.c_double), ("c_max", C.c_double), ("sensor_alpha0", C.c_double * 8),
+                ("sensor_alpha_min", C.c_double * 8), ("sensor_alpha_min_t", C.c_double * 8)]
 
 
 _LIBS = {}
@@ -229,7 +230,10 @@ def solve(sp, N: int, bubbles_si: np.ndarray, count_flops: bool = False,
 
     QoIs in SI: p_peak [Pa], its cell-centre location [m] and time [s], its
     distance from the domain centre [m], sensor peaks [Pa], conserved totals
-    (non-dimensional), step count and status bits.
+    (non-dimensional), step count and status bits; c_max [m/s], the maximum
+    over time of the maximum mixture sound speed; per sensor the gas fraction
+    (mean alpha2 over the sensor's cells) at t = 0, its minimum over time and
+    the first time of that minimum [s].
     """
     g = grid_from_params(sp, N)
     u = Units(sp.domain_L, sp.p_liq)
@@ -261,5 +265,9 @@ def solve(sp, N: int, bubbles_si: np.ndarray, count_flops: bool = False,
         n_steps=out.n_steps,
         status=out.status,
         t_final=out.t_final * u.t_ref,
+        c_max=out.c_max * u.u_ref,
+        sensor_alpha0=np.array(out.sensor_alpha0[:ns]),
+        sensor_alpha_min=np.array(out.sensor_alpha_min[:ns]),
+        sensor_alpha_min_t=np.array(out.sensor_alpha_min_t[:ns]) * u.t_ref,
     )
     return q, hist[: ns * n_out].reshape(ns, n_out) * u.p_ref, Q

@@ -363,6 +363,27 @@ def test_solve_time_loop_and_qois():
     assert 25 <= q["n_steps"] <= 40
 
 
+def test_sound_speed_and_gas_fraction_sensor_qois():
+    """Liquid at rest (no bubbles): the state stays uniform, so c_max is the
+    textbook stiffened-gas sound speed sqrt(gamma (p + p_c) / rho) of the
+    liquid (the 1e-6 gas fraction moves it by < 1e-5) and the gas-fraction
+    sensors read 1e-6 throughout, with the minimum at t = 0.  One centred
+    bubble at 10 MPa: its gas is compressed, so the gas fraction of a sensor
+    ball around it falls, its minimum coming later than t = 0."""
+    sp = W.SolverParams(sensors=((0.05, 0.05, 0.05, 0.02), W.centre_sensor()[0]))
+    q, _, _ = S.solve(sp, 16, np.zeros((0, 4)))
+    c_text = math.sqrt(sp.gamma[0] * (sp.p_liq + sp.pc[0]) / sp.rho0[0])
+    assert abs(q["c_max"] / c_text - 1) < 1e-5
+    assert np.allclose(q["sensor_alpha0"], 1e-6, rtol=1e-9)
+    assert np.allclose(q["sensor_alpha_min"], 1e-6, rtol=1e-9)
+    assert np.all(q["sensor_alpha_min_t"] == 0.0)
+    q, _, _ = S.solve(sp, 16, np.array([[0.05, 0.05, 0.05, 0.015]]))
+    assert q["status"] == 0
+    assert q["sensor_alpha0"][0] > 0.1 and q["sensor_alpha_min"][0] < q["sensor_alpha0"][0]
+    assert 0.0 < q["sensor_alpha_min_t"][0] <= q["t_final"]
+    assert q["c_max"] >= c_text * (1 - 1e-5)
+
+
 # ---------------------------------------------------------------- initial condition and sampler
 
 def test_initial_condition_far_and_inside():
