@@ -113,6 +113,10 @@ typedef struct {
     double t_final;         /* [s] */
     int n_steps;
     int status;             /* OFM_ST_* bits */
+    double c_max;           /* max over time (t = 0 and every step) of max over cells of the mixture sound speed [m/s] */
+    double sensor_alpha0[OFM_MAX_SENSORS];      /* gas-fraction sensors: mean alpha2 over each sensor's cells at t = 0 */
+    double sensor_alpha_min[OFM_MAX_SENSORS];   /* their minimum over time (t = 0 and every step) */
+    double sensor_alpha_min_t[OFM_MAX_SENSORS]; /* the first time of that minimum [s] (gas-volume collapse time) */
 } ofm_qoi;
 
 /* One group of samples on one grid. */

@@ -105,7 +105,10 @@ class Group:
                             p_peak_t=q.p_peak_t, p_peak_dist=q.p_peak_dist,
                             sensor_peak=np.array(q.sensor_peak[:n_sensors]),
                             totals0=np.array(q.totals0[:]), totals_end=np.array(q.totals_end[:]),
-                            t_final=q.t_final, n_steps=q.n_steps, status=q.status))
+                            t_final=q.t_final, n_steps=q.n_steps, status=q.status, c_max=q.c_max,
+                            sensor_alpha0=np.array(q.sensor_alpha0[:n_sensors]),
+                            sensor_alpha_min=np.array(q.sensor_alpha_min[:n_sensors]),
+                            sensor_alpha_min_t=np.array(q.sensor_alpha_min_t[:n_sensors])))
         return out
 
 

@@ -269,20 +269,22 @@ __device__ __forceinline__ bool decode_block(const Params<T>& P, long long b, Bl
 // Per-cell health / speed / pressure reduction and its block combine
 // --------------------------------------------------------------------------
 struct Red {
-    double smax, pmax;
+    double smax, cmax, pmax;
     long long idx;
     int status;
 };
 
 __device__ __forceinline__ void red_init(Red& r) {
     r.smax = 0.0;
+    r.cmax = 0.0;
     r.pmax = -INFINITY;
     r.idx = 0x7fffffffffffffffLL;
     r.status = 0;
 }
 
-__device__ __forceinline__ void red_merge(Red& a, double smax, double pmax, long long idx, int st) {
+__device__ __forceinline__ void red_merge(Red& a, double smax, double cmax, double pmax, long long idx, int st) {
     a.smax = fmax(a.smax, smax);
+    a.cmax = fmax(a.cmax, cmax);
     if (pmax > a.pmax || (pmax == a.pmax && idx < a.idx)) {
         a.pmax = pmax;
         a.idx = idx;
@@ -290,8 +292,38 @@ __device__ __forceinline__ void red_merge(Red& a, double smax, double pmax, long
     a.status |= st;
 }
 
+// A thread's running record in the stencil precision: maxima and the first
+// maximiser need no wider type (conversion to double is exact and monotone),
+// and single-precision compares avoid the slow FP64 pipe in the cell loop.
 template <typename T>
-__device__ __forceinline__ void red_cell(const Eos<T>& e, const T* q, long long gi, Red& r) {
+struct RedT {
+    T smax, cmax, pmax;
+    long long idx;
+    int status;
+};
+
+template <typename T>
+__device__ __forceinline__ void red_init(RedT<T>& r) {
+    r.smax = T(0);
+    r.cmax = T(0);
+    r.pmax = -INFINITY;
+    r.idx = 0x7fffffffffffffffLL;
+    r.status = 0;
+}
+
+template <typename T>
+__device__ __forceinline__ Red red_widen(const RedT<T>& r) {
+    Red o;
+    o.smax = (double)r.smax;
+    o.cmax = (double)r.cmax;
+    o.pmax = (double)r.pmax;
+    o.idx = r.idx;
+    o.status = r.status;
+    return o;
+}
+
+template <typename T>
+__device__ __forceinline__ void red_cell(const Eos<T>& e, const T* q, long long gi, RedT<T>& r) {
     T w[7];
     cons2prim(e, q, w);
     int bad = 0;
@@ -308,9 +340,10 @@ __device__ __forceinline__ void red_cell(const Eos<T>& e, const T* q, long long 
     if (bad) return;
     const T c = sqrt(c2);
     const T s = fmax(fabs(w[2]) + c, fmax(fabs(w[3]) + c, fabs(w[4]) + c));
-    r.smax = fmax(r.smax, (double)s);
-    if ((double)w[5] > r.pmax) {   // cells arrive in increasing linear index
-        r.pmax = (double)w[5];
+    r.smax = fmax(r.smax, s);
+    r.cmax = fmax(r.cmax, c);
+    if (w[5] > r.pmax) {   // cells arrive in increasing linear index
+        r.pmax = w[5];
         r.idx = gi;
     }
 }
@@ -323,17 +356,20 @@ __device__ void block_reduce_write(Red r, Partial* out) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const double sm = __shfl_down_sync(0xffffffffu, r.smax, off);
+        const double cm = __shfl_down_sync(0xffffffffu, r.cmax, off);
         const double pm = __shfl_down_sync(0xffffffffu, r.pmax, off);
         const long long ix = __shfl_down_sync(0xffffffffu, r.idx, off);
         const int st = __shfl_down_sync(0xffffffffu, r.status, off);
-        red_merge(r, sm, pm, ix, st);
+        red_merge(r, sm, cm, pm, ix, st);
     }
     if (lane == 0) sred[warp] = r;
     __syncthreads();
     if (threadIdx.x == 0) {
         Red a = sred[0];
-        for (int w = 1; w < NT / 32; ++w) red_merge(a, sred[w].smax, sred[w].pmax, sred[w].idx, sred[w].status);
+        for (int w = 1; w < NT / 32; ++w)
+            red_merge(a, sred[w].smax, sred[w].cmax, sred[w].pmax, sred[w].idx, sred[w].status);
         out->smax = a.smax;
+        out->cmax = a.cmax;
         out->pmax = a.pmax;
         out->idx = a.idx;
         out->status = a.status;
@@ -429,7 +465,7 @@ __global__ void __launch_bounds__(NT) reduce_kernel(const __grid_constant__ Para
     const int N = G.N;
     const size_t n3 = (size_t)N * N * N;
     const T* Q = (const T*)(parity ? G.QB : G.QA) + (size_t)bw.s_local * 7 * n3;
-    Red r;
+    RedT<T> r;
     red_init(r);
     for (int c = threadIdx.x; c < NCELL; c += NT) {
         const int x = bw.x0 + (c & 7), y = bw.y0 + ((c >> 3) & 7), z = bw.z0 + (c >> 6);
@@ -440,7 +476,7 @@ __global__ void __launch_bounds__(NT) reduce_kernel(const __grid_constant__ Para
         red_cell(P.eos, q, (long long)gi, r);
     }
     const long long tile = blockIdx.x - G.block0 - (long long)bw.s_local * G.tps;
-    block_reduce_write(r, G.part + (size_t)bw.s_local * G.tps + tile);
+    block_reduce_write(red_widen(r), G.part + (size_t)bw.s_local * G.tps + tile);
 }
 
 // Both WENO5 face states of the face between the cells holding c0 and p1,
@@ -971,7 +1007,7 @@ __device__ __forceinline__ void tile_update(const Params<T>& P, const TileCtx<T>
     T (&rhs)[CELLS_PER_THREAD][7] = R.rhs;
     T (&divu)[CELLS_PER_THREAD] = R.divu;
     const T A = (T)P.rkA[STAGE], B = (T)P.rkB[STAGE];
-    Red red;
+    RedT<T> red;
     red_init(red);
 #pragma unroll
     for (int k = 0; k < CELLS_PER_THREAD; ++k) {
@@ -1002,7 +1038,7 @@ __device__ __forceinline__ void tile_update(const Params<T>& P, const TileCtx<T>
     }
     if (STAGE == 2) {
         const long long tile = tile_index - G.block0 - (long long)bw.s_local * G.tps;
-        block_reduce_write(red, G.part + (size_t)bw.s_local * G.tps + tile);
+        block_reduce_write(red_widen(red), G.part + (size_t)bw.s_local * G.tps + tile);
     }
 }
 
@@ -1129,32 +1165,37 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ P
     Red r;
     red_init(r);
     for (int t = threadIdx.x; t < G.tps; t += blockDim.x)
-        red_merge(r, part[t].smax, part[t].pmax, part[t].idx, part[t].status);
+        red_merge(r, part[t].smax, part[t].cmax, part[t].pmax, part[t].idx, part[t].status);
     __shared__ Red sred[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const double sm = __shfl_down_sync(0xffffffffu, r.smax, off);
+        const double cm = __shfl_down_sync(0xffffffffu, r.cmax, off);
         const double pm = __shfl_down_sync(0xffffffffu, r.pmax, off);
         const long long ix = __shfl_down_sync(0xffffffffu, r.idx, off);
         const int st = __shfl_down_sync(0xffffffffu, r.status, off);
-        red_merge(r, sm, pm, ix, st);
+        red_merge(r, sm, cm, pm, ix, st);
     }
     if (lane == 0) sred[warp] = r;
     __syncthreads();
     if (threadIdx.x != 0) return;
     for (int w = 1; w < (int)(blockDim.x / 32); ++w)
-        red_merge(r, sred[w].smax, sred[w].pmax, sred[w].idx, sred[w].status);
+        red_merge(r, sred[w].smax, sred[w].cmax, sred[w].pmax, sred[w].idx, sred[w].status);
 
     const int N = G.N;
     const size_t n3 = (size_t)N * N * N;
     const T* Q = (const T*)(parity ? G.QB : G.QA) + (size_t)s_local * 7 * n3;
-    double sv[OFM_MAX_SENSORS];
+    double sv[OFM_MAX_SENSORS], sa[OFM_MAX_SENSORS];
     for (int s = 0; s < P.n_sens; ++s) {
-        double acc = 0.0;
+        double acc = 0.0, acca = 0.0;
         const int a0 = G.sens_off[s], a1 = G.sens_off[s + 1];
-        for (int a = a0; a < a1; ++a) acc += cell_pressure(P.eos, Q, n3, G.sens_cells[a]);
+        for (int a = a0; a < a1; ++a) {
+            acc += cell_pressure(P.eos, Q, n3, G.sens_cells[a]);
+            acca += (double)Q[6 * n3 + G.sens_cells[a]];
+        }
         sv[s] = a1 > a0 ? acc / (double)(a1 - a0) : NAN;
+        sa[s] = a1 > a0 ? acca / (double)(a1 - a0) : NAN;
     }
     DevQoi& q = P.s.qoi[slot];
     double* old = P.s.sens_old + (size_t)slot * OFM_MAX_SENSORS;
@@ -1166,7 +1207,10 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ P
         q.p_peak = r.pmax;
         q.peak_index = r.idx;
         q.p_peak_t = 0.0;
+        q.c_max = r.cmax;
         for (int s = 0; s < P.n_sens; ++s) {
+            q.sensor_alpha0[s] = q.sensor_alpha_min[s] = sa[s];
+            q.sensor_alpha_min_t[s] = 0.0;
             q.sensor_peak[s] = sv[s];
             old[s] = sv[s];
             if (P.n_out > 0) hist[s * P.n_out] = sv[s];
@@ -1184,8 +1228,14 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ P
             q.peak_index = r.idx;
             q.p_peak_t = t;
         }
-        for (int s = 0; s < P.n_sens; ++s)
+        if (r.cmax > q.c_max) q.c_max = r.cmax;
+        for (int s = 0; s < P.n_sens; ++s) {
             if (sv[s] > q.sensor_peak[s]) q.sensor_peak[s] = sv[s];
+            if (sa[s] < q.sensor_alpha_min[s]) {
+                q.sensor_alpha_min[s] = sa[s];
+                q.sensor_alpha_min_t[s] = t;
+            }
+        }
         if (P.n_out > 1) {
             int k = P.s.kout[slot];
             while (k < P.n_out) {

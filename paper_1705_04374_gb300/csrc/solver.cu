@@ -631,6 +631,12 @@ extern "C" int ofm_batch_qoi(ofm_batch* b) {
                                           (o.p_peak_xyz[2] - cx) * (o.p_peak_xyz[2] - cx));
                 o.p_peak_t = d.p_peak_t * s->t_ref;
                 for (int k2 = 0; k2 < c.n_sensors; ++k2) o.sensor_peak[k2] = d.sensor_peak[k2] * s->p_ref;
+                o.c_max = d.c_max * s->u_ref;
+                for (int k2 = 0; k2 < c.n_sensors; ++k2) {
+                    o.sensor_alpha0[k2] = d.sensor_alpha0[k2];
+                    o.sensor_alpha_min[k2] = d.sensor_alpha_min[k2];
+                    o.sensor_alpha_min_t[k2] = d.sensor_alpha_min_t[k2] * s->t_ref;
+                }
                 for (int v = 0; v < 6; ++v) {
                     o.totals0[v] = d.totals0[v];
                     o.totals_end[v] = d.totals_end[v];

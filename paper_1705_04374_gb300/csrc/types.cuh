@@ -34,6 +34,7 @@ struct Eos {
 
 struct Partial {          // per-tile reduction of one state
     double smax;          // max over cells of max_d(|u_d| + c)
+    double cmax;          // max over cells of the mixture sound speed c
     double pmax;          // max pressure
     long long idx;        // first linear index of pmax
     int status;           // OR of health bits
@@ -50,6 +51,10 @@ struct DevQoi {           // per-sample record, non-dimensional
     double t_final;
     int n_steps;
     int status;
+    double c_max;                              // max over time of the max sound speed
+    double sensor_alpha0[OFM_MAX_SENSORS];     // sensor gas fractions at t = 0
+    double sensor_alpha_min[OFM_MAX_SENSORS];  // their minimum over time
+    double sensor_alpha_min_t[OFM_MAX_SENSORS];  // and the first time of it
 };
 
 struct GroupDev {

@@ -47,7 +47,9 @@ class ofm_qoi(C.Structure):
                 ("p_peak_dist", C.c_double), ("peak_index", C.c_int64),
                 ("sensor_peak", C.c_double * OFM_MAX_SENSORS), ("totals0", C.c_double * 6),
                 ("totals_end", C.c_double * 6), ("t_final", C.c_double), ("n_steps", C.c_int),
-                ("status", C.c_int)]
+                ("status", C.c_int), ("c_max", C.c_double), ("sensor_alpha0", C.c_double * OFM_MAX_SENSORS),
+                ("sensor_alpha_min", C.c_double * OFM_MAX_SENSORS),
+                ("sensor_alpha_min_t", C.c_double * OFM_MAX_SENSORS)]
 
 
 class ofm_group(C.Structure):

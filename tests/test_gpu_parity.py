@@ -158,6 +158,10 @@ def compare_qoi(qg, hg, qo, ho, tol, n_sens):
     assert np.all(np.abs(qg["sensor_peak"] - qo["sensor_peak"]) <= tol * np.abs(qo["sensor_peak"]))
     assert np.allclose(qg["totals_end"], qo["totals_end"], rtol=tol, atol=1e-14)
     assert np.allclose(qg["totals0"], qo["totals0"], rtol=1e-13, atol=1e-15)
+    assert abs(qg["c_max"] - qo["c_max"]) <= tol * qo["c_max"]
+    assert np.allclose(qg["sensor_alpha0"], qo["sensor_alpha0"], rtol=1e-13, atol=0)
+    assert np.allclose(qg["sensor_alpha_min"], qo["sensor_alpha_min"], rtol=tol, atol=0)
+    assert np.allclose(qg["sensor_alpha_min_t"], qo["sensor_alpha_min_t"], rtol=tol, atol=0)
     if hg is not None and ho.size:
         assert np.all(np.abs(hg - ho) <= tol * np.abs(ho))
 
@@ -195,7 +199,7 @@ def test_fp32_qoi_errors_are_small_and_stated(capsys):
     b.qoi()
     got = groups[0].qoi_dicts(len(sp.sensors))
     ref = oracle_qois(sp, 32, w.cloud, ids)
-    errs = {"p_peak": [], "sensor_peak": [], "hist": []}
+    errs = {"p_peak": [], "sensor_peak": [], "hist": [], "c_max": [], "alpha_min": []}
     for i in range(3):
         qo, ho = ref[i]
         qg = got[i]
@@ -203,12 +207,17 @@ def test_fp32_qoi_errors_are_small_and_stated(capsys):
         errs["p_peak"].append(abs(qg["p_peak"] - qo["p_peak"]) / qo["p_peak"])
         errs["sensor_peak"].append(float(np.max(np.abs(qg["sensor_peak"] - qo["sensor_peak"]) / qo["sensor_peak"])))
         errs["hist"].append(float(np.max(np.abs(groups[0].hist[i] - ho)) / np.max(np.abs(ho))))
+        errs["c_max"].append(abs(qg["c_max"] - qo["c_max"]) / qo["c_max"])
+        errs["alpha_min"].append(float(np.max(np.abs(qg["sensor_alpha_min"] - qo["sensor_alpha_min"])
+                                              / qo["sensor_alpha_min"])))
     with capsys.disabled():
         print("\nFP32 vs FP64 oracle, relative QoI errors (32^3, 4 bubbles):",
               {k: f"{max(v):.2e}" for k, v in errs.items()})
     assert max(errs["p_peak"]) < 1e-3
     assert max(errs["sensor_peak"]) < 1e-2
     assert max(errs["hist"]) < 1e-2
+    assert max(errs["c_max"]) < 1e-3
+    assert max(errs["alpha_min"]) < 1e-3
     b.close()
 
 

@@ -34,7 +34,7 @@ def test_library_exports_every_declared_function():
 
 def test_struct_sizes_match_header_layout():
     assert C.sizeof(nv.ofm_bubble) == 32
-    assert C.sizeof(nv.ofm_qoi) == 8 * (1 + 3 + 1 + 1 + 1 + 8 + 6 + 6 + 1) + 8
+    assert C.sizeof(nv.ofm_qoi) == 8 * (1 + 3 + 1 + 1 + 1 + 8 + 6 + 6 + 1) + 8 + 8 * (1 + 8 + 8 + 8)
     assert C.sizeof(nv.ofm_estimate_out) == 8 * (4 * 16 + 2)
 
 
@@ -149,3 +149,36 @@ def test_summary_estimator_matches_oracle_and_pair_estimator():
     assert abs(est["mean"] - whole["mean"]) <= 1e-12 * abs(whole["mean"])
     with pytest.raises(nv.OfmError):
         api.estimate_moments([api.level_moments(pairs[0][:1])], [1.0])   # one sample: no variance
+
+
+def test_binding_structs_match_the_c_header(tmp_path):
+    """Every struct of the ABI: size and field offsets from a C compiler reading
+    include/ofmlmc.h equal the ctypes layout of the binding."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {name: cls for name, cls in vars(nv).items()
+               if isinstance(cls, type) and issubclass(cls, C.Structure) and name.startswith("ofm_")}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ofmlmc.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f in cls._fields_:
+            lines.append(f'printf("{name} {f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {}
+    for line in out:
+        if line:
+            name, field, val = line.split()
+            got[(name, field)] = int(val)
+    assert len(structs) >= 8
+    for name, cls in structs.items():
+        assert got[(name, "size")] == C.sizeof(cls), name
+        for f in cls._fields_:
+            assert got[(name, f[0])] == getattr(cls, f[0]).offset, (name, f[0])
