@@ -198,14 +198,17 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- GPU arm
 
-def config_dict(precision, world):
-    return {"workload": "ensemble: 512 seeded clouds x 20 bubbles, 64^3, to t_end (~120 RK3 steps), "
+def config_dict(precision, world, samples=M_SAMPLES):
+    es = 4 if precision == "fp32" else 8
+    buf_gb = samples * 7 * N_GRID ** 3 * es / 1e9
+    return {"workload": f"ensemble: {samples} seeded clouds x 20 bubbles, 64^3, to t_end (~120 RK3 steps), "
                         "QoIs: peak pressure + location, 8 sensor histories",
-            "grid": N_GRID, "samples_per_gpu": M_SAMPLES, "bubbles": 20,
+            "grid": N_GRID, "samples_per_gpu": samples, "bubbles": 20,
             "stencil_precision": precision, "reductions": "f64",
             "graphs": "8-step CUDA-graph chunks",
             "parallelism": f"replicas x{max(world, 1)} (independent samples per GPU)",
-            "l2": "inputs larger than L2: 3 state buffers of 3.76 GB (fp32) per GPU"}
+            "l2": f"inputs {'larger' if buf_gb > 0.129 else 'smaller'} than L2: 3 state buffers of "
+                  f"{buf_gb:.2f} GB ({precision}) per GPU"}
 
 
 def load_json(path):
@@ -399,7 +402,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f64",
         "data": "synthetic: seeded random clouds (no dataset exists for this workload)",
-        "config": config_dict(args.precision, world),
+        "config": config_dict(args.precision, world, args.samples),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "api": "ofm_solve_batch (host clouds in pinned memory, "
                                                  "QoIs and sensor histories back to the host)"},
