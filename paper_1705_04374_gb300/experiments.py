@@ -363,6 +363,50 @@ def cmd_cfg5(quick):
     return out
 
 
+# ------------------------------------------------------------------------------ paper500
+
+def cmd_paper500(quick):
+    """The paper's Sec. 3.1 experiment shrunk to one GPU: 500-bubble clouds (R_cloud 20 mm,
+    log-normal radii in [0.8, 1.2] mm), bubbles and the cloud's liquid at 0.5 MPa, 1/r ramp
+    to 10 MPa from 1 mm beyond the cloud surface; QoI the centre pressure sensor p_c (Eq.
+    sensor).  (a) An OF-MLMC run on 4 levels 32^3..256^3 for a fixed budget of cell-steps
+    (Eq. M-budget, FP32 stencil, 16 starting pairs per level, to the paper's 70 us).  The
+    paper's levels are 512^3..4096^3; here 16^3..128^3 (h = 0.78 mm on the finest, about a
+    bubble radius), so that 16 finest pairs fit the budget.  (b) Plain Monte Carlo
+    statistics of the other QoIs of Sec. 3.2 on 64^3: peak pressure and its distance from
+    the centre, maximum sound speed, and the cloud's gas-volume collapse time (time of the
+    minimum gas fraction of a 20 mm ball about the centre, the paper's sensor #5)."""
+    cloud = W.cloud_paper500()
+    c = 0.5 * W.DOMAIN_L
+    sp = W.solver_paper500(sensors=(W.centre_sensor()[0], (c, c, c, 0.02)), t_end=70e-6)
+    levels = [8, 16, 32, 64] if quick else [16, 32, 64, 128]
+    budget = 5.0e9 if quick else 6.0e10
+    s32 = api.Solver(sp, "fp32")
+    res, pairs, ids = api.run_ofmlmc(s32, cloud, levels, target=budget, mode="budget", qoi=1, max_iterations=4,
+                                     max_cell_steps=2.0 * budget, min_samples=16, capacity=1 << 18)
+    out = dict(experiment="paper500", levels=levels, bubbles=500, qoi="centre sensor peak pressure p_c [Pa]",
+               budget_cell_steps=budget, M=res["M"], W_cell_steps=res["W"], iterations=res["iterations"],
+               capped=res["capped"], failed=res["failed"], gpu_seconds=res["gpu_seconds"],
+               cell_updates_per_s=res["cell_steps"] / max(res["gpu_seconds"], 1e-30),
+               mean=res["est"]["mean"], eps=math.sqrt(res["est"]["eps2"]), alpha=res["est"]["alpha"].tolist(),
+               sigma_tilde2=res["est"]["sigma_tilde2"].tolist())
+    n_mc = 32 if quick else 256
+    (q,), secs, cells = solve_groups(s32, cloud, [(64, level_ids(9, 0, n_mc))])
+    ok = [d for d in q if d["status"] == 0]
+    def stats(vals):
+        v = np.array(vals, dtype=np.float64)
+        return dict(mean=float(v.mean()), std=float(v.std(ddof=1)), min=float(v.min()), max=float(v.max()))
+    out["mc_64"] = dict(samples=n_mc, ok=len(ok), gpu_seconds=secs,
+                        p_peak=stats([d["p_peak"] for d in ok]),
+                        p_peak_dist=stats([d["p_peak_dist"] for d in ok]),
+                        p_c_peak=stats([d["sensor_peak"][0] for d in ok]),
+                        c_max=stats([d["c_max"] for d in ok]),
+                        gas_fraction_t0=stats([d["sensor_alpha0"][1] for d in ok]),
+                        gas_fraction_min=stats([d["sensor_alpha_min"][1] for d in ok]),
+                        collapse_time=stats([d["sensor_alpha_min_t"][1] for d in ok]))
+    return out
+
+
 # ------------------------------------------------------------------------------ epsval
 
 def cmd_epsval(quick, min_samples=16):
@@ -403,13 +447,13 @@ def cmd_epsval(quick, min_samples=16):
 def main():
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["uneven3", "surrogate", "rmse", "cfg5", "epsval"])
+    ap.add_argument("what", choices=["uneven3", "surrogate", "rmse", "cfg5", "epsval", "paper500"])
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--min-samples", type=int, default=16, help="epsval: pairs every level starts with")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     fn = {"uneven3": cmd_uneven3, "surrogate": cmd_surrogate, "rmse": cmd_rmse, "cfg5": cmd_cfg5,
-          "epsval": cmd_epsval}[a.what]
+          "epsval": cmd_epsval, "paper500": cmd_paper500}[a.what]
     print(json.dumps(fn(a.quick, a.min_samples) if a.what == "epsval" else fn(a.quick)), flush=True)
 
 
