@@ -58,12 +58,16 @@ def _qoi(q, which):
     return q["p_peak"] if which == 0 else q["sensor_peak"][which - 1]
 
 
-def solve_groups(solver, cloud, spec, seed=W.BASE_SEED):
-    """spec: list of (N, ids).  One uneven batch; returns (per-group QoI dicts, device seconds, cell-steps)."""
+def solve_groups(solver, cloud, spec, seed=W.BASE_SEED, variant=None, tune=None):
+    """spec: list of (N, ids).  One uneven batch (stage-kernel variant: the batch's default, or
+    the given one; -1 autotunes and, with a dict `tune`, reports the choice and its timings);
+    returns (per-group QoI dicts, device seconds, cell-steps)."""
     import torch
     sp = solver.sp
     groups = [api.make_group(sp, N, ids, seed) for (N, ids) in spec]
     b = api.Batch(solver, cloud, groups)
+    if variant is not None:
+        b.set_variant(variant)
     e0, e1 = _events()
     e0.record()
     b.init()
@@ -75,6 +79,9 @@ def solve_groups(solver, cloud, spec, seed=W.BASE_SEED):
     cells = b.cell_steps()
     b.qoi(allow_bad=True)
     out = [g.qoi_dicts(len(sp.sensors)) for g in groups]
+    if tune is not None:
+        v, t = b.variant()
+        tune.update(chosen=v, tune_ms=list(t))
     b.close()
     return out, secs, cells
 
@@ -187,12 +194,22 @@ def cmd_uneven3(quick):
     r = run_levels(solver, w.cloud, w.levels, counts)
     rs = run_levels(solver, w.cloud, w.levels, counts, separate=True)
     est = api.estimate(r["pairs"], r["W_cells"])
+    # the same uneven batch with the stage-kernel variant chosen by the autotuner
+    spec = []
+    for l, (N, M) in enumerate(zip(w.levels, counts)):
+        spec.append((N, level_ids(l, 0, M)))
+        if l > 0:
+            spec.append((w.levels[l - 1], level_ids(l, 0, M)))
+    tune = {}
+    _, secs_tuned, _ = solve_groups(solver, w.cloud, spec, variant=-1, tune=tune)
     return dict(experiment="uneven3", levels=list(w.levels), counts=list(counts), precision="fp32",
                 bubbles=w.cloud.n_bubbles, qoi="centre sensor peak pressure [Pa]",
                 device_seconds=r["secs"], cell_steps=r["cells"], cell_updates_per_s=r["cells"] / r["secs"],
                 separate_batches_seconds=rs["secs"], speedup_one_batch=rs["secs"] / r["secs"],
                 identical_to_separate=bool(all(np.array_equal(a, b) for a, b in zip(r["pairs"], rs["pairs"]))),
                 W_cell_steps_per_pair=r["W_cells"], failed=r["failed"],
+                autotuned=dict(seconds=secs_tuned, variant=tune.get("chosen"),
+                               two_step_ms_per_variant=tune.get("tune_ms")),
                 estimator={k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in est.items()})
 
 
