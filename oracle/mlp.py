@@ -131,10 +131,11 @@ def unflatten(vec: np.ndarray, sizes) -> list:
     return out
 
 
-def cloud_features(bubbles: np.ndarray, domain_L: float, scale: float) -> np.ndarray:
+def cloud_features(bubbles: np.ndarray, domain_L: float, scale: float, n_keep: int = 0) -> np.ndarray:
     """Bubbles (nb, 4) in metres -> features ordered by the gap between each
     bubble's surface and the domain centre, |x_b - c| - r_b (ties by index):
-    ((x-c)/s, (y-c)/s, (z-c)/s, r/s)."""
+    ((x-c)/s, (y-c)/s, (z-c)/s, r/s), for the n_keep bubbles nearest the
+    centre in that order (0: all)."""
     c = 0.5 * domain_L
     inv = 1.0 / scale
     d = bubbles[:, :3] - c
@@ -143,4 +144,5 @@ def cloud_features(bubbles: np.ndarray, domain_L: float, scale: float) -> np.nda
     f = np.empty((len(key), 4))
     f[:, :3] = (bubbles[order, :3] - c) * inv
     f[:, 3] = bubbles[order, 3] * inv
-    return f.ravel()
+    k = len(key) if n_keep <= 0 else min(n_keep, len(key))
+    return f[:k].ravel()

@@ -90,3 +90,19 @@ def test_surrogate_cv_variance_formula():
     v_formula = (1.25 - 0.9 ** 2 / (0.81 * (1 + M / N))) / M
     assert abs(np.var(est) / v_formula - 1) < 0.1
     assert abs(np.mean(formula) / v_formula - 1) < 0.1
+
+
+def test_cloud_features_order_and_nearest_subset():
+    """Hand-made cloud in a 0.1 m box: the bubble containing the centre has a
+    negative surface gap and comes first, then the others by |x_b - c| - r_b;
+    n_keep keeps that many nearest bubbles."""
+    from oracle import mlp as M
+    b = np.array([[0.05, 0.05, 0.06, 0.001],    # gap 0.010 - 0.001 = 0.009
+                  [0.02, 0.05, 0.05, 0.002],    # gap 0.030 - 0.002 = 0.028
+                  [0.05, 0.05, 0.05, 0.0005],   # gap -0.0005 (contains the centre)
+                  [0.05, 0.07, 0.05, 0.012]])   # gap 0.020 - 0.012 = 0.008
+    f = M.cloud_features(b, 0.1, 0.02).reshape(-1, 4)
+    assert np.allclose(f[:, 3] * 0.02, [0.0005, 0.012, 0.001, 0.002])
+    assert np.allclose(f[1, :3] * 0.02, [0.0, 0.02, 0.0])
+    assert np.array_equal(M.cloud_features(b, 0.1, 0.02, 2), f[:2].ravel())
+    assert np.array_equal(M.cloud_features(b, 0.1, 0.02, 9), f.ravel())
