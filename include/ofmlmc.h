@@ -420,14 +420,15 @@ int ofm_mlp_train(ofm_mlp* mlp, const float* X, const float* T, int n, int steps
 /* Column mean and standard deviation (M-1) of a device matrix, into device
  * FP64 arrays, fixed summation order. */
 int ofm_column_moments(const float* X, int rows, int cols, double* mean_dev, double* std_dev, void* stream);
-/* Surrogate inputs: per cloud, its bubbles ordered by the gap between the
- * bubble's surface and the domain centre, |x_b - L/2| - r_b (ties by index),
- * each as
+/* Surrogate inputs: per cloud, its n_keep bubbles nearest the domain centre
+ * by the gap between the bubble's surface and the centre, |x_b - L/2| - r_b
+ * (ties by index), in that order, each as
  * ((x - L/2)/scale, (y - L/2)/scale, (z - L/2)/scale, r/scale).
  * bubbles_dev: device [n_clouds][n_bubbles][4] doubles (metres);
- * X_dev: device [n_clouds][4 n_bubbles] floats. */
-int ofm_cloud_features(const double* bubbles_dev, int n_clouds, int n_bubbles, double domain_L, double scale,
-                       float* X_dev, void* stream);
+ * n_keep: 1..n_bubbles (0 = all); X_dev: device [n_clouds][4 n_keep] floats.
+ * Errors: OFM_EINVAL for bad sizes, OFM_ECUDA. */
+int ofm_cloud_features(const double* bubbles_dev, int n_clouds, int n_bubbles, int n_keep, double domain_L,
+                       double scale, float* X_dev, void* stream);
 
 #ifdef __cplusplus
 }

@@ -242,8 +242,8 @@ __global__ void column_moments_kernel(int rows, int cols, const float* __restric
 // Features of one cloud per block: bubbles ordered by the gap between the
 // bubble's surface and the domain centre, |x_b - c| - r_b (ties by bubble
 // index), each as ((x - c)/s, (y - c)/s, (z - c)/s, r/s).
-__global__ void features_kernel(int n_clouds, int nb, const double* __restrict__ bub, double centre, double inv_scale,
-                                float* __restrict__ X) {
+__global__ void features_kernel(int n_clouds, int nb, int keep, const double* __restrict__ bub, double centre,
+                                double inv_scale, float* __restrict__ X) {
     extern __shared__ double skey[];
     const int cl = blockIdx.x;
     if (cl >= n_clouds) return;
@@ -257,7 +257,8 @@ __global__ void features_kernel(int n_clouds, int nb, const double* __restrict__
         const double ki = skey[i];
         int rank = 0;
         for (int j = 0; j < nb; ++j) rank += (skey[j] < ki || (skey[j] == ki && j < i)) ? 1 : 0;
-        float* o = X + (size_t)cl * nb * 4 + 4 * rank;
+        if (rank >= keep) continue;
+        float* o = X + (size_t)cl * keep * 4 + 4 * rank;
         o[0] = (float)((b[4 * i] - centre) * inv_scale);
         o[1] = (float)((b[4 * i + 1] - centre) * inv_scale);
         o[2] = (float)((b[4 * i + 2] - centre) * inv_scale);
@@ -622,15 +623,17 @@ extern "C" int ofm_column_moments(const float* X, int rows, int cols, double* me
     return OFM_OK;
 }
 
-extern "C" int ofm_cloud_features(const double* bubbles_dev, int n_clouds, int n_bubbles, double domain_L,
-                                  double scale, float* X_dev, void* stream) {
+extern "C" int ofm_cloud_features(const double* bubbles_dev, int n_clouds, int n_bubbles, int n_keep,
+                                  double domain_L, double scale, float* X_dev, void* stream) {
     ofm::clear_error();
-    if (!bubbles_dev || !X_dev || n_clouds < 0 || n_bubbles < 1 || n_bubbles > 4096 || !(scale > 0.0))
+    if (!bubbles_dev || !X_dev || n_clouds < 0 || n_bubbles < 1 || n_bubbles > 4096 || !(scale > 0.0) ||
+        n_keep < 0 || n_keep > n_bubbles)
         return fail(OFM_EINVAL, "ofm_cloud_features: bad arguments");
     if (n_clouds == 0) return OFM_OK;
+    const int keep = n_keep == 0 ? n_bubbles : n_keep;
     const size_t sm = (size_t)n_bubbles * sizeof(double);
-    features_kernel<<<n_clouds, 128, sm, (cudaStream_t)stream>>>(n_clouds, n_bubbles, bubbles_dev, 0.5 * domain_L,
-                                                                 1.0 / scale, X_dev);
+    features_kernel<<<n_clouds, 128, sm, (cudaStream_t)stream>>>(n_clouds, n_bubbles, keep, bubbles_dev,
+                                                                 0.5 * domain_L, 1.0 / scale, X_dev);
     MLP_TRY(cudaGetLastError());
     return OFM_OK;
 }

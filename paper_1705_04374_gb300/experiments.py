@@ -135,16 +135,36 @@ def run_levels(solver, cloud, levels, counts, which=QOI, separate=False):
     return dict(pairs=pairs, W_cells=W_cells, secs=secs, cells=cells, failed=failed, fine=fine, coarse=coarse)
 
 
-def features_for(cloud, ids, seed=W.BASE_SEED):
+def features_for(cloud, ids, seed=W.BASE_SEED, n_keep=0):
     import torch
     bub = np.stack([api.sample_cloud(cloud, seed, int(i)) for i in ids])
-    return S.cloud_features(torch.from_numpy(bub).cuda(), cloud.n_bubbles, cloud.domain_L, cloud.cloud_radius)
+    return S.cloud_features(torch.from_numpy(bub).cuda(), cloud.n_bubbles, cloud.domain_L, cloud.cloud_radius,
+                            n_keep)
 
 
-def train_surrogate(X, y, steps, lr=1e-3, hidden=256, seed=0, chunk=25):
+def fit_geometry_surrogate(cloud, ids, y, steps, ks=(1, 2, 4, 0)):
+    """Geometry-only surrogate of y: one MLP per number of nearest bubbles in
+    ks (0: all), the one with the lowest held-out error on its own training
+    rows kept.  Returns (net, n_keep, device seconds of all the training)."""
+    best = None
+    secs = 0.0
+    for k in ks:
+        net, t, _, err = train_surrogate(features_for(cloud, ids, n_keep=k), y, steps, return_err=True)
+        secs += t
+        if best is None or err < best[2]:
+            if best is not None:
+                best[0].close()
+            best = (net, k, err)
+        else:
+            net.close()
+    return best[0], best[1], secs
+
+
+def train_surrogate(X, y, steps, lr=1e-3, hidden=256, seed=0, chunk=25, return_err=False):
     """Train the MLP on (X rows, y) with early stopping: 80 % of the rows train,
     20 % validate after every `chunk` Adam steps; the parameters with the
-    lowest validation error are kept.  Returns (net, device seconds, loss history)."""
+    lowest validation error are kept.  Returns (net, device seconds, loss
+    history[, that validation error])."""
     import torch
     n, d = X.shape
     n_tr = max(2, int(0.8 * n))
@@ -172,6 +192,8 @@ def train_surrogate(X, y, steps, lr=1e-3, hidden=256, seed=0, chunk=25):
     net.set_params(best)
     e1.record()
     torch.cuda.synchronize()
+    if return_err:
+        return net, e0.elapsed_time(e1) / 1e3, np.array(hist), best_err
     return net, e0.elapsed_time(e1) / 1e3, np.array(hist)
 
 
@@ -236,12 +258,11 @@ def cmd_surrogate(quick):
                           solve_seconds=r["secs"]))
     # (a) level-0 term, geometry only; trained on half of the level-0 samples, CV on the other half
     ids0 = level_ids(0, 0, counts[0])
-    X0 = features_for(cloud, ids0)
     q0 = pairs[0][:, 0]
     n_tr = len(q0) // 2
-    net, t_train, hist = train_surrogate(X0[:n_tr], q0[:n_tr], steps)
-    s_pair, t_inf0 = infer(net, X0[n_tr:])
-    Xe = features_for(cloud, level_ids(7, 0, N_extra))     # independent extra clouds
+    net, k0, t_train = fit_geometry_surrogate(cloud, ids0[:n_tr], q0[:n_tr], steps)
+    s_pair, t_inf0 = infer(net, features_for(cloud, ids0[n_tr:], n_keep=k0))
+    Xe = features_for(cloud, level_ids(7, 0, N_extra), n_keep=k0)     # independent extra clouds
     s_extra, t_inf = infer(net, Xe)
     D0 = alpha[0] * q0[n_tr:]
     cv = S.surrogate_cv(D0, alpha[0] * s_pair, alpha[0] * s_extra)
@@ -250,7 +271,7 @@ def cmd_surrogate(quick):
     # equal GPU-seconds: the plain estimator spends sur_seconds on more level-0 samples instead
     extra_plain = sur_seconds / Wsec[0]
     plain_var0_eq = np.var(D0, ddof=1) / (len(D0) + extra_plain)
-    out["level0_geometry"] = dict(train_rows=n_tr, cv_rows=len(D0), loss_first_last=[float(hist[0]), float(hist[-1])],
+    out["level0_geometry"] = dict(train_rows=n_tr, cv_rows=len(D0), nearest_bubbles=k0,
                                   corr=float(np.corrcoef(s_pair, q0[n_tr:])[0, 1]), beta=cv["beta"],
                                   var_plain=plain_var0, var_with_surrogate=cv["var"],
                                   var_plain_equal_gpu_seconds=plain_var0_eq,
@@ -319,11 +340,11 @@ def cmd_rmse(quick):
     # level-0 surrogate on the FP32 run: the variance it removes from the level-0 term
     q0 = p32[0][:, 0]
     if len(q0) >= 64:
-        X0 = features_for(cloud, [int(i) for i in i32[0]])
+        ids0 = [int(i) for i in i32[0]]
         n_tr = len(q0) // 2
-        net, t_train, hist = train_surrogate(X0[:n_tr], q0[:n_tr], 400)
-        s_pair, t1 = infer(net, X0[n_tr:])
-        s_extra, t2 = infer(net, features_for(cloud, level_ids(7, 0, 65536)))
+        net, k0, t_train = fit_geometry_surrogate(cloud, ids0[:n_tr], q0[:n_tr], 400)
+        s_pair, t1 = infer(net, features_for(cloud, ids0[n_tr:], n_keep=k0))
+        s_extra, t2 = infer(net, features_for(cloud, level_ids(7, 0, 65536), n_keep=k0))
         a0 = r32["est"]["alpha"][0]
         cv = S.surrogate_cv(a0 * q0[n_tr:], a0 * s_pair, a0 * s_extra)
         ratio = cv["var"] / (np.var(a0 * q0[n_tr:], ddof=1) / (len(q0) - n_tr))
@@ -334,6 +355,7 @@ def cmd_rmse(quick):
         st_sur = st2.copy()
         st_sur[0] *= ratio
         out["fp32_surrogate"] = dict(level0_variance_ratio=ratio, corr=float(np.corrcoef(s_pair, q0[n_tr:])[0, 1]),
+                                     nearest_bubbles=k0,
                                      train_seconds=t_train, infer_seconds=t1 + t2,
                                      model_gpu_seconds_plain=cost(st2),
                                      model_gpu_seconds_with_surrogate=cost(st_sur) + t_train + t1 + t2)
@@ -366,14 +388,15 @@ def cmd_cfg5(quick):
                alpha=res["est"]["alpha"].tolist(), sigma_tilde2=res["est"]["sigma_tilde2"].tolist())
     q0 = pairs[0][:, 0]
     if len(q0) >= 40:
-        X0 = features_for(cloud, [int(i) for i in ids[0]])
+        ids0 = [int(i) for i in ids[0]]
         n_tr = len(q0) // 2
-        net, t_train, hist = train_surrogate(X0[:n_tr], q0[:n_tr], 400)
-        s_pair, t1 = infer(net, X0[n_tr:])
-        s_extra, t2 = infer(net, features_for(cloud, level_ids(7, 0, 65536 if not quick else 4096)))
+        net, k0, t_train = fit_geometry_surrogate(cloud, ids0[:n_tr], q0[:n_tr], 400)
+        s_pair, t1 = infer(net, features_for(cloud, ids0[n_tr:], n_keep=k0))
+        s_extra, t2 = infer(net, features_for(cloud, level_ids(7, 0, 65536 if not quick else 4096), n_keep=k0))
         a0 = res["est"]["alpha"][0]
         cv = S.surrogate_cv(a0 * q0[n_tr:], a0 * s_pair, a0 * s_extra)
         out["level0_surrogate"] = dict(corr=float(np.corrcoef(s_pair, q0[n_tr:])[0, 1]), beta=cv["beta"],
+                                       nearest_bubbles=k0,
                                        variance_ratio=cv["var"] / (np.var(a0 * q0[n_tr:], ddof=1) / (len(q0) - n_tr)),
                                        train_seconds=t_train, infer_seconds=t1 + t2)
         net.close()

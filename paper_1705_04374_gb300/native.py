@@ -129,7 +129,7 @@ SIGNATURES = {
     "ofm_mlp_gradients": (C.c_int, [_vp, _vp, _vp, C.c_int, _P(C.c_float), _P(C.c_float), _vp]),
     "ofm_mlp_train": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _P(C.c_float), _vp]),
     "ofm_column_moments": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp]),
-    "ofm_cloud_features": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp]),
+    "ofm_cloud_features": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp]),
     "ofm_estimate": (C.c_int, [C.c_int, _P(C.c_int64), _P(_P(C.c_double)), _P(C.c_double),
                                _P(ofm_estimate_out)]),
     "ofm_level_moments_of": (C.c_int, [_P(C.c_double), C.c_int64, _P(ofm_level_moments)]),

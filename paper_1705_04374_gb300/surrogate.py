@@ -97,13 +97,15 @@ def column_moments(X):
     return mean, std
 
 
-def cloud_features(bubbles_dev, n_bubbles: int, domain_L: float, scale: float):
-    """bubbles_dev: (n_clouds, n_bubbles, 4) float64 CUDA tensor in metres."""
+def cloud_features(bubbles_dev, n_bubbles: int, domain_L: float, scale: float, n_keep: int = 0):
+    """bubbles_dev: (n_clouds, n_bubbles, 4) float64 CUDA tensor in metres; features of the
+    n_keep bubbles nearest the centre (0: all)."""
     import torch
     n = bubbles_dev.shape[0]
-    X = torch.empty((n, 4 * n_bubbles), dtype=torch.float32, device="cuda")
-    nv.check(nv.lib().ofm_cloud_features(_ptr(bubbles_dev), n, n_bubbles, domain_L, scale, _ptr(X), _stream()),
-             "ofm_cloud_features")
+    k = n_bubbles if n_keep <= 0 else n_keep
+    X = torch.empty((n, 4 * k), dtype=torch.float32, device="cuda")
+    nv.check(nv.lib().ofm_cloud_features(_ptr(bubbles_dev), n, n_bubbles, n_keep, domain_L, scale, _ptr(X),
+                                         _stream()), "ofm_cloud_features")
     return X
 
 
