@@ -647,7 +647,9 @@ static double sensor_value(const orc_grid* g, const double* Q, const long* idx, 
 /*   c_max = max over t = 0 and every step of max_cells c (Sec. 3.2 maximum */
 /*   speed of sound); gas-fraction sensors (Sec. 3.2 alpha sensors): mean   */
 /*   alpha2 over the same cells as the pressure sensor, its value at t = 0, */
-/*   its minimum over the recorded steps and the first time of that minimum. */
+/*   its minimum over the recorded steps and the first time of that minimum; */
+/*   its history on the output times of the pressure sensors (ahist, may be */
+/*   NULL), linear in time between steps like theirs.                       */
 /* ------------------------------------------------------------------ */
 typedef struct {
     double p_peak;
@@ -673,7 +675,7 @@ static double sensor_alpha(const orc_grid* g, const double* Q, const long* idx, 
 }
 
 int orc_solve(const orc_grid* g, double* Q, double t_end, int max_steps, int n_sensors,
-              const double* sensors, int n_out, double* hist, orc_qoi* out) {
+              const double* sensors, int n_out, double* hist, double* ahist, orc_qoi* out) {
     if (n_sensors > 8) return -2;
     long* sidx[8];
     int scount[8];
@@ -682,7 +684,7 @@ int orc_solve(const orc_grid* g, double* Q, double t_end, int max_steps, int n_s
         sidx[s] = (long*)malloc(sizeof(long) * (scount[s] > 0 ? scount[s] : 1));
         sensor_cells(g, sensors + 4 * s, sidx[s], scount[s]);
     }
-    double sv_old[8], sv_new[8];
+    double sv_old[8], sv_new[8], sa_old[8], sa_new[8];
     orc_reduce r;
     reduce_state(g, Q, &r);
     out->status = r.status;
@@ -695,8 +697,9 @@ int orc_solve(const orc_grid* g, double* Q, double t_end, int max_steps, int n_s
         sv_old[s] = sensor_value(g, Q, sidx[s], scount[s]);
         out->sensor_peak[s] = sv_old[s];
         if (hist && n_out > 0) hist[s * n_out + 0] = sv_old[s];
-        out->sensor_alpha0[s] = out->sensor_alpha_min[s] = sensor_alpha(g, Q, sidx[s], scount[s]);
+        out->sensor_alpha0[s] = out->sensor_alpha_min[s] = sa_old[s] = sensor_alpha(g, Q, sidx[s], scount[s]);
         out->sensor_alpha_min_t[s] = 0.0;
+        if (ahist && n_out > 0) ahist[s * n_out + 0] = sa_old[s];
     }
     double t = 0.0;
     int nsteps = 0;
@@ -726,7 +729,7 @@ int orc_solve(const orc_grid* g, double* Q, double t_end, int max_steps, int n_s
         for (int s = 0; s < n_sensors; ++s) {
             sv_new[s] = sensor_value(g, Q, sidx[s], scount[s]);
             if (sv_new[s] > out->sensor_peak[s]) out->sensor_peak[s] = sv_new[s];
-            double a = sensor_alpha(g, Q, sidx[s], scount[s]);
+            double a = sa_new[s] = sensor_alpha(g, Q, sidx[s], scount[s]);
             if (a < out->sensor_alpha_min[s]) {
                 out->sensor_alpha_min[s] = a;
                 out->sensor_alpha_min_t[s] = t_new;
@@ -737,12 +740,17 @@ int orc_solve(const orc_grid* g, double* Q, double t_end, int max_steps, int n_s
                 double tk = (kout * t_end) / (n_out - 1);
                 if (tk > t_new) break;
                 double wgt = (tk - t) / (t_new - t);
-                for (int s = 0; s < n_sensors; ++s)
+                for (int s = 0; s < n_sensors; ++s) {
                     hist[s * n_out + kout] = (1.0 - wgt) * sv_old[s] + wgt * sv_new[s];
+                    if (ahist) ahist[s * n_out + kout] = (1.0 - wgt) * sa_old[s] + wgt * sa_new[s];
+                }
                 ++kout;
             }
         }
-        for (int s = 0; s < n_sensors; ++s) sv_old[s] = sv_new[s];
+        for (int s = 0; s < n_sensors; ++s) {
+            sv_old[s] = sv_new[s];
+            sa_old[s] = sa_new[s];
+        }
         t = t_new;
     }
     orc_totals(g, Q, out->totals_end);

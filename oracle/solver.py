@@ -68,7 +68,7 @@ def _lib(count: bool = False) -> C.CDLL:
                                        C.c_double, C.c_double, C.c_double, _D]
         lib.orc_sensor_cell_count.argtypes = [G, _D]
         lib.orc_sensor_cell_count.restype = C.c_int
-        lib.orc_solve.argtypes = [G, _D, C.c_double, C.c_int, C.c_int, _D, C.c_int, _D,
+        lib.orc_solve.argtypes = [G, _D, C.c_double, C.c_int, C.c_int, _D, C.c_int, _D, _D,
                                   C.POINTER(OrcQoi)]
         lib.orc_solve.restype = C.c_int
         lib.orc_advance.argtypes = [G, _D, C.c_double, C.c_int, C.POINTER(C.c_int)]
@@ -243,9 +243,10 @@ def solve(sp, N: int, bubbles_si: np.ndarray, count_flops: bool = False,
         if ns else np.zeros(4)
     n_out = sp.n_out_times
     hist = np.zeros(max(ns, 1) * n_out)
+    ahist = np.zeros(max(ns, 1) * n_out)
     out = OrcQoi()
     rc = _lib(count_flops).orc_solve(C.byref(g), _p(Q), sp.t_end / u.t_ref, sp.max_steps, ns,
-                                     _p(sens), n_out, _p(hist), C.byref(out))
+                                     _p(sens), n_out, _p(hist), _p(ahist), C.byref(out))
     if rc != 0:
         raise RuntimeError(f"orc_solve rc={rc}")
     idx = out.peak_index
@@ -269,5 +270,6 @@ def solve(sp, N: int, bubbles_si: np.ndarray, count_flops: bool = False,
         sensor_alpha0=np.array(out.sensor_alpha0[:ns]),
         sensor_alpha_min=np.array(out.sensor_alpha_min[:ns]),
         sensor_alpha_min_t=np.array(out.sensor_alpha_min_t[:ns]) * u.t_ref,
+        alpha_hist=ahist[: ns * n_out].reshape(ns, n_out).copy(),
     )
     return q, hist[: ns * n_out].reshape(ns, n_out) * u.p_ref, Q

@@ -377,11 +377,17 @@ def test_sound_speed_and_gas_fraction_sensor_qois():
     assert np.allclose(q["sensor_alpha0"], 1e-6, rtol=1e-9)
     assert np.allclose(q["sensor_alpha_min"], 1e-6, rtol=1e-9)
     assert np.all(q["sensor_alpha_min_t"] == 0.0)
+    assert np.allclose(q["alpha_hist"], 1e-6, rtol=1e-9)
     q, _, _ = S.solve(sp, 16, np.array([[0.05, 0.05, 0.05, 0.015]]))
     assert q["status"] == 0
     assert q["sensor_alpha0"][0] > 0.1 and q["sensor_alpha_min"][0] < q["sensor_alpha0"][0]
     assert 0.0 < q["sensor_alpha_min_t"][0] <= q["t_final"]
     assert q["c_max"] >= c_text * (1 - 1e-5)
+    # the history starts at the t = 0 value and, interpolating between step values, never
+    # goes below their minimum
+    ah = q["alpha_hist"]
+    assert ah[0, 0] == q["sensor_alpha0"][0] and ah.shape == (2, sp.n_out_times)
+    assert np.all(ah[0] >= q["sensor_alpha_min"][0] * (1 - 1e-15)) and ah[0].min() < ah[0, 0]
 
 
 # ---------------------------------------------------------------- initial condition and sampler
