@@ -128,6 +128,9 @@ typedef struct {
     const ofm_bubble* bubbles;   /* host [n_samples * n_bubbles] or NULL: sample the clouds */
     ofm_qoi* qoi_out;            /* host [n_samples], written by ofm_batch_qoi / ofm_solve_batch */
     double* sensor_hist;         /* host [n_samples][n_sensors][n_out_times] [Pa], or NULL */
+    double* alpha_hist;          /* host [n_samples][n_sensors][n_out_times] gas-fraction sensor
+                                  * histories (mean alpha2 over each sensor's cells, same output
+                                  * times, linear in time between steps), or NULL */
 } ofm_group;
 
 typedef struct ofm_solver ofm_solver;

@@ -77,13 +77,15 @@ class Group:
     """Host-side arrays of one group (kept alive for the C side)."""
 
     def __init__(self, N: int, sample_ids: Sequence[int], seed: int, n_sensors: int, n_out: int,
-                 bubbles: Optional[np.ndarray] = None, n_bubbles: int = 0):
+                 bubbles: Optional[np.ndarray] = None, n_bubbles: int = 0, alpha_hist: bool = False):
         self.N = N
         self.M = len(sample_ids)
         self.ids = np.ascontiguousarray(np.asarray(sample_ids, dtype=np.uint64))
         self.seed = seed
         self.qoi = (nv.ofm_qoi * self.M)()
         self.hist = np.zeros((self.M, max(n_sensors, 0), n_out)) if n_sensors and n_out else None
+        # gas-fraction sensor histories on the same output times (opt-in: one more device-to-host copy)
+        self.alpha_hist = np.zeros_like(self.hist) if alpha_hist and self.hist is not None else None
         self.bub = None
         if bubbles is not None:
             b = np.ascontiguousarray(np.asarray(bubbles, dtype=np.float64).reshape(self.M * n_bubbles, 4))
@@ -97,6 +99,8 @@ class Group:
         self.c.qoi_out = C.cast(self.qoi, C.POINTER(nv.ofm_qoi))
         self.c.sensor_hist = (self.hist.ctypes.data_as(C.POINTER(C.c_double))
                               if self.hist is not None else None)
+        self.c.alpha_hist = (self.alpha_hist.ctypes.data_as(C.POINTER(C.c_double))
+                             if self.alpha_hist is not None else None)
 
     def qoi_dicts(self, n_sensors: int) -> List[dict]:
         out = []
@@ -214,8 +218,10 @@ class Batch:
         self.close()
 
 
-def make_group(sp, N: int, ids: Sequence[int], seed: int, bubbles=None, n_bubbles: int = 0) -> Group:
-    return Group(N, ids, seed, len(sp.sensors), sp.n_out_times, bubbles=bubbles, n_bubbles=n_bubbles)
+def make_group(sp, N: int, ids: Sequence[int], seed: int, bubbles=None, n_bubbles: int = 0,
+               alpha_hist: bool = False) -> Group:
+    return Group(N, ids, seed, len(sp.sensors), sp.n_out_times, bubbles=bubbles, n_bubbles=n_bubbles,
+                 alpha_hist=alpha_hist)
 
 
 def solve_batch_host(solver: Solver, cloud, groups: List[Group], workspace=None) -> int:

@@ -1200,6 +1200,8 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ P
     DevQoi& q = P.s.qoi[slot];
     double* old = P.s.sens_old + (size_t)slot * OFM_MAX_SENSORS;
     double* hist = P.s.hist + (size_t)slot * P.n_sens * P.n_out;
+    double* aold = P.s.ahist ? P.s.alpha_old + (size_t)slot * OFM_MAX_SENSORS : nullptr;
+    double* ahist = P.s.ahist ? P.s.ahist + (size_t)slot * P.n_sens * P.n_out : nullptr;
     double t;
     int nsteps;
     if (first) {
@@ -1214,6 +1216,10 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ P
             q.sensor_peak[s] = sv[s];
             old[s] = sv[s];
             if (P.n_out > 0) hist[s * P.n_out] = sv[s];
+            if (ahist) {
+                aold[s] = sa[s];
+                if (P.n_out > 0) ahist[s * P.n_out] = sa[s];
+            }
         }
         t = 0.0;
         nsteps = 0;
@@ -1242,12 +1248,18 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ P
                 const double tk = ((double)k * P.t_end) / (double)(P.n_out - 1);
                 if (tk > t) break;
                 const double wgt = (tk - t_old) / (t - t_old);
-                for (int s = 0; s < P.n_sens; ++s) hist[s * P.n_out + k] = (1.0 - wgt) * old[s] + wgt * sv[s];
+                for (int s = 0; s < P.n_sens; ++s) {
+                    hist[s * P.n_out + k] = (1.0 - wgt) * old[s] + wgt * sv[s];
+                    if (ahist) ahist[s * P.n_out + k] = (1.0 - wgt) * aold[s] + wgt * sa[s];
+                }
                 ++k;
             }
             P.s.kout[slot] = k;
         }
-        for (int s = 0; s < P.n_sens; ++s) old[s] = sv[s];
+        for (int s = 0; s < P.n_sens; ++s) {
+            old[s] = sv[s];
+            if (aold) aold[s] = sa[s];
+        }
     }
     P.s.t[slot] = t;
     P.s.nsteps[slot] = nsteps;

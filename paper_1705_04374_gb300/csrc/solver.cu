@@ -67,6 +67,7 @@ struct GroupHost {
     int N, M;
     ofm_qoi* qoi_out;
     double* hist_out;
+    double* ahist_out;
     std::vector<int> sens_cells;
     int sens_off[OFM_MAX_SENSORS + 1];
     size_t off_QA, off_QB, off_dQ, off_part, off_sens;
@@ -103,7 +104,7 @@ struct ofm_batch {
     Params<double> pd_s;      // table the stage kernels walk: groups with unfinished samples
     Params<float> pf_s;
     unsigned active_mask;     // groups in the stage table
-    size_t off_t, off_dt, off_last, off_done, off_nsteps, off_kout, off_qoi, off_sold, off_hist,
+    size_t off_t, off_dt, off_last, off_done, off_nsteps, off_kout, off_qoi, off_sold, off_hist, off_aold, off_ahist,
         off_active, off_bub;
 };
 
@@ -167,6 +168,8 @@ void fill_params(ofm_batch* b, Params<T>& P) {
     P.s.qoi = (DevQoi*)(b->ws + b->off_qoi);
     P.s.sens_old = (double*)(b->ws + b->off_sold);
     P.s.hist = (double*)(b->ws + b->off_hist);
+    P.s.alpha_old = (double*)(b->ws + b->off_aold);
+    P.s.ahist = (double*)(b->ws + b->off_ahist);
     P.s.n_active = (int*)(b->ws + b->off_active);
     P.s.g_active = (int*)(b->ws + b->off_active + 16);
     P.s.bubbles = (const double*)(b->ws + b->off_bub);
@@ -344,6 +347,8 @@ static void layout(const ofm_solver* s, const ofm_cloud_params* cloud, const ofm
     b->off_qoi = Lo.take(S * sizeof(DevQoi));
     b->off_sold = Lo.take(S * OFM_MAX_SENSORS * 8);
     b->off_hist = Lo.take(std::max<size_t>(1, S * s->cfg.n_sensors * s->cfg.n_out_times) * 8);
+    b->off_aold = Lo.take(S * OFM_MAX_SENSORS * 8);
+    b->off_ahist = Lo.take(std::max<size_t>(1, S * s->cfg.n_sensors * s->cfg.n_out_times) * 8);
     b->off_active = Lo.take(16 + sizeof(int) * OFM_MAX_GROUPS);
     b->off_bub = Lo.take(std::max<size_t>(1, S * cloud->n_bubbles * 4) * 8);
 }
@@ -402,6 +407,7 @@ extern "C" int ofm_batch_create(ofm_batch** out, ofm_solver* s, const ofm_cloud_
         b->gh[g].M = groups[g].n_samples;
         b->gh[g].qoi_out = groups[g].qoi_out;
         b->gh[g].hist_out = groups[g].sensor_hist;
+        b->gh[g].ahist_out = groups[g].alpha_hist;
         slots += groups[g].n_samples;
     }
     b->total_slots = slots;
@@ -596,15 +602,19 @@ extern "C" int ofm_batch_qoi(ofm_batch* b) {
     std::vector<int> nsteps(b->total_slots), done(b->total_slots);
     std::vector<double> tt(b->total_slots);
     const size_t hist_n = (size_t)b->total_slots * c.n_sensors * c.n_out_times;
-    std::vector<double> hist(hist_n);
+    std::vector<double> hist(hist_n), ahist(hist_n);
     CUDA_TRY(cudaMemcpyAsync(q.data(), b->ws + b->off_qoi, q.size() * sizeof(DevQoi), cudaMemcpyDeviceToHost, b->priv));
     CUDA_TRY(cudaMemcpyAsync(nsteps.data(), b->ws + b->off_nsteps, nsteps.size() * 4, cudaMemcpyDeviceToHost, b->priv));
     CUDA_TRY(cudaMemcpyAsync(done.data(), b->ws + b->off_done, done.size() * 4, cudaMemcpyDeviceToHost, b->priv));
     CUDA_TRY(cudaMemcpyAsync(tt.data(), b->ws + b->off_t, tt.size() * 8, cudaMemcpyDeviceToHost, b->priv));
+    bool want_ahist = false;
+    for (int g = 0; g < b->n_groups; ++g) want_ahist = want_ahist || b->gh[g].ahist_out != nullptr;
     if (hist_n)
         CUDA_TRY(cudaMemcpyAsync(hist.data(), b->ws + b->off_hist, hist_n * 8, cudaMemcpyDeviceToHost, b->priv));
+    if (hist_n && want_ahist)
+        CUDA_TRY(cudaMemcpyAsync(ahist.data(), b->ws + b->off_ahist, hist_n * 8, cudaMemcpyDeviceToHost, b->priv));
     b->d2h_bytes += (long long)(q.size() * sizeof(DevQoi) + nsteps.size() * 4 + done.size() * 4 + tt.size() * 8 +
-                                hist_n * 8);
+                                hist_n * 8 * (want_ahist ? 2 : 1));
     CUDA_TRY(cudaStreamSynchronize(b->priv));
     const ofm_solver* s = b->solver;
     int any_bad = 0;
@@ -648,6 +658,10 @@ extern "C" int ofm_batch_qoi(ofm_batch* b) {
             if (gh.hist_out && hist_n) {
                 const size_t per = (size_t)c.n_sensors * c.n_out_times;
                 for (size_t a = 0; a < per; ++a) gh.hist_out[(size_t)i * per + a] = hist[(size_t)slot * per + a] * s->p_ref;
+            }
+            if (gh.ahist_out && hist_n) {
+                const size_t per = (size_t)c.n_sensors * c.n_out_times;
+                for (size_t a = 0; a < per; ++a) gh.ahist_out[(size_t)i * per + a] = ahist[(size_t)slot * per + a];
             }
         }
     }
@@ -809,5 +823,6 @@ extern "C" int ofm_solve_level(ofm_solver* s, const ofm_cloud_params* cloud, int
     g.bubbles = nullptr;
     g.qoi_out = out;
     g.sensor_hist = sensor_hist;
+    g.alpha_hist = nullptr;
     return ofm_solve_batch(s, cloud, &g, 1, workspace, workspace_bytes, stream);
 }

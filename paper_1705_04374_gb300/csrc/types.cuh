@@ -79,6 +79,8 @@ struct SampleDev {
     DevQoi* qoi;
     double* sens_old;     // [slot][OFM_MAX_SENSORS]
     double* hist;         // [slot][n_sens][n_out]
+    double* alpha_old;    // [slot][OFM_MAX_SENSORS] (NULL: no gas-fraction histories)
+    double* ahist;        // [slot][n_sens][n_out] gas-fraction histories, or NULL
     int* n_active;
     int* g_active;          // [group] samples not yet finished
     const double* bubbles;  // [slot][nb][4], non-dimensional

@@ -55,7 +55,8 @@ class ofm_qoi(C.Structure):
 class ofm_group(C.Structure):
     _fields_ = [("N", C.c_int), ("n_samples", C.c_int), ("sample_ids", C.POINTER(C.c_uint64)),
                 ("seed", C.c_uint64), ("bubbles", C.POINTER(ofm_bubble)),
-                ("qoi_out", C.POINTER(ofm_qoi)), ("sensor_hist", C.POINTER(C.c_double))]
+                ("qoi_out", C.POINTER(ofm_qoi)), ("sensor_hist", C.POINTER(C.c_double)),
+                ("alpha_hist", C.POINTER(C.c_double))]
 
 
 class ofm_level_moments(C.Structure):

@@ -59,9 +59,9 @@ def oracle_one_step(sp, N, bub):
     return osolver.rk3_step(g, Q0, dt)
 
 
-def gpu_batch(sp, precision, groups_spec, cloud, seed=W.BASE_SEED):
+def gpu_batch(sp, precision, groups_spec, cloud, seed=W.BASE_SEED, alpha_hist=True):
     s = api.Solver(sp, precision)
-    groups = [api.make_group(sp, N, ids, seed) for (N, ids) in groups_spec]
+    groups = [api.make_group(sp, N, ids, seed, alpha_hist=alpha_hist) for (N, ids) in groups_spec]
     b = api.Batch(s, cloud, groups)
     return s, groups, b
 
@@ -150,7 +150,7 @@ def oracle_qois(sp, N, cloud, ids, seed=W.BASE_SEED):
         return list(ex.map(one, ids))
 
 
-def compare_qoi(qg, hg, qo, ho, tol, n_sens):
+def compare_qoi(qg, hg, qo, ho, tol, n_sens, ag=None):
     assert qg["status"] == 0 and qo["status"] == 0
     assert qg["n_steps"] == qo["n_steps"]
     for k in QOI_KEYS:
@@ -164,6 +164,11 @@ def compare_qoi(qg, hg, qo, ho, tol, n_sens):
     assert np.allclose(qg["sensor_alpha_min_t"], qo["sensor_alpha_min_t"], rtol=tol, atol=0)
     if hg is not None and ho.size:
         assert np.all(np.abs(hg - ho) <= tol * np.abs(ho))
+    if ag is not None and ho.size:
+        ao = qo["alpha_hist"]
+        assert ag.shape == ao.shape
+        assert np.all(np.abs(ag - ao) <= tol * ao)
+        assert np.array_equal(ag[:, 0], qg["sensor_alpha0"])
 
 
 def test_two_level_config_fp64_qois_at_t_end():
@@ -183,7 +188,8 @@ def test_two_level_config_fp64_qois_at_t_end():
         ref = oracle_qois(sp, N, w.cloud, ids)
         got = groups[gi].qoi_dicts(ns)
         for i in range(len(ids)):
-            compare_qoi(got[i], groups[gi].hist[i], ref[i][0], ref[i][1], TOL_QOI_FP64, ns)
+            compare_qoi(got[i], groups[gi].hist[i], ref[i][0], ref[i][1], TOL_QOI_FP64, ns,
+                        ag=groups[gi].alpha_hist[i])
             assert got[i]["peak_index"] == ref[i][0]["peak_index"]
     b.close()
 
@@ -199,7 +205,7 @@ def test_fp32_qoi_errors_are_small_and_stated(capsys):
     b.qoi()
     got = groups[0].qoi_dicts(len(sp.sensors))
     ref = oracle_qois(sp, 32, w.cloud, ids)
-    errs = {"p_peak": [], "sensor_peak": [], "hist": [], "c_max": [], "alpha_min": []}
+    errs = {"p_peak": [], "sensor_peak": [], "hist": [], "c_max": [], "alpha_min": [], "alpha_hist": []}
     for i in range(3):
         qo, ho = ref[i]
         qg = got[i]
@@ -210,6 +216,8 @@ def test_fp32_qoi_errors_are_small_and_stated(capsys):
         errs["c_max"].append(abs(qg["c_max"] - qo["c_max"]) / qo["c_max"])
         errs["alpha_min"].append(float(np.max(np.abs(qg["sensor_alpha_min"] - qo["sensor_alpha_min"])
                                               / qo["sensor_alpha_min"])))
+        errs["alpha_hist"].append(float(np.max(np.abs(groups[0].alpha_hist[i] - qo["alpha_hist"]))
+                                        / np.max(qo["alpha_hist"])))
     with capsys.disabled():
         print("\nFP32 vs FP64 oracle, relative QoI errors (32^3, 4 bubbles):",
               {k: f"{max(v):.2e}" for k, v in errs.items()})
@@ -218,6 +226,7 @@ def test_fp32_qoi_errors_are_small_and_stated(capsys):
     assert max(errs["hist"]) < 1e-2
     assert max(errs["c_max"]) < 1e-3
     assert max(errs["alpha_min"]) < 1e-3
+    assert max(errs["alpha_hist"]) < 1e-3
     b.close()
 
 
