@@ -83,7 +83,7 @@ def test_memory_admission_splits_batches_without_changing_results():
     s = api.Solver(w.solver, "fp32")
     a, pa, ia = api.run_ofmlmc(s, w.cloud, [8, 16], target=1e9, qoi=0, max_iterations=1, max_cell_steps=1e8)
     b, pb, ib = api.run_ofmlmc(s, w.cloud, [8, 16], target=1e9, qoi=0, max_iterations=1, max_cell_steps=1e8,
-                               max_batch_bytes=600 * 1024)
+                               max_batch_bytes=680 * 1024)
     for l in range(2):
         assert np.array_equal(ia[l], ib[l])
         assert np.array_equal(pa[l], pb[l])
