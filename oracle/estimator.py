@@ -26,7 +26,17 @@ Readings of points the paper leaves open:
     over pair l (of alpha_0 q_0 for l = 0);
   - the tolerance constraint is eps_OF <= tau, i.e. sum sigma~^2_l/M_l <= tau^2;
   - the MC-equivalent sample number is ceil((sigma_L/eps)^2) (the printed
-    formula omits the square).
+    formula omits the square);
+  - the optional fit of step 3 (Sec. 2.4.3, Sec. 3.2 and the appendix on
+    M_L = 1) is applied to the variances of the level differences
+    V_l = V[q_l - q_{l-1}] (the quantity the results section fits), not to
+    the covariances: ln V_l = a + b l by least squares over the levels l >= 1
+    with at least two pairs, each weighted by the inverse of the Gaussian
+    error of ln V_l, Var[ln V_l] ~ 2/(M_l - 1) (the posterior mean under
+    flat priors); the fitted V_l give the covariances of Eq. (alpha-matvec)
+    as (sigma^2_l + sigma^2_{l-1} - V_l)/2; a level with one pair takes
+    sigma^2_l = sigma^2_{l-1} (no sample variance exists) and its sigma~^2_l
+    from the fitted second moments.
 """
 from __future__ import annotations
 
@@ -140,6 +150,72 @@ def estimate(pairs, W):
     M = [p.shape[0] for p in pairs]
     return dict(alpha=alpha, sigma2=sigma2, cov=cov, sigma_tilde2=st2,
                 mean=ofmlmc_mean(pairs, alpha), eps2=eps2(st2, M), M=M)
+
+
+# ---------------------------------------------------------------------------
+# Step 3's optional fit: an exponential decay of the level-difference
+# variances, so that the finest level can start from one warm-up pair.
+
+def diff_variances(pairs) -> np.ndarray:
+    """V[q_l - q_{l-1}] of pair l (nan for l = 0 and for fewer than two pairs)."""
+    out = np.full(len(pairs), np.nan)
+    for l in range(1, len(pairs)):
+        out[l] = _var(pairs[l][:, 0] - pairs[l][:, 1])
+    return out
+
+
+def fit_diff_variances(V, M):
+    """Weighted least-squares line through ln V_l over l >= 1 with M_l >= 2 and
+    V_l > 0, weights (M_l - 1)/2.  Returns (a, b, V_fit) with
+    V_fit[l] = exp(a + b l) for l >= 1 (V_fit[0] = nan)."""
+    L = len(V) - 1
+    used = [l for l in range(1, L + 1) if M[l] >= 2 and V[l] > 0.0]
+    if len(used) < 2:
+        raise ValueError("the fit needs two levels l >= 1 with at least two pairs")
+    w = np.array([(M[l] - 1) / 2.0 for l in used])
+    x = np.array(used, dtype=np.float64)
+    y = np.array([math.log(V[l]) for l in used])
+    # normal equations of min sum w (y - a - b x)^2
+    Sw, Sx, Sy = w.sum(), (w * x).sum(), (w * y).sum()
+    Sxx, Sxy = (w * x * x).sum(), (w * x * y).sum()
+    det = Sw * Sxx - Sx * Sx
+    b = (Sw * Sxy - Sx * Sy) / det
+    a = (Sy - b * Sx) / Sw
+    V_fit = np.full(L + 1, np.nan)
+    for l in range(1, L + 1):
+        V_fit[l] = math.exp(a + b * l)
+    return a, b, V_fit
+
+
+def estimate_fitted(pairs, W):
+    """estimate() with the fitted level-difference variances in Eq. (alpha-matvec).
+    Level 0 needs two samples; a level l >= 1 may have one pair."""
+    L = len(pairs) - 1
+    M = [p.shape[0] for p in pairs]
+    if M[0] < 2 or min(M) < 1:
+        raise ValueError("level 0 needs two samples and every level one pair")
+    sigma2 = np.zeros(L + 1)
+    for l in range(L + 1):
+        members = [pairs[l][:, 0]]
+        if l < L:
+            members.append(pairs[l + 1][:, 1])
+        pooled = np.concatenate(members)
+        sigma2[l] = _var(pooled) if pooled.size >= 2 else sigma2[l - 1]
+    a, b, V_fit = fit_diff_variances(diff_variances(pairs), M)
+    cov = np.zeros(L + 1)
+    for l in range(1, L + 1):
+        cov[l] = 0.5 * (sigma2[l] + sigma2[l - 1] - V_fit[l])
+    alpha = alpha_optimal(sigma2, cov, W)
+    st2 = np.zeros(L + 1)
+    for l in range(L + 1):
+        if M[l] >= 2:
+            d = alpha[l] * pairs[l][:, 0] - (alpha[l - 1] * pairs[l][:, 1] if l > 0 else 0.0)
+            st2[l] = _var(d)
+        else:
+            st2[l] = (alpha[l] ** 2 * sigma2[l] + alpha[l - 1] ** 2 * sigma2[l - 1]
+                      - 2.0 * alpha[l] * alpha[l - 1] * cov[l])
+    return dict(alpha=alpha, sigma2=sigma2, cov=cov, sigma_tilde2=st2, mean=ofmlmc_mean(pairs, alpha),
+                eps2=eps2(st2, M), M=M, fit=(a, b), V_fit=V_fit)
 
 
 # ---------------------------------------------------------------------------
@@ -279,16 +355,20 @@ def total_work(M, W) -> float:
 
 
 def adaptive(draw, W, tau: float, max_iter: int = 10, mode: str = "tol",
-             budget: Optional[float] = None, min_samples: int = 2):
+             budget: Optional[float] = None, min_samples: int = 2, fit: bool = False):
     """Steps 1-8 of the adaptive OF-MLMC algorithm.
 
     ``draw(l, m)`` returns m new pairs for level l (an (m, 2) array).  Returns
     the final estimate dict plus the per-iteration sample numbers.  Reading:
     without the optional Bayesian fit of step 3, a sample variance needs two
-    samples, so every level starts with at least ``min_samples``.
+    samples, so every level starts with at least ``min_samples``.  With the
+    fit (``fit=True``) and L >= 3 the finest level keeps Eq. (warmup)'s single
+    pair (the appendix on M_L = 1): levels 1..L-1 carry the fit.
     """
     L = len(W) - 1
     M_target = np.maximum(warmup_M(W), min_samples)                # step 1
+    if fit and L >= 3:
+        M_target[L] = warmup_M(W)[L]
     pairs: List[np.ndarray] = [np.zeros((0, 2)) for _ in range(L + 1)]
     history = []
     est = None
@@ -298,7 +378,7 @@ def adaptive(draw, W, tau: float, max_iter: int = 10, mode: str = "tol",
             if need > 0:
                 pairs[l] = np.concatenate([pairs[l], draw(l, need)])
         history.append([p.shape[0] for p in pairs])
-        est = estimate(pairs, W)                                     # steps 3-5
+        est = estimate_fitted(pairs, W) if fit else estimate(pairs, W)  # steps 3-5
         spent = total_work([p.shape[0] for p in pairs], W)
         if math.sqrt(est["eps2"]) <= tau or (mode == "budget" and spent >= budget):
             break                                                    # step 6

@@ -204,3 +204,133 @@ def test_estimate_from_summaries_equals_estimate_from_pairs():
         assert np.allclose(got[k], ref[k], rtol=1e-11, atol=1e-14), k
     assert abs(got["mean"] - ref["mean"]) <= 1e-12 * abs(ref["mean"])
     assert abs(got["eps2"] - ref["eps2"]) <= 1e-11 * ref["eps2"]
+
+
+# ----------------------------------------------------------------- step 3's optional variance fit
+
+def test_fit_recovers_an_exact_exponential():
+    V = np.array([np.nan] + [3.0 * 0.25 ** l for l in range(1, 4)])
+    a, b, V_fit = E.fit_diff_variances(V, [9, 7, 5, 3])
+    assert abs(a - math.log(3.0)) < 1e-13 and abs(b - math.log(0.25)) < 1e-13
+    assert np.allclose(V_fit[1:], V[1:], rtol=1e-13, atol=0)
+
+
+def test_fit_is_the_weighted_least_squares_line():
+    """Against numpy's weighted polynomial fit (it minimises sum (w (y - p))^2,
+    so w = sqrt of the inverse log-variance 2/(M - 1))."""
+    rng = np.random.default_rng(5)
+    M = [50, 40, 9, 3]
+    V = np.array([np.nan, 0.8, 0.15, 0.05])
+    V[1:] *= np.exp(rng.normal(0.0, 0.3, 3))
+    a, b, _ = E.fit_diff_variances(V, M)
+    x = np.array([1.0, 2.0, 3.0])
+    w = np.sqrt((np.array(M[1:]) - 1) / 2.0)
+    slope, icpt = np.polyfit(x, np.log(V[1:]), 1, w=w)
+    assert abs(b - slope) < 1e-12 and abs(a - icpt) < 1e-12
+    # levels with fewer than two pairs carry no empirical variance and are left out
+    a2, b2, V2 = E.fit_diff_variances(np.array([np.nan, 0.8, 0.15, np.nan]), [50, 40, 9, 1])
+    slope2, icpt2 = np.polyfit([1.0, 2.0], np.log([0.8, 0.15]), 1)
+    assert abs(b2 - slope2) < 1e-12 and abs(a2 - icpt2) < 1e-12
+    assert abs(V2[3] - math.exp(a2 + 3 * b2)) < 1e-15
+
+
+def test_fit_is_the_posterior_mean_under_flat_priors():
+    """Bayesian inference (Sec. 2.4.3, step 3) with Gaussian errors of ln V_l
+    and flat priors: the posterior mean of (a, b), integrated on a grid."""
+    M = [0, 12, 6, 4]
+    V = np.array([np.nan, 0.5, 0.2, 0.03])
+    a, b, _ = E.fit_diff_variances(V, M)
+    x = np.array([1.0, 2.0, 3.0])
+    y = np.log(V[1:])
+    s2 = 2.0 / (np.array(M[1:]) - 1)
+    A = np.linspace(a - 8, a + 8, 801)
+    B = np.linspace(b - 5, b + 5, 801)
+    AA, BB = np.meshgrid(A, B, indexing="ij")
+    logp = np.zeros_like(AA)
+    for xi, yi, si in zip(x, y, s2):
+        logp -= (yi - AA - BB * xi) ** 2 / (2.0 * si)
+    p = np.exp(logp - logp.max())
+    assert abs((p * AA).sum() / p.sum() - a) < 1e-6
+    assert abs((p * BB).sum() / p.sum() - b) < 1e-6
+
+
+def test_log_sample_variance_error_model():
+    """Var[ln V^] ~ 2/(M - 1) for Gaussian level differences (the error bars
+    the fit's weights stand for), by Monte Carlo."""
+    rng = np.random.default_rng(7)
+    M = 101
+    x = rng.standard_normal((20000, M)) * 0.3
+    lv = np.log(x.var(axis=1, ddof=1))
+    assert abs(lv.var() / (2.0 / (M - 1)) - 1.0) < 0.05
+
+
+def test_fit_needs_two_levels():
+    with pytest.raises(ValueError):
+        E.fit_diff_variances(np.array([np.nan, 0.5, np.nan]), [4, 4, 1])
+
+
+def _toy_alpha_and_diffvar(L, a, b, W):
+    _, var, cov = toy_moments(L, a, b)
+    V = np.array([np.nan] + [4.0 ** (-l) * (a * a + 5.0 * b * b) for l in range(1, L + 1)])
+    return E.alpha_optimal(var, cov, W), var, cov, V
+
+
+def test_fitted_estimator_converges_to_closed_forms():
+    """Toy hierarchy: V[q_l - q_{l-1}] = 4^-l (a^2 + 5 b^2) is an exact
+    exponential, so the fit and alpha approach the closed forms."""
+    L, a, b = 3, 0.4, 0.6
+    W = np.array([1.0] + [16.0 ** l + 16.0 ** (l - 1) for l in range(1, L + 1)])
+    alpha_true, var, cov, V = _toy_alpha_and_diffvar(L, a, b, W)
+    pairs = Wk.toy_levels([40000, 20000, 20000, 20000], L, a, b, seed=3)
+    est = E.estimate_fitted(pairs, W)
+    assert np.allclose(est["V_fit"][1:], V[1:], rtol=0.03)
+    assert abs(est["fit"][1] - math.log(0.25)) < 0.03
+    assert np.allclose(est["alpha"], alpha_true, atol=0.02)
+    assert np.allclose(est["cov"][1:], cov[1:], rtol=0.03)
+
+
+def test_fitted_estimator_with_one_finest_pair():
+    """M_L = 1 (the appendix's warm-up): V_L is extrapolated from levels
+    1..L-1, sigma^2_L = sigma^2_{L-1}, sigma~^2_L from the fitted moments.
+    Against the closed forms under that reading; the reading itself moves
+    Cov[q_L, q_{L-1}] by (sigma^2_L - sigma^2_{L-1})/2, which on this toy
+    (variance falling 10 % from level 2 to 3) shifts alpha by about 0.05."""
+    L, a, b = 3, 0.4, 0.6
+    W = np.array([1.0] + [16.0 ** l + 16.0 ** (l - 1) for l in range(1, L + 1)])
+    alpha_true, var, cov, V = _toy_alpha_and_diffvar(L, a, b, W)
+    var_r = var.copy()
+    var_r[L] = var[L - 1]
+    cov_r = cov.copy()
+    cov_r[L] = 0.5 * (var_r[L] + var_r[L - 1] - V[L])
+    alpha_r = E.alpha_optimal(var_r, cov_r, W)
+    pairs = Wk.toy_levels([40000, 20000, 20000, 1], L, a, b, seed=4)
+    est = E.estimate_fitted(pairs, W)
+    assert est["M"][L] == 1
+    assert est["sigma2"][L] == est["sigma2"][L - 1]
+    assert abs(est["V_fit"][L] / V[L] - 1.0) < 0.1
+    assert np.allclose(est["alpha"], alpha_r, atol=0.02)
+    assert np.max(np.abs(est["alpha"] - alpha_true)) < 0.08
+    al = est["alpha"]
+    st2_r = al[L] ** 2 * var_r[L] + al[L - 1] ** 2 * var_r[L - 1] - 2 * al[L] * al[L - 1] * cov_r[L]
+    assert abs(est["sigma_tilde2"][L] / st2_r - 1.0) < 0.2
+    with pytest.raises(ValueError):
+        E.estimate_fitted(Wk.toy_levels([100, 100, 1], 2, a, b, seed=4), W[:3])
+
+
+def test_adaptive_loop_with_fit_starts_the_finest_level_from_one_pair():
+    L, a, b = 3, 0.4, 0.6
+    mean, _, _ = toy_moments(L, a, b)
+    W = np.array([1.0] + [16.0 ** l + 16.0 ** (l - 1) for l in range(1, L + 1)])
+    seed = [40]
+
+    def draw(l, m):
+        seed[0] += 1
+        Ms = [0] * (L + 1)
+        Ms[l] = m
+        return Wk.toy_levels(Ms, L, a, b, seed=seed[0])[l]
+
+    est = E.adaptive(draw, W, tau=0.02, fit=True)
+    assert est["history"][0][L] == 1
+    assert est["history"][0][:L] == list(np.maximum(E.warmup_M(W), 2))[:L]
+    assert math.sqrt(est["eps2"]) <= 0.02
+    assert abs(est["mean"] - mean[L]) < 5 * 0.02
