@@ -283,6 +283,29 @@ typedef struct {
 int ofm_estimate(int L, const int64_t* M, const double* const* q, const double* W,
                  ofm_estimate_out* out);
 
+/* Step 3's optional fit (Section 2.4.3; Section 3.2 fits the level-difference
+ * variances with an exponential decay; the appendix on M_L = 1 uses it to
+ * start the finest level from one warm-up pair).
+ *   ofm_fit_level_variances: V[l] (l = 1..L; V[0] ignored) are the sample
+ *     variances of q_l - q_{l-1} over M[l] pairs.  Fits ln V_l = a + b l by
+ *     least squares over the levels with M[l] >= 2 and V[l] > 0, each
+ *     weighted by (M[l] - 1)/2, the inverse of the Gaussian error of ln V_l:
+ *     the posterior mean of (a, b) under flat priors.  Writes
+ *     V_fit[l] = exp(a + b l) for l = 1..L, V_fit[0] = 0, and coef = {a, b}
+ *     (coef may be NULL).  OFM_EINVAL with fewer than two usable levels.
+ *   ofm_estimate_fitted: ofm_estimate with the fitted variances: the
+ *     covariances of Eq. (alpha-matvec) become (sigma2_l + sigma2_{l-1} -
+ *     V_fit_l)/2 and are returned in out->cov.  Level 0 needs M >= 2, every
+ *     level l >= 1 at least one pair; a level whose q_l has a single computed
+ *     value takes sigma2_l = sigma2_{l-1}, and a level with one pair takes
+ *     sigma_tilde2_l = alpha_l^2 sigma2_l + alpha_{l-1}^2 sigma2_{l-1}
+ *     - 2 alpha_l alpha_{l-1} cov_l.  V_fit (L+1 doubles, may be NULL)
+ *     receives the fitted level-difference variances.
+ * Host FP64 arrays; errors as ofm_estimate plus the fit's. */
+int ofm_fit_level_variances(int L, const int64_t* M, const double* V, double* V_fit, double* coef);
+int ofm_estimate_fitted(int L, const int64_t* M, const double* const* q, const double* W,
+                        ofm_estimate_out* out, double* V_fit);
+
 /* The same estimator from per-level summaries, for pairs spread over several
  * processes (one process per GPU).  Section 2.4 needs only per-level means,
  * pooled variances and the fine/coarse covariance, so each process
@@ -323,11 +346,12 @@ int ofm_warmup_samples(int L, const double* W, int64_t* M_out);
  * (l << 40) | i for both its members (N[l] and N[l-1]).  Step 1 takes the
  * warm-up numbers of Eq. (warmup) from the cost model W_l ~ N_l^4 (+ N_{l-1}^4),
  * raised to min_samples (>= 2: without the optional Bayesian fit of step 3 a
- * variance needs two samples).  Each iteration solves every level's missing
+ * variance needs two samples; with it, fit_variances, the finest of L >= 3
+ * levels is not raised).  Each iteration solves every level's missing
  * pairs in one uneven batch (split only if it exceeds max_batch_bytes; 0 =
  * 80% of the free device memory), measures the pair costs W_l as mean
  * cell-steps per pair, excludes pairs with a failed member (status != 0),
- * computes the estimator (ofm_estimate) and stops when eps_OF <= target (tol
+ * computes the estimator (ofm_estimate, or ofm_estimate_fitted) and stops when eps_OF <= target (tol
  * mode) or the cell-steps spent reach target (budget mode); otherwise step 7
  * re-optimises M_l (ofm_optimal_samples, keeping computed pairs).
  * pairs_out / ids_out (host, may be NULL): the (q_l, q_{l-1}) rows and sample
@@ -345,6 +369,9 @@ typedef struct {
     size_t max_batch_bytes;
     double max_cell_steps;     /* safety cap on the total work (0 = none): an iteration that
                                   would exceed it is not started and result.capped is set */
+    int fit_variances;         /* 1: step 3's variance fit (ofm_estimate_fitted) in every
+                                  iteration; with L >= 3 the finest level keeps the single
+                                  warm-up pair of Eq. (warmup) (L < 2 is refused) */
 } ofm_run_config;
 
 typedef struct {

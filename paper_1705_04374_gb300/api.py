@@ -237,18 +237,37 @@ def solve_batch_host(solver: Solver, cloud, groups: List[Group], workspace=None)
     return nv.lib().ofm_solve_batch(solver.h, C.byref(cp), garr, len(groups), ws_ptr, ws_bytes, stream)
 
 
-def estimate(pairs: Sequence[np.ndarray], W: Sequence[float]) -> dict:
-    """ofm_estimate on per-level (M_l, 2) arrays of (q_l, q_{l-1})."""
+def estimate(pairs: Sequence[np.ndarray], W: Sequence[float], fit: bool = False) -> dict:
+    """ofm_estimate (or, with fit, ofm_estimate_fitted) on per-level (M_l, 2)
+    arrays of (q_l, q_{l-1})."""
     L = len(pairs) - 1
-    arrs = [np.ascontiguousarray(p, dtype=np.float64) for p in pairs]
+    arrs = [np.ascontiguousarray(np.asarray(p, dtype=np.float64).reshape(-1, 2)) for p in pairs]
     M = (C.c_int64 * (L + 1))(*[a.shape[0] for a in arrs])
     ptrs = (C.POINTER(C.c_double) * (L + 1))(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs])
     Wc = (C.c_double * (L + 1))(*W)
     out = nv.ofm_estimate_out()
-    nv.check(nv.lib().ofm_estimate(L, M, ptrs, Wc, C.byref(out)), "ofm_estimate")
     n = L + 1
-    return dict(alpha=np.array(out.alpha[:n]), sigma2=np.array(out.sigma2[:n]), cov=np.array(out.cov[:n]),
-                sigma_tilde2=np.array(out.sigma_tilde2[:n]), mean=out.mean, eps2=out.eps2)
+    res = {}
+    if fit:
+        vf = (C.c_double * n)()
+        nv.check(nv.lib().ofm_estimate_fitted(L, M, ptrs, Wc, C.byref(out), vf), "ofm_estimate_fitted")
+        res["V_fit"] = np.array(vf[:n])
+    else:
+        nv.check(nv.lib().ofm_estimate(L, M, ptrs, Wc, C.byref(out)), "ofm_estimate")
+    res.update(alpha=np.array(out.alpha[:n]), sigma2=np.array(out.sigma2[:n]), cov=np.array(out.cov[:n]),
+               sigma_tilde2=np.array(out.sigma_tilde2[:n]), mean=out.mean, eps2=out.eps2)
+    return res
+
+
+def fit_level_variances(V: Sequence[float], M: Sequence[int]):
+    """ofm_fit_level_variances: (a, b, V_fit) of ln V_l = a + b l (V[0] ignored)."""
+    L = len(V) - 1
+    Vc = (C.c_double * (L + 1))(*[0.0 if not np.isfinite(v) else float(v) for v in V])
+    Mc = (C.c_int64 * (L + 1))(*[int(m) for m in M])
+    vf = (C.c_double * (L + 1))()
+    coef = (C.c_double * 2)()
+    nv.check(nv.lib().ofm_fit_level_variances(L, Mc, Vc, vf, coef), "ofm_fit_level_variances")
+    return coef[0], coef[1], np.array(vf[:])
 
 
 def level_moments(pairs: np.ndarray) -> tuple:
@@ -312,8 +331,10 @@ def warmup_samples(W) -> np.ndarray:
 
 def run_ofmlmc(solver: Solver, cloud, levels, target: float, mode: str = "tol", qoi: int = 0,
                seed: int = 20170509, max_iterations: int = 10, min_samples: int = 2,
-               max_batch_bytes: int = 0, capacity: int = 1 << 16, max_cell_steps: float = 0.0):
-    """ofm_run: the adaptive OF-MLMC loop over GPU solves.  Returns (result dict, pairs per level, ids per level)."""
+               max_batch_bytes: int = 0, capacity: int = 1 << 16, max_cell_steps: float = 0.0,
+               fit_variances: bool = False):
+    """ofm_run: the adaptive OF-MLMC loop over GPU solves.  Returns (result dict, pairs per level, ids per level).
+    fit_variances: step 3's variance fit, and one warm-up pair on the finest of L >= 3 levels."""
     cfg = nv.ofm_run_config()
     cfg.L = len(levels) - 1
     for i, n in enumerate(levels):
@@ -326,6 +347,7 @@ def run_ofmlmc(solver: Solver, cloud, levels, target: float, mode: str = "tol", 
     cfg.min_samples = min_samples
     cfg.max_batch_bytes = max_batch_bytes
     cfg.max_cell_steps = max_cell_steps
+    cfg.fit_variances = 1 if fit_variances else 0
     cp = cloud_params(cloud)
     pairs = np.zeros((capacity, 2))
     ids = np.zeros(capacity, dtype=np.uint64)

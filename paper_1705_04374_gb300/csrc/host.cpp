@@ -144,13 +144,42 @@ int solve_alpha(int L, const double* sigma2, const double* cov, const double* W,
 
 }  // namespace
 
-extern "C" int ofm_estimate(int L, const int64_t* M, const double* const* q, const double* W,
-                            ofm_estimate_out* out) {
-    if (L < 0 || L >= OFM_MAX_LEVELS || !M || !q || !W || !out)
-        return fail(OFM_EINVAL, "ofm_estimate: bad arguments");
+namespace {
+
+// Weighted least squares of ln V_l = a + b l over the levels l >= 1 with at
+// least two pairs and V_l > 0, weights (M_l - 1)/2 (the inverse of the
+// Gaussian error of ln V_l): the posterior mean of (a, b) under flat priors.
+int fit_line(int L, const int64_t* M, const double* V, double* a, double* b) {
+    double Sw = 0.0, Sx = 0.0, Sy = 0.0, Sxx = 0.0, Sxy = 0.0;
+    int used = 0;
+    for (int l = 1; l <= L; ++l) {
+        if (M[l] < 2 || !(V[l] > 0.0) || !std::isfinite(V[l])) continue;
+        const double w = 0.5 * (double)(M[l] - 1), x = (double)l, y = std::log(V[l]);
+        Sw += w;
+        Sx += w * x;
+        Sy += w * y;
+        Sxx += w * x * x;
+        Sxy += w * x * y;
+        ++used;
+    }
+    if (used < 2) return fail(OFM_EINVAL, "variance fit: needs two levels l >= 1 with at least two pairs");
+    const double det = Sw * Sxx - Sx * Sx;
+    *b = (Sw * Sxy - Sx * Sy) / det;
+    *a = (Sy - *b * Sx) / Sw;
+    return OFM_OK;
+}
+
+// Steps 3-5 and the estimator; fit = true replaces the covariances of
+// Eq. (alpha-matvec) by (sigma2_l + sigma2_{l-1} - V_fit_l)/2.
+int estimate_core(int L, const int64_t* M, const double* const* q, const double* W, ofm_estimate_out* out, bool fit,
+                  double* V_fit_out) {
+    const char* who = fit ? "ofm_estimate_fitted" : "ofm_estimate";
+    if (L < 0 || L >= OFM_MAX_LEVELS || !M || !q || !W || !out) return fail(OFM_EINVAL, "%s: bad arguments", who);
+    if (fit && L < 1) return fail(OFM_EINVAL, "%s: the fit needs L >= 1", who);
     for (int l = 0; l <= L; ++l) {
-        if (M[l] < 2 || !q[l]) return fail(OFM_EINVAL, "ofm_estimate: level %d needs >= 2 samples", l);
-        if (!(W[l] > 0.0)) return fail(OFM_EINVAL, "ofm_estimate: W[%d] must be > 0", l);
+        const int64_t need = (fit && l > 0) ? 1 : 2;
+        if (M[l] < need || !q[l]) return fail(OFM_EINVAL, "%s: level %d needs >= %lld samples", who, l, (long long)need);
+        if (!(W[l] > 0.0)) return fail(OFM_EINVAL, "%s: W[%d] must be > 0", who, l);
     }
     std::memset(out, 0, sizeof(*out));
     std::vector<std::vector<double>> fine(L + 1), coarse(L + 1);
@@ -165,8 +194,27 @@ extern "C" int ofm_estimate(int L, const int64_t* M, const double* const* q, con
     for (int l = 0; l <= L; ++l) {
         std::vector<double> pooled = fine[l];
         if (l < L) pooled.insert(pooled.end(), coarse[l + 1].begin(), coarse[l + 1].end());
-        out->sigma2[l] = var_of(pooled);
-        out->cov[l] = l > 0 ? cov_of(fine[l], coarse[l]) : 0.0;
+        // one computed q_l (the finest level's single warm-up pair): no sample variance exists
+        out->sigma2[l] = pooled.size() >= 2 ? var_of(pooled) : out->sigma2[l - 1];
+        out->cov[l] = (l > 0 && !fit) ? cov_of(fine[l], coarse[l]) : 0.0;
+    }
+    if (fit) {
+        std::vector<double> V(L + 1, 0.0);
+        for (int l = 1; l <= L; ++l) {
+            if (M[l] < 2) continue;
+            std::vector<double> d(M[l]);
+            for (int64_t i = 0; i < M[l]; ++i) d[i] = fine[l][i] - coarse[l][i];
+            V[l] = var_of(d);
+        }
+        double a = 0.0, b = 0.0;
+        int rc = fit_line(L, M, V.data(), &a, &b);
+        if (rc != OFM_OK) return rc;
+        for (int l = 1; l <= L; ++l) {
+            const double vf = std::exp(a + b * (double)l);
+            out->cov[l] = 0.5 * (out->sigma2[l] + out->sigma2[l - 1] - vf);
+            if (V_fit_out) V_fit_out[l] = vf;
+        }
+        if (V_fit_out) V_fit_out[0] = 0.0;
     }
     int rc = solve_alpha(L, out->sigma2, out->cov, W, out->alpha);
     if (rc != OFM_OK) return rc;
@@ -176,12 +224,44 @@ extern "C" int ofm_estimate(int L, const int64_t* M, const double* const* q, con
         for (int64_t i = 0; i < M[l]; ++i)
             d[i] = l == 0 ? out->alpha[0] * fine[0][i]
                           : out->alpha[l] * fine[l][i] - out->alpha[l - 1] * coarse[l][i];
-        out->sigma_tilde2[l] = var_of(d);
+        if (M[l] >= 2)
+            out->sigma_tilde2[l] = var_of(d);
+        else  // from the fitted second moments
+            out->sigma_tilde2[l] = out->alpha[l] * out->alpha[l] * out->sigma2[l] +
+                                   out->alpha[l - 1] * out->alpha[l - 1] * out->sigma2[l - 1] -
+                                   2.0 * out->alpha[l] * out->alpha[l - 1] * out->cov[l];
         mean += mean_of(d);
         eps2 += out->sigma_tilde2[l] / (double)M[l];
     }
     out->mean = mean;
     out->eps2 = eps2;
+    return OFM_OK;
+}
+
+}  // namespace
+
+extern "C" int ofm_estimate(int L, const int64_t* M, const double* const* q, const double* W,
+                            ofm_estimate_out* out) {
+    return estimate_core(L, M, q, W, out, false, nullptr);
+}
+
+extern "C" int ofm_estimate_fitted(int L, const int64_t* M, const double* const* q, const double* W,
+                                   ofm_estimate_out* out, double* V_fit) {
+    return estimate_core(L, M, q, W, out, true, V_fit);
+}
+
+extern "C" int ofm_fit_level_variances(int L, const int64_t* M, const double* V, double* V_fit, double* coef) {
+    if (L < 1 || L >= OFM_MAX_LEVELS || !M || !V || !V_fit)
+        return fail(OFM_EINVAL, "ofm_fit_level_variances: bad arguments");
+    double a = 0.0, b = 0.0;
+    int rc = fit_line(L, M, V, &a, &b);
+    if (rc != OFM_OK) return rc;
+    V_fit[0] = 0.0;
+    for (int l = 1; l <= L; ++l) V_fit[l] = std::exp(a + b * (double)l);
+    if (coef) {
+        coef[0] = a;
+        coef[1] = b;
+    }
     return OFM_OK;
 }
 

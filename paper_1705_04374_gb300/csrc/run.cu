@@ -144,6 +144,8 @@ extern "C" int ofm_run(ofm_solver* s, const ofm_cloud_params* cloud, const ofm_r
     if (!(rc->target > 0.0) || (rc->mode != OFM_MODE_TOL && rc->mode != OFM_MODE_BUDGET) || rc->max_iterations < 1 ||
         rc->qoi < 0 || rc->qoi > s->cfg.n_sensors)
         return fail(OFM_EINVAL, "ofm_run: bad target, mode, iteration limit or QoI index");
+    if (rc->fit_variances && L < 2)
+        return fail(OFM_EINVAL, "ofm_run: the variance fit needs two difference levels (L >= 2)");
     for (int l = 0; l <= L; ++l)
         if (rc->N[l] < 8 || (l > 0 && rc->N[l] <= rc->N[l - 1]))
             return fail(OFM_EINVAL, "ofm_run: levels must refine (N[%d] = %d)", l, rc->N[l]);
@@ -166,6 +168,12 @@ extern "C" int ofm_run(ofm_solver* s, const ofm_cloud_params* cloud, const ofm_r
     int r = ofm_warmup_samples(L, Wmodel.data(), target.data());
     if (r != OFM_OK) return r;
     for (int l = 0; l <= L; ++l) target[l] = std::max<int64_t>(target[l], min_m);
+    if (rc->fit_variances && L >= 3) {
+        // the appendix on M_L = 1: levels 1..L-1 carry the fit, the finest keeps Eq. (warmup)'s value
+        std::vector<int64_t> w(L + 1);
+        ofm_warmup_samples(L, Wmodel.data(), w.data());
+        target[L] = w[L];
+    }
 
     std::vector<LevelData> lv(L + 1);
     double gpu_ms = 0.0;
@@ -201,7 +209,8 @@ extern "C" int ofm_run(ofm_solver* s, const ofm_cloud_params* cloud, const ofm_r
             res->W[l] = W[l];
         }
         res->failed = failed;
-        r = ofm_estimate(L, M.data(), ptr.data(), W.data(), &res->est);
+        r = rc->fit_variances ? ofm_estimate_fitted(L, M.data(), ptr.data(), W.data(), &res->est, nullptr)
+                              : ofm_estimate(L, M.data(), ptr.data(), W.data(), &res->est);
         if (r != OFM_OK) return r;
         double spent = 0.0;
         for (int l = 0; l <= L; ++l) spent += lv[l].cell_steps;

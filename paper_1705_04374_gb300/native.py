@@ -73,7 +73,7 @@ class ofm_estimate_out(C.Structure):
 class ofm_run_config(C.Structure):
     _fields_ = [("L", C.c_int), ("N", C.c_int * OFM_MAX_LEVELS), ("mode", C.c_int), ("target", C.c_double),
                 ("qoi", C.c_int), ("seed", C.c_uint64), ("max_iterations", C.c_int), ("min_samples", C.c_int),
-                ("max_batch_bytes", C.c_size_t), ("max_cell_steps", C.c_double)]
+                ("max_batch_bytes", C.c_size_t), ("max_cell_steps", C.c_double), ("fit_variances", C.c_int)]
 
 
 class ofm_run_result(C.Structure):
@@ -133,6 +133,10 @@ SIGNATURES = {
     "ofm_cloud_features": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp]),
     "ofm_estimate": (C.c_int, [C.c_int, _P(C.c_int64), _P(_P(C.c_double)), _P(C.c_double),
                                _P(ofm_estimate_out)]),
+    "ofm_estimate_fitted": (C.c_int, [C.c_int, _P(C.c_int64), _P(_P(C.c_double)), _P(C.c_double),
+                                      _P(ofm_estimate_out), _P(C.c_double)]),
+    "ofm_fit_level_variances": (C.c_int, [C.c_int, _P(C.c_int64), _P(C.c_double), _P(C.c_double),
+                                          _P(C.c_double)]),
     "ofm_level_moments_of": (C.c_int, [_P(C.c_double), C.c_int64, _P(ofm_level_moments)]),
     "ofm_merge_moments": (C.c_int, [_P(ofm_level_moments), _P(ofm_level_moments), _P(ofm_level_moments)]),
     "ofm_estimate_moments": (C.c_int, [C.c_int, _P(ofm_level_moments), _P(C.c_double), _P(ofm_estimate_out)]),

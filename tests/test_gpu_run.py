@@ -67,6 +67,27 @@ def test_two_level_run_matches_oracle_estimator_and_solves():
             assert np.array_equal(pairs2[l][:res["M"][l]], pairs[l])
 
 
+def test_run_with_variance_fit_starts_the_finest_level_from_one_pair():
+    """Step 3's fit in ofm_run: four levels, Eq. (warmup) numbers with one pair
+    on the finest, and the fitted estimator of the oracle on the returned pairs."""
+    w = W.tiny(16, 4)
+    s = api.Solver(w.solver, "fp32")
+    levels = [8, 16, 24, 32]
+    res, pairs, ids = api.run_ofmlmc(s, w.cloud, levels, target=1e-12, qoi=0, max_iterations=1,
+                                     max_cell_steps=5e8, fit_variances=True)
+    Wm = [float(levels[0]) ** 4] + [float(levels[l]) ** 4 + float(levels[l - 1]) ** 4 for l in range(1, 4)]
+    want = list(np.maximum(E.warmup_M(Wm), 2))
+    want[3] = 1
+    assert res["iterations"] == 1 and res["failed"] == 0
+    assert res["M"] == want
+    ref = E.estimate_fitted(pairs, res["W"])
+    for k in ("alpha", "sigma2", "cov", "sigma_tilde2"):
+        assert np.allclose(res["est"][k], ref[k], rtol=1e-12, atol=1e-12), k
+    assert abs(res["est"]["mean"] - ref["mean"]) <= 1e-12 * abs(ref["mean"])
+    with pytest.raises(api.nv.OfmError):
+        api.run_ofmlmc(s, w.cloud, [8, 16], target=1.0, max_iterations=1, fit_variances=True)
+
+
 def test_budget_mode_stops_when_spent():
     w = W.tiny(16, 4)
     s = api.Solver(w.solver, "fp32")

@@ -60,6 +60,33 @@ def test_estimator_matches_oracle():
         assert abs(a["eps2"] - b["eps2"]) < 1e-12 * b["eps2"]
 
 
+def test_fitted_estimator_matches_oracle():
+    """ofm_estimate_fitted / ofm_fit_level_variances against the oracle,
+    with several pairs on every level and with one pair on the finest."""
+    for L, M in ((2, [60, 20, 6]), (3, [300, 50, 9, 3]), (3, [300, 50, 9, 1])):
+        pairs = W.toy_levels(M, L, 0.4, 0.7, seed=12)
+        Wc = [1.0] + [16.0 ** l + 16.0 ** (l - 1) for l in range(1, L + 1)]
+        a = api.estimate(pairs, Wc, fit=True)
+        b = E.estimate_fitted(pairs, Wc)
+        for k in ("alpha", "sigma2", "cov", "sigma_tilde2"):
+            assert np.allclose(a[k], b[k], rtol=1e-12, atol=1e-14), (M, k)
+        assert np.allclose(a["V_fit"][1:], b["V_fit"][1:], rtol=1e-12, atol=0)
+        assert abs(a["mean"] - b["mean"]) < 1e-12 * max(1, abs(b["mean"]))
+        assert abs(a["eps2"] - b["eps2"]) < 1e-12 * b["eps2"]
+        V = E.diff_variances(pairs)
+        fa, fb, vf = api.fit_level_variances(V, M)
+        oa, ob, ovf = E.fit_diff_variances(V, M)
+        assert abs(fa - oa) < 1e-12 * max(1, abs(oa)) and abs(fb - ob) < 1e-12 * max(1, abs(ob))
+        assert np.allclose(vf[1:], ovf[1:], rtol=1e-12, atol=0)
+    # fewer than two usable difference levels, or a level-0 with one sample
+    with pytest.raises(nv.OfmError):
+        api.estimate(W.toy_levels([20, 20, 1], 2, 0.4, 0.7, seed=1), [1.0, 17.0, 272.0], fit=True)
+    with pytest.raises(nv.OfmError):
+        api.estimate(W.toy_levels([1, 20, 20], 2, 0.4, 0.7, seed=1), [1.0, 17.0, 272.0], fit=True)
+    with pytest.raises(nv.OfmError):
+        api.fit_level_variances([0.0, 0.3, -1.0], [0, 5, 5])
+
+
 def test_optimal_and_warmup_samples_match_oracle():
     st2 = [1.0, 0.2, 0.04, 0.01]
     Wc = [1.0, 17.0, 272.0, 4352.0]
