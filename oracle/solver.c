@@ -63,13 +63,16 @@ void orc_flop_reset(void) {
 
 typedef struct {
     int nx, ny, nz;   /* cells per axis */
-    int bc;           /* 0: transmissive (nearest interior cell), 1: periodic */
+    int bc;           /* 0: transmissive (nearest interior cell), 1: periodic,
+                         2: characteristic far field (see char_ghost) */
     double h;         /* cell width, non-dimensional */
     double gamma1;    /* phase 1 = liquid */
     double gamma2;    /* phase 2 = gas */
     double pc1, pc2;  /* stiffening pressures, non-dimensional */
     double cfl;
     double weno_eps;
+    double p_inf;      /* far-field pressure of bc 2, non-dimensional */
+    double bc_penalty; /* kappa of bc 2 in [0, 1]: 0 = transmissive, 1 = far field */
 } orc_grid;
 
 /* ------------------------------------------------------------------ */
@@ -329,6 +332,32 @@ static int wrap(int i, int n, int bc) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Characteristic far-field boundary (Sec. 3.1: non-reflecting,          */
+/* characteristic boundaries with a penalty towards p_inf, after Poinsot */
+/* and Lele 1992), in ghost-cell form.  Along the outward normal n (side */
+/* s = +1 at the high face, -1 at the low face) with u_n = s u_axis and  */
+/* the acoustic impedance Z = rho c of the interior cell next to the     */
+/* face, the outgoing characteristic p + Z u_n is taken from that cell   */
+/* and the incoming one p - Z u_n from a blend of that cell (weight      */
+/* 1 - kappa) and the far field at rest at p_inf (weight kappa):         */
+/*   p_b   = p + kappa/2 (p_inf - p + Z u_n)                             */
+/*   u_n,b = u_n + kappa/(2 Z) (p - p_inf - Z u_n).                      */
+/* kappa = 0 is the transmissive boundary; kappa = 1 passes a linear     */
+/* plane wave leaving along n unchanged (no reflection) and relaxes the  */
+/* domain towards p_inf.  Partial densities, alpha2 and the tangential   */
+/* velocities are the interior cell's.  Every ghost layer takes this     */
+/* state.                                                                */
+/* ------------------------------------------------------------------ */
+static void char_ghost(const orc_grid* g, const double* wi, int axis, double s, double* wb) {
+    for (int v = 0; v < NV; ++v) wb[v] = wi[v];
+    const double Z = (wi[0] + wi[1]) * sqrt(sound2(g, wi));
+    const double un = s * wi[2 + axis];
+    const double k = g->bc_penalty;
+    wb[5] = wi[5] + 0.5 * k * (g->p_inf - wi[5] + Z * un);
+    wb[2 + axis] = s * (un + 0.5 * k * (wi[5] - g->p_inf - Z * un) / Z);
+}
+
+/* ------------------------------------------------------------------ */
 /* Right-hand side L(Q) of Eq. (ode):                                    */
 /*   rows 1-6: -(1/h) sum_d (F_{+} - F_{-})                              */
 /*   row 7:    -(1/h) sum_d (Fa_{+} - Fa_{-}) + (alpha2 + K)(1/h) sum_d  */
@@ -361,7 +390,9 @@ int orc_rhs(const orc_grid* g, const double* Q, double* R) {
                 long pc = ((long)(k + 3) * py + (j + 3)) * px + (i + 3);
                 for (int v = 0; v < NV; ++v) W[v * pn + pc] = w[v];
             }
-    /* three ghost layers: copies of interior primitives (no arithmetic) */
+    /* three ghost layers: copies of interior primitives; for bc 2 the     */
+    /* ghosts outside along one axis (the only ones a stencil reads) take */
+    /* the characteristic state of the interior cell next to the face     */
     for (int k = -3; k < nz + 3; ++k)
         for (int j = -3; j < ny + 3; ++j)
             for (int i = -3; i < nx + 3; ++i) {
@@ -369,7 +400,17 @@ int orc_rhs(const orc_grid* g, const double* Q, double* R) {
                 int ks = wrap(k, nz, g->bc), js = wrap(j, ny, g->bc), is = wrap(i, nx, g->bc);
                 long dst = ((long)(k + 3) * py + (j + 3)) * px + (i + 3);
                 long src = ((long)(ks + 3) * py + (js + 3)) * px + (is + 3);
-                for (int v = 0; v < NV; ++v) W[v * pn + dst] = W[v * pn + src];
+                int out_x = i < 0 || i >= nx, out_y = j < 0 || j >= ny, out_z = k < 0 || k >= nz;
+                if (g->bc == 2 && out_x + out_y + out_z == 1) {
+                    int axis = out_x ? 0 : (out_y ? 1 : 2);
+                    int c = out_x ? i : (out_y ? j : k);
+                    double wi[NV], wb[NV];
+                    for (int v = 0; v < NV; ++v) wi[v] = W[v * pn + src];
+                    char_ghost(g, wi, axis, c < 0 ? -1.0 : 1.0, wb);
+                    for (int v = 0; v < NV; ++v) W[v * pn + dst] = wb[v];
+                } else {
+                    for (int v = 0; v < NV; ++v) W[v * pn + dst] = W[v * pn + src];
+                }
             }
 
     for (long c = 0; c < n; ++c)

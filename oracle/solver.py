@@ -28,7 +28,7 @@ class OrcGrid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("bc", C.c_int),
                 ("h", C.c_double), ("gamma1", C.c_double), ("gamma2", C.c_double),
                 ("pc1", C.c_double), ("pc2", C.c_double), ("cfl", C.c_double),
-                ("weno_eps", C.c_double)]
+                ("weno_eps", C.c_double), ("p_inf", C.c_double), ("bc_penalty", C.c_double)]
 
 
 class OrcQoi(C.Structure):
@@ -99,7 +99,7 @@ class Units:
 
 def make_grid(nx: int, ny: Optional[int] = None, nz: Optional[int] = None, *, gamma=(6.12, 1.4),
               pc_nd=(34.3, 0.0), bc: int = 0, h: Optional[float] = None, cfl: float = 0.3,
-              weno_eps: float = 1e-6) -> OrcGrid:
+              weno_eps: float = 1e-6, p_inf: float = 1.0, bc_penalty: float = 1.0) -> OrcGrid:
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     g = OrcGrid()
@@ -109,13 +109,17 @@ def make_grid(nx: int, ny: Optional[int] = None, nz: Optional[int] = None, *, ga
     g.pc1, g.pc2 = pc_nd
     g.cfl = cfl
     g.weno_eps = weno_eps
+    g.p_inf = p_inf
+    g.bc_penalty = bc_penalty
     return g
 
 
 def grid_from_params(sp, N: int) -> OrcGrid:
     u = Units(sp.domain_L, sp.p_liq)
+    # the far field of the characteristic boundary is the liquid pressure p_liq = p_ref
     return make_grid(N, gamma=tuple(sp.gamma), pc_nd=(sp.pc[0] / u.p_ref, sp.pc[1] / u.p_ref),
-                     bc=sp.bc, cfl=sp.cfl, weno_eps=sp.weno_eps)
+                     bc=sp.bc, cfl=sp.cfl, weno_eps=sp.weno_eps, p_inf=1.0,
+                     bc_penalty=getattr(sp, "bc_penalty", 1.0))
 
 
 def cells(g: OrcGrid) -> int:

@@ -478,3 +478,106 @@ def test_cloud_pressure_ramp_is_harmonic_and_continuous():
     q0 = S.init_cloud(W.SolverParams(), N, np.zeros((0, 4)))
     p0 = S.cons_to_prim(g, q0.reshape(7, -1))[5]
     assert np.allclose(p0, 1.0, rtol=1e-13)
+
+
+# ---------------------------------------------------------------- characteristic far-field boundary (Sec. 3.1)
+
+C_LIQ = math.sqrt(GAM[0] * (1.0 + PC[0]))   # liquid sound speed at p = 1, rho = 1 (impedance Z = rho c)
+
+
+def _liquid(n, p, bc, kappa=1.0, rho=None, u=None):
+    g = S.make_grid(n, gamma=GAM, pc_nd=PC, bc=bc, bc_penalty=kappa)
+    Wp = np.zeros((7, n, n, n))
+    Wp[0] = 1.0 if rho is None else rho
+    Wp[5] = p
+    if u is not None:
+        Wp[2] = u
+    return g, S.prim_to_cons(g, Wp.reshape(7, -1)).reshape(7, n, n, n), Wp
+
+
+def _prim(g, Q):
+    n = g.nx
+    return S.cons_to_prim(g, Q.reshape(7, -1)).reshape(7, n, n, n)
+
+
+def test_characteristic_boundary_with_zero_penalty_is_transmissive():
+    sp = W.tiny(16, 4).solver
+    bub = cloud.sample_cloud(W.tiny(16, 4).cloud, W.BASE_SEED, 3)
+    Q0 = S.init_cloud(sp, 16, bub)
+    g0 = S.grid_from_params(sp, 16)
+    g2 = S.grid_from_params(sp, 16)
+    g2.bc, g2.bc_penalty = 2, 0.0
+    a, b = Q0, Q0
+    dt = 0.3 * g0.h / S.max_speed(g0, Q0)
+    for _ in range(2):
+        a = S.rk3_step(g0, a, dt)
+        b = S.rk3_step(g2, b, dt)
+    assert np.array_equal(a, b)
+
+
+def test_characteristic_boundary_keeps_the_far_field_at_rest():
+    g, Q, _ = _liquid(8, 1.0, 2)
+    dt = 0.3 * g.h / S.max_speed(g, Q)
+    Q1 = Q
+    for _ in range(3):
+        Q1 = S.rk3_step(g, Q1, dt)
+    assert np.array_equal(Q1, Q)
+
+
+def test_characteristic_boundary_admits_the_far_field_wave_of_linear_acoustics():
+    """Liquid at rest at p0 = p_inf - d: each face admits the wave of the
+    acoustic Riemann problem against the far field, p0 + d/2 moving inwards
+    at d/(2 Z), and the incoming characteristic at the face carries p_inf.
+    At t = L/(4c) the face centres are still reached by their own face's
+    wave only."""
+    n, d = 32, 0.01
+    p0 = 1.0 - d
+    g, Q, _ = _liquid(n, p0, 2)
+    c = math.sqrt(GAM[0] * (p0 + PC[0]))
+    Z = c
+    Qt, _ = S.advance(g, Q, 0.25 / c)
+    Wn = _prim(g, Qt)
+    p, u = Wn[5][16, 16, :], Wn[2][16, 16, :]
+    for i, sgn in ((0, 1.0), (n - 1, -1.0)):      # low face: wave moves +x; high face: -x
+        assert abs((p[i] - p0) / d - 0.5) < 0.03, (i, p[i])
+        assert abs(u[i] * sgn * 2.0 * Z / d - 1.0) < 0.03, (i, u[i])
+        # incoming characteristic p - Z u_n (u_n outward = -sgn u) equals the far field
+        assert abs(p[i] + sgn * Z * u[i] - 1.0) < 0.01 * d
+    # the middle of the domain has not been reached by a wave front
+    assert abs(p[n // 2] - p0) < 0.05 * d and abs(u[n // 2]) < 0.05 * d / Z
+
+
+def test_characteristic_boundary_relaxes_the_domain_to_the_far_field_pressure():
+    """The penalty term drives the pressure to p_inf (the transmissive
+    boundary keeps the initial state for ever)."""
+    n, d = 16, 0.01
+    for bc, want in ((2, 0.01), (0, None)):
+        g, Q, _ = _liquid(n, 1.0 - d, bc)
+        Qt, _ = S.advance(g, Q, 3.0 / C_LIQ)
+        pm = np.mean(np.abs(_prim(g, Qt)[5] - 1.0)) / d
+        if want is None:
+            assert abs(pm - 1.0) < 1e-12
+        else:
+            assert pm < want
+
+
+def test_characteristic_boundary_lets_an_acoustic_pulse_leave():
+    """A Gaussian pressure pulse next to the x = L face: once the direct
+    waves have left (t = 1.2 L/c) little acoustic energy is reflected back,
+    less than with the transmissive boundary."""
+    n, d = 24, 0.01
+    x = (np.arange(n) + 0.5) / n
+    Zc, Yc, Xc = np.meshgrid(x, x, x, indexing="ij")
+    gs = np.exp(-0.5 * (np.sqrt((Xc - 0.85) ** 2 + (Yc - 0.5) ** 2 + (Zc - 0.5) ** 2) / 0.05) ** 2)
+
+    def energy(Wp):
+        return np.sum(0.5 * (Wp[5] - 1.0) ** 2 / C_LIQ ** 2 + 0.5 * (Wp[2] ** 2 + Wp[3] ** 2 + Wp[4] ** 2))
+
+    left = {}
+    for bc in (2, 0):
+        g, _, Wp = _liquid(n, 1.0 + d * gs, bc, rho=1.0 + d * gs / C_LIQ ** 2)
+        Q = S.prim_to_cons(g, Wp.reshape(7, -1)).reshape(7, n, n, n)
+        Qt, _ = S.advance(g, Q, 1.2 / C_LIQ)
+        left[bc] = energy(_prim(g, Qt)) / energy(Wp)
+    assert left[2] < 1e-3
+    assert left[2] < 0.5 * left[0]

@@ -52,7 +52,8 @@ class SolverParams:
     p_liq: float = 1.0e7
     cfl: float = 0.3
     t_end: float = T_END_CONFIG
-    bc: int = 0                    # 0 transmissive, 1 periodic
+    bc: int = 0                    # 0 transmissive, 1 periodic, 2 characteristic far field at p_liq
+    bc_penalty: float = 1.0        # kappa of the characteristic boundary (0 = transmissive)
     weno_eps: float = 1e-6
     max_steps: int = 100000
     domain_L: float = DOMAIN_L
