@@ -41,7 +41,15 @@ enum {
 };
 
 enum { OFM_FP64 = 0, OFM_FP32 = 1 };                      /* stencil storage/arithmetic */
-enum { OFM_BC_TRANSMISSIVE = 0, OFM_BC_PERIODIC = 1 };    /* ghost cells */
+/* Ghost cells: transmissive (nearest interior cell), periodic, or the
+ * characteristic far field of Sec. 3.1 (non-reflecting, with a penalty
+ * towards the far-field pressure p_liq, after Poinsot and Lele 1992): along
+ * the outward normal, with Z = rho c of the interior cell next to the face,
+ * the outgoing characteristic p + Z u_n is that cell's and the incoming one
+ * p - Z u_n is (1 - bc_penalty) times that cell's plus bc_penalty times the
+ * far field at rest, p_liq; partial densities, alpha2 and the tangential
+ * velocities are that cell's. */
+enum { OFM_BC_TRANSMISSIVE = 0, OFM_BC_PERIODIC = 1, OFM_BC_CHARACTERISTIC = 2 };
 enum { OFM_RADII_UNIFORM = 0, OFM_RADII_LOGNORMAL = 1 };  /* cloud radius law */
 enum { OFM_MODE_TOL = 0, OFM_MODE_BUDGET = 1 };           /* sample-number optimisation */
 
@@ -98,6 +106,9 @@ typedef struct {
      * pressure of a liquid at rest around a sphere); 0 = uniform p_liq. */
     double p_cloud;
     double ramp_radius;
+    double bc_penalty;  /* OFM_BC_CHARACTERISTIC: weight in [0, 1] of the far field in the incoming
+                           characteristic (0 = transmissive, 1 = no reflection of a plane wave
+                           leaving along the normal and full penalty); ignored otherwise */
 } ofm_solver_config;
 
 /* Per-sample quantities of interest (Section 3.2). */

@@ -825,6 +825,47 @@ __device__ __forceinline__ void fill_rows(int* sRow) {
     }
 }
 
+// Characteristic far-field ghost (Sec. 3.1, after Poinsot and Lele): the
+// slot holds the primitives of the interior cell next to the face (staged
+// through the transmissive map); along the outward normal (side s) with
+// Z = rho c of that cell, the outgoing characteristic p + Z u_n stays that
+// cell's and the incoming p - Z u_n becomes (1 - kappa) of that cell's plus
+// kappa of the far field at rest at p_inf.  Rewrites p and the normal
+// velocity in place; same operation order as the oracle.
+template <typename T>
+__device__ __forceinline__ void char_ghost(const Eos<T>& e, T pinf, T kappa, T* sW, int si, int axis, T s) {
+    const T rho = sW[si] + sW[NCROSS + si];
+    const T p = sW[5 * NCROSS + si];
+    T G, Pi;
+    closure(e, sW[6 * NCROSS + si], G, Pi);
+    const T Z = rho * sqrt(((G + T(1)) * p + Pi) / (G * rho));
+    const T un = s * sW[(2 + axis) * NCROSS + si];
+    sW[5 * NCROSS + si] = p + T(0.5) * kappa * (pinf - p + Z * un);
+    sW[(2 + axis) * NCROSS + si] = s * (un + T(0.5) * kappa * (p - pinf - Z * un) / Z);
+}
+
+// The characteristic ghosts of a tile: the three halo layers behind each
+// tile face that lies on a domain face (ghosts outside along one axis only,
+// the only ones a stencil reads; every layer takes the same state).
+template <typename T>
+__device__ __forceinline__ void tile_char_bc(const Params<T>& P, const BlockWork<T>& bw, T* sW) {
+    const int N = bw.G->N;
+    const T pinf = (T)P.p_liq, kappa = (T)P.bc_penalty;
+    constexpr int PER = HALO * TS * TS;
+    for (int u = threadIdx.x; u < 6 * PER; u += NT) {
+        const int face = u / PER, r = u - face * PER;
+        const int axis = face >> 1, hi = face & 1;
+        const int o = axis == 0 ? bw.x0 : (axis == 1 ? bw.y0 : bw.z0);
+        if (hi ? (o + TS < N) : (o > 0)) continue;   // an interior tile face
+        const int layer = r / (TS * TS), a = (r / TS) % TS, b = r % TS;
+        const int off = hi ? TS + layer : -1 - layer;
+        const int x = axis == 0 ? off : b;
+        const int y = axis == 1 ? off : (axis == 0 ? b : a);
+        const int z = axis == 2 ? off : a;
+        char_ghost(P.eos, pinf, kappa, sW, row_off(y, z) + x, axis, hi ? T(1) : T(-1));
+    }
+}
+
 // Raw Q of every staged cell -> primitives, in place.
 template <typename T>
 __device__ __forceinline__ void tile_convert(const Eos<T>& e, T* sW) {
@@ -1071,6 +1112,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
     cp_async_wait_all();
     __syncthreads();
     tile_convert(P.eos, sW);
+    if (P.bc == OFM_BC_CHARACTERISTIC) {
+        __syncthreads();
+        tile_char_bc(P, c.bw, sW);
+    }
     __syncthreads();
     tile_body<T, STAGE>(P, c, (long long)blockIdx.x, sW, sF, sRow);
 }
@@ -1118,6 +1163,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
         cp_async_wait_all();
         __syncthreads();
         tile_convert(P.eos, sW);
+        if (P.bc == OFM_BC_CHARACTERISTIC) {
+            __syncthreads();
+            tile_char_bc(P, c.bw, sW);
+        }
         __syncthreads();
         TileRhs<T> R;
         tile_faces<T>(P, c, sW, sF, sRow, R);

@@ -189,6 +189,7 @@ void fill_params(ofm_batch* b, Params<T>& P) {
         P.rkB[s] = RK_B[s];
     }
     P.bc = c.bc;
+    P.bc_penalty = c.bc_penalty;
     P.nb = b->nb;
     P.n_sens = c.n_sensors;
     P.n_out = c.n_out_times;
@@ -283,8 +284,10 @@ extern "C" int ofm_solver_create(ofm_solver** out, const ofm_solver_config* c) {
         return fail(OFM_EINVAL, "ofm_solver_create: non-physical configuration");
     if (c->precision != OFM_FP64 && c->precision != OFM_FP32)
         return fail(OFM_EINVAL, "ofm_solver_create: precision must be OFM_FP64 or OFM_FP32");
-    if (c->bc != OFM_BC_TRANSMISSIVE && c->bc != OFM_BC_PERIODIC)
+    if (c->bc != OFM_BC_TRANSMISSIVE && c->bc != OFM_BC_PERIODIC && c->bc != OFM_BC_CHARACTERISTIC)
         return fail(OFM_EINVAL, "ofm_solver_create: unknown boundary condition");
+    if (c->bc == OFM_BC_CHARACTERISTIC && !(c->bc_penalty >= 0.0 && c->bc_penalty <= 1.0))
+        return fail(OFM_EINVAL, "ofm_solver_create: bc_penalty must lie in [0, 1]");
     if (c->n_sensors < 0 || c->n_sensors > OFM_MAX_SENSORS || c->n_out_times < 0 || c->max_steps < 1)
         return fail(OFM_EINVAL, "ofm_solver_create: bad sensor / output / step settings");
     ofm_solver* s = new (std::nothrow) ofm_solver;

@@ -148,6 +148,7 @@ void static_params(const ofm_solver* s, int N, int M, int nb, unsigned char* ws,
         P.rkB[k] = RK_B[k];
     }
     P.bc = c.bc;
+    P.bc_penalty = c.bc_penalty;
     P.nb = nb;
     P.n_sens = c.n_sensors;
     P.n_out = c.n_out_times;

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libofmlmc.so")
 
 OFM_OK, OFM_EINVAL, OFM_ENOMEM, OFM_ECUDA, OFM_ENUMERIC, OFM_ETIMEOUT = 0, -1, -2, -3, -4, -5
 OFM_FP64, OFM_FP32 = 0, 1
-OFM_BC_TRANSMISSIVE, OFM_BC_PERIODIC = 0, 1
+OFM_BC_TRANSMISSIVE, OFM_BC_PERIODIC, OFM_BC_CHARACTERISTIC = 0, 1, 2
 OFM_RADII_UNIFORM, OFM_RADII_LOGNORMAL = 0, 1
 OFM_MODE_TOL, OFM_MODE_BUDGET = 0, 1
 OFM_ST_NONFINITE, OFM_ST_NEGATIVE, OFM_ST_MAXSTEPS = 1, 2, 4
@@ -39,7 +39,8 @@ class ofm_solver_config(C.Structure):
                 ("t_end", C.c_double), ("weno_eps", C.c_double), ("domain_L", C.c_double),
                 ("precision", C.c_int), ("bc", C.c_int), ("max_steps", C.c_int),
                 ("n_sensors", C.c_int), ("sensors", (C.c_double * 4) * OFM_MAX_SENSORS),
-                ("n_out_times", C.c_int), ("p_cloud", C.c_double), ("ramp_radius", C.c_double)]
+                ("n_out_times", C.c_int), ("p_cloud", C.c_double), ("ramp_radius", C.c_double),
+                ("bc_penalty", C.c_double)]
 
 
 class ofm_qoi(C.Structure):

@@ -90,7 +90,7 @@ def test_one_step_with_cloud_pressure_ramp(precision, tol):
     10 MPa from 1 mm beyond the cloud surface) on 24^3: the initial state and one
     step against the oracle."""
     N = 24
-    sp = W.solver_paper500()
+    sp = W.solver_paper500(bc=nv.OFM_BC_TRANSMISSIVE)
     cloud = W.cloud_uniform(20)
     ids = [0, 3]
     s, groups, b = gpu_batch(sp, precision, [(N, ids)], cloud)
@@ -120,6 +120,52 @@ def test_one_step_fp64_periodic_smooth_field():
     dt = sp.cfl * g.h / osolver.max_speed(g, Q0)
     ref = osolver.rk3_step(g, Q0, dt)
     assert np.all(rel_l1(b.state(0, 0), ref) <= TOL_STEP_FP64)
+    b.close()
+
+
+@pytest.mark.parametrize("precision,tol,kappa,variant", [("fp64", TOL_STEP_FP64, 1.0, 0),
+                                                          ("fp64", TOL_STEP_FP64, 0.5, 1),
+                                                          ("fp32", TOL_STEP_FP32, 1.0, 0),
+                                                          ("fp32", TOL_STEP_FP32, 1.0, 1)])
+def test_one_step_characteristic_boundary(precision, tol, kappa, variant):
+    """Sec. 3.1 setup with the characteristic far-field boundary on 24^3 (the
+    ramp leaves ~6 MPa at the faces against the 10 MPa far field, so the
+    ghosts differ from the transmissive ones from the first stage): one step
+    of both stage-kernel variants against the oracle."""
+    from dataclasses import replace
+    N = 24
+    sp = replace(W.solver_paper500(), bc=nv.OFM_BC_CHARACTERISTIC, bc_penalty=kappa)
+    cloud = W.cloud_uniform(20)
+    ids = [0, 3]
+    s, groups, b = gpu_batch(sp, precision, [(N, ids)], cloud)
+    b.set_variant(variant)
+    b.init()
+    b.run(1)
+    for i, sid in enumerate(ids):
+        bub = ocloud.sample_cloud(cloud, W.BASE_SEED, sid)
+        ref = oracle_one_step(sp, N, bub)
+        got = b.state(0, i)
+        assert np.all(rel_l1(got, ref) <= tol), (sid, rel_l1(got, ref))
+        trans = oracle_one_step(replace(sp, bc=nv.OFM_BC_TRANSMISSIVE), N, bub)
+        assert np.max(rel_l1(got, trans)) > 100 * tol   # the boundary did act
+    b.close()
+
+
+def test_characteristic_boundary_qois_at_t_end_fp64():
+    from dataclasses import replace
+    w = W.tiny(16, 4)
+    sp = replace(w.solver, bc=nv.OFM_BC_CHARACTERISTIC, p_cloud=0.5e6, p_gas=0.5e6, ramp_radius=0.035)
+    ids = [0, 1]
+    s, groups, b = gpu_batch(sp, "fp64", [(16, ids)], w.cloud)
+    b.init()
+    while b.run(64) > 0:
+        pass
+    b.qoi()
+    got = groups[0].qoi_dicts(len(sp.sensors))
+    ref = oracle_qois(sp, 16, w.cloud, ids)
+    for i in range(2):
+        compare_qoi(got[i], groups[0].hist[i], ref[i][0], ref[i][1], TOL_QOI_FP64, len(sp.sensors),
+                    ag=groups[0].alpha_hist[i])
     b.close()
 
 

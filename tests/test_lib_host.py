@@ -111,6 +111,12 @@ def test_invalid_arguments_are_rejected_on_the_host():
     cfg = api.solver_config(W.SolverParams(), "fp64")
     cfg.ramp_radius, cfg.p_cloud = 0.02, 0.0          # a ramp needs a cloud pressure
     assert L.ofm_solver_create(C.byref(h), C.byref(cfg)) == nv.OFM_EINVAL
+    for bc, kappa in ((3, 1.0), (nv.OFM_BC_CHARACTERISTIC, 1.5), (nv.OFM_BC_CHARACTERISTIC, -0.1)):
+        cfg = api.solver_config(W.SolverParams(bc=bc, bc_penalty=kappa), "fp64")
+        assert L.ofm_solver_create(C.byref(h), C.byref(cfg)) == nv.OFM_EINVAL, (bc, kappa)
+    cfg = api.solver_config(W.SolverParams(bc=nv.OFM_BC_CHARACTERISTIC, bc_penalty=0.25), "fp64")
+    assert L.ofm_solver_create(C.byref(h), C.byref(cfg)) == nv.OFM_OK
+    L.ofm_solver_destroy(h)
     # estimator needs two samples per level
     with pytest.raises(nv.OfmError):
         api.estimate([np.zeros((1, 2)), np.zeros((5, 2))], [1.0, 2.0])

@@ -127,8 +127,10 @@ def cfg3() -> Workload:
 
 def solver_paper500(**kw) -> SolverParams:
     """Section 3.1 pressures: bubbles and the liquid around them at 0.5 MPa, rising
-    from 1 mm beyond the 20 mm cloud surface towards p_inf = 10 MPa."""
+    from 1 mm beyond the 20 mm cloud surface towards p_inf = 10 MPa; characteristic
+    far-field boundaries at p_inf."""
     kw.setdefault("sensors", centre_sensor())
+    kw.setdefault("bc", 2)
     return SolverParams(p_gas=0.5e6, p_liq=1.0e7, p_cloud=0.5e6, ramp_radius=0.021, **kw)
 
 
