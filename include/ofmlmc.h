@@ -304,9 +304,11 @@ int ofm_estimate(int L, const int64_t* M, const double* const* q, const double* 
  *     the posterior mean of (a, b) under flat priors.  Writes
  *     V_fit[l] = exp(a + b l) for l = 1..L, V_fit[0] = 0, and coef = {a, b}
  *     (coef may be NULL).  OFM_EINVAL with fewer than two usable levels.
- *   ofm_estimate_fitted: ofm_estimate with the fitted variances: the
- *     covariances of Eq. (alpha-matvec) become (sigma2_l + sigma2_{l-1} -
- *     V_fit_l)/2 and are returned in out->cov.  Level 0 needs M >= 2, every
+ *   ofm_estimate_fitted: ofm_estimate with the fitted variances, each
+ *     clamped to [(sigma_l - sigma_{l-1})^2, (sigma_l + sigma_{l-1})^2] (so
+ *     that |cov_l| <= sigma_l sigma_{l-1}): the covariances of Eq.
+ *     (alpha-matvec) become (sigma2_l + sigma2_{l-1} - V_fit_l)/2 and are
+ *     returned in out->cov.  Level 0 needs M >= 2, every
  *     level l >= 1 at least one pair; a level whose q_l has a single computed
  *     value takes sigma2_l = sigma2_{l-1}, and a level with one pair takes
  *     sigma_tilde2_l = alpha_l^2 sigma2_l + alpha_{l-1}^2 sigma2_{l-1}
@@ -344,7 +346,9 @@ int ofm_estimate_moments(int L, const ofm_level_moments* moments, const double* 
 
 /* Eq. (M-tol) (mode OFM_MODE_TOL, target = tau, constraint eps_OF <= tau) or
  * Eq. (M-budget) (OFM_MODE_BUDGET, target = budget) with the step-7 rule that
- * keeps already computed samples (M_done may be NULL = none). */
+ * keeps already computed samples (M_done may be NULL = none).  OFM_EINVAL for a
+ * negative or non-finite sigma_tilde2, W <= 0, a target the kept samples
+ * already exceed, or a level that would need more than 4e18 samples. */
 int ofm_optimal_samples(int L, const double* sigma_tilde2, const double* W, const int64_t* M_done,
                         double target, int mode, int64_t* M_out);
 
@@ -362,9 +366,11 @@ int ofm_warmup_samples(int L, const double* W, int64_t* M_out);
  * pairs in one uneven batch (split only if it exceeds max_batch_bytes; 0 =
  * 80% of the free device memory), measures the pair costs W_l as mean
  * cell-steps per pair, excludes pairs with a failed member (status != 0),
- * computes the estimator (ofm_estimate, or ofm_estimate_fitted) and stops when eps_OF <= target (tol
- * mode) or the cell-steps spent reach target (budget mode); otherwise step 7
- * re-optimises M_l (ofm_optimal_samples, keeping computed pairs).
+ * computes the estimator (ofm_estimate, or ofm_estimate_fitted) and stops
+ * when eps_OF <= target (tol mode) or the cell-steps spent reach target
+ * (budget mode); otherwise, unless
+ * it was the last of max_iterations, step 7 re-optimises M_l
+ * (ofm_optimal_samples, keeping computed pairs).
  * pairs_out / ids_out (host, may be NULL): the (q_l, q_{l-1}) rows and sample
  * ids of the pairs used, level by level; pairs_capacity rows.
  * ------------------------------------------------------------------------- */

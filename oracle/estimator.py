@@ -33,8 +33,10 @@ Readings of points the paper leaves open:
     the covariances: ln V_l = a + b l by least squares over the levels l >= 1
     with at least two pairs, each weighted by the inverse of the Gaussian
     error of ln V_l, Var[ln V_l] ~ 2/(M_l - 1) (the posterior mean under
-    flat priors); the fitted V_l give the covariances of Eq. (alpha-matvec)
-    as (sigma^2_l + sigma^2_{l-1} - V_l)/2; a level with one pair takes
+    flat priors); the fitted V_l, clamped to [(sigma_l - sigma_{l-1})^2,
+    (sigma_l + sigma_{l-1})^2] (the range in which the second moments of
+    (q_l, q_{l-1}) stay positive semi-definite), give the covariances of
+    Eq. (alpha-matvec) as (sigma^2_l + sigma^2_{l-1} - V_l)/2; a level with one pair takes
     sigma^2_l = sigma^2_{l-1} (no sample variance exists) and its sigma~^2_l
     from the fitted second moments.
 """
@@ -204,6 +206,10 @@ def estimate_fitted(pairs, W):
     a, b, V_fit = fit_diff_variances(diff_variances(pairs), M)
     cov = np.zeros(L + 1)
     for l in range(1, L + 1):
+        # Cauchy-Schwarz: |Cov| <= sigma_l sigma_{l-1}
+        lo = (math.sqrt(sigma2[l]) - math.sqrt(sigma2[l - 1])) ** 2
+        hi = (math.sqrt(sigma2[l]) + math.sqrt(sigma2[l - 1])) ** 2
+        V_fit[l] = min(max(V_fit[l], lo), hi)
         cov[l] = 0.5 * (sigma2[l] + sigma2[l - 1] - V_fit[l])
     alpha = alpha_optimal(sigma2, cov, W)
     st2 = np.zeros(L + 1)

@@ -2,6 +2,7 @@
 // OF-MLMC estimator (Section 2.4 of the paper).  All FP64; compiled with
 // -ffp-contract=off so the sampler's arithmetic rounds identically on x86 and
 // Arm hosts.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -210,7 +211,10 @@ int estimate_core(int L, const int64_t* M, const double* const* q, const double*
         int rc = fit_line(L, M, V.data(), &a, &b);
         if (rc != OFM_OK) return rc;
         for (int l = 1; l <= L; ++l) {
-            const double vf = std::exp(a + b * (double)l);
+            // clamped so that |Cov| <= sigma_l sigma_{l-1} (positive semi-definite second moments)
+            const double sl = std::sqrt(out->sigma2[l]), sm = std::sqrt(out->sigma2[l - 1]);
+            const double lo = (sl - sm) * (sl - sm), hi = (sl + sm) * (sl + sm);
+            const double vf = std::min(std::max(std::exp(a + b * (double)l), lo), hi);
             out->cov[l] = 0.5 * (out->sigma2[l] + out->sigma2[l - 1] - vf);
             if (V_fit_out) V_fit_out[l] = vf;
         }
@@ -363,6 +367,10 @@ extern "C" int ofm_optimal_samples(int L, const double* st2, const double* W, co
         (mode != OFM_MODE_TOL && mode != OFM_MODE_BUDGET))
         return fail(OFM_EINVAL, "ofm_optimal_samples: bad arguments");
     const int n = L + 1;
+    for (int l = 0; l < n; ++l)
+        if (!(st2[l] >= 0.0) || !std::isfinite(st2[l]) || !(W[l] > 0.0))
+            return fail(OFM_EINVAL, "ofm_optimal_samples: sigma_tilde2[%d] or W[%d] is not a finite positive value", l,
+                        l);
     bool fixed[OFM_MAX_LEVELS] = {false};
     for (;;) {
         double rem = mode == OFM_MODE_TOL ? target * target : target;
@@ -388,6 +396,8 @@ extern "C" int ofm_optimal_samples(int L, const double* st2, const double* W, co
             }
             double raw = mode == OFM_MODE_TOL ? (1.0 / (t * t)) * std::sqrt(st2[l] / W[l]) * total
                                               : t * std::sqrt(st2[l] / W[l]) / total;
+            if (!(raw < 4.0e18))
+                return fail(OFM_EINVAL, "ofm_optimal_samples: level %d needs more than 4e18 samples", l);
             M_out[l] = (int64_t)std::ceil(raw);
             if (M_done && M_out[l] < M_done[l]) {
                 fixed[l] = true;

@@ -218,6 +218,7 @@ extern "C" int ofm_run(ofm_solver* s, const ofm_cloud_params* cloud, const ofm_r
         res->gpu_seconds = gpu_ms * 1e-3;
         // step 6: stop?
         if (rc->mode == OFM_MODE_TOL ? std::sqrt(res->est.eps2) <= rc->target : spent >= rc->target) break;
+        if (it + 1 == rc->max_iterations) break;   // no iteration left to take step 7's numbers
         // step 7: optimal numbers, keeping what is computed
         std::vector<int64_t> done(L + 1);
         for (int l = 0; l <= L; ++l) done[l] = lv[l].computed;

@@ -85,6 +85,23 @@ def test_fitted_estimator_matches_oracle():
         api.estimate(W.toy_levels([1, 20, 20], 2, 0.4, 0.7, seed=1), [1.0, 17.0, 272.0], fit=True)
     with pytest.raises(nv.OfmError):
         api.fit_level_variances([0.0, 0.3, -1.0], [0, 5, 5])
+    # few pairs: the clamped fit agrees with the oracle where the clamp acts
+    Wc = [4096.0, 69632.0, 397312.0, 1380352.0]
+    for seed in (6, 26, 95):
+        pairs = W.toy_levels([43, 5, 2, 1], 3, 0.4, 0.7, seed=seed)
+        a = api.estimate(pairs, Wc, fit=True)
+        b = E.estimate_fitted(pairs, Wc)
+        for k in ("alpha", "cov", "sigma_tilde2", "V_fit"):
+            assert np.allclose(a[k][1:], b[k][1:], rtol=1e-11, atol=1e-13), (seed, k)
+        assert np.all(a["sigma_tilde2"] >= 0.0)
+
+
+def test_optimal_samples_rejects_invalid_variances_and_overflow():
+    for st2 in ([1.0, -0.1], [1.0, float("nan")]):
+        with pytest.raises(nv.OfmError):
+            api.optimal_samples(st2, [1.0, 17.0], 0.1, "tol")
+    with pytest.raises(nv.OfmError):
+        api.optimal_samples([1.0, 0.5], [1.0, 17.0], 1e-12, "tol")
 
 
 def test_optimal_and_warmup_samples_match_oracle():

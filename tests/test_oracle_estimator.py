@@ -317,6 +317,24 @@ def test_fitted_estimator_with_one_finest_pair():
         E.estimate_fitted(Wk.toy_levels([100, 100, 1], 2, a, b, seed=4), W[:3])
 
 
+def test_fitted_moments_stay_positive_semi_definite_with_few_pairs():
+    """With two or three pairs a level's fitted V_l can leave the range a
+    covariance allows; clamped, |Cov_l| <= sigma_l sigma_{l-1} and every
+    sigma~^2 is a variance (>= 0), including the modelled finest one."""
+    Wc = [4096.0, 69632.0, 397312.0, 1380352.0]
+    clamped = 0
+    for seed in range(300):
+        pairs = Wk.toy_levels([43, 5, 2, 1], 3, 0.4, 0.7, seed=seed)
+        est = E.estimate_fitted(pairs, Wc)
+        s2, cov = est["sigma2"], est["cov"]
+        for l in range(1, 4):
+            assert abs(cov[l]) <= math.sqrt(s2[l] * s2[l - 1]) * (1 + 1e-12)
+        assert np.all(est["sigma_tilde2"] >= -1e-12 * np.max(s2))
+        free = E.fit_diff_variances(E.diff_variances(pairs), [43, 5, 2, 1])[2]
+        clamped += int(not np.allclose(free[1:], est["V_fit"][1:], rtol=1e-14))
+    assert clamped > 0        # the clamp was exercised
+
+
 def test_adaptive_loop_with_fit_starts_the_finest_level_from_one_pair():
     L, a, b = 3, 0.4, 0.6
     mean, _, _ = toy_moments(L, a, b)
