@@ -73,6 +73,7 @@ typedef struct {
     double weno_eps;
     double p_inf;      /* far-field pressure of bc 2, non-dimensional */
     double bc_penalty; /* kappa of bc 2 in [0, 1]: 0 = transmissive, 1 = far field */
+    int weno_order;    /* 5 (WENO5) or 3 (WENO3) */
 } orc_grid;
 
 /* ------------------------------------------------------------------ */
@@ -185,6 +186,26 @@ double orc_weno5(double a, double b, double c, double d, double e, double eps) {
        convex combination 3 mul + 4 add + 1 div */
     FL(16 + 33 + 9 + 8);
     return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+}
+
+/* ------------------------------------------------------------------ */
+/* WENO3 of Jiang & Shu (1996), the paper's third-order option: value at */
+/* the right face of the cell holding b from the averages a, b, c.       */
+/* Candidates (3b - a)/2 on {a, b} and (b + c)/2 on {b, c}, smoothness   */
+/* (b - a)^2 and (c - b)^2, ideal weights (1/3, 2/3),                    */
+/* alpha_k = d_k/(eps + beta_k)^2.  The left face of the same cell is   */
+/* the same formula with the three averages reversed.                    */
+/* ------------------------------------------------------------------ */
+double orc_weno3(double a, double b, double c, double eps) {
+    double q0 = 0.5 * (3.0 * b - a);
+    double q1 = 0.5 * (b + c);
+    double b0 = (b - a) * (b - a);
+    double b1 = (c - b) * (c - b);
+    double w0 = (1.0 / 3.0) / ((eps + b0) * (eps + b0));
+    double w1 = (2.0 / 3.0) / ((eps + b1) * (eps + b1));
+    /* candidates 3 + 2; smoothness 2 x 2; alphas 2 x 3; combination 2 mul + 2 add + 1 div */
+    FL(5 + 4 + 6 + 5);
+    return (w0 * q0 + w1 * q1) / (w0 + w1);
 }
 
 /* Face-state admissibility for the fallback of the positivity reading:
@@ -437,8 +458,13 @@ int orc_rhs(const orc_grid* g, const double* Q, double* R) {
                             const double* P = W + v * pn;
                             double m2 = P[base - 2 * st], m1 = P[base - st], c0 = P[base];
                             double p1 = P[base + st], p2 = P[base + 2 * st];
-                            wl[v] = orc_weno5(m2, m1, c0, p1, p2, g->weno_eps);
-                            wr[v] = orc_weno5(P[base + 3 * st], p2, p1, c0, m1, g->weno_eps);
+                            if (g->weno_order == 3) {
+                                wl[v] = orc_weno3(m1, c0, p1, g->weno_eps);
+                                wr[v] = orc_weno3(p2, p1, c0, g->weno_eps);
+                            } else {
+                                wl[v] = orc_weno5(m2, m1, c0, p1, p2, g->weno_eps);
+                                wr[v] = orc_weno5(P[base + 3 * st], p2, p1, c0, m1, g->weno_eps);
+                            }
                             wcl[v] = c0;
                             wcr[v] = p1;
                         }

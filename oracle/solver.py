@@ -28,7 +28,8 @@ class OrcGrid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("bc", C.c_int),
                 ("h", C.c_double), ("gamma1", C.c_double), ("gamma2", C.c_double),
                 ("pc1", C.c_double), ("pc2", C.c_double), ("cfl", C.c_double),
-                ("weno_eps", C.c_double), ("p_inf", C.c_double), ("bc_penalty", C.c_double)]
+                ("weno_eps", C.c_double), ("p_inf", C.c_double), ("bc_penalty", C.c_double),
+                ("weno_order", C.c_int)]
 
 
 class OrcQoi(C.Structure):
@@ -55,6 +56,8 @@ def _lib(count: bool = False) -> C.CDLL:
         lib.orc_cons_to_prim_array.argtypes = [G, _D, _D, C.c_long]
         lib.orc_weno5.argtypes = [C.c_double] * 6
         lib.orc_weno5.restype = C.c_double
+        lib.orc_weno3.argtypes = [C.c_double] * 4
+        lib.orc_weno3.restype = C.c_double
         lib.orc_hllc.argtypes = [G, _D, _D, C.c_int, _D, _D]
         lib.orc_rhs.argtypes = [G, _D, _D]
         lib.orc_rhs.restype = C.c_int
@@ -99,7 +102,8 @@ class Units:
 
 def make_grid(nx: int, ny: Optional[int] = None, nz: Optional[int] = None, *, gamma=(6.12, 1.4),
               pc_nd=(34.3, 0.0), bc: int = 0, h: Optional[float] = None, cfl: float = 0.3,
-              weno_eps: float = 1e-6, p_inf: float = 1.0, bc_penalty: float = 1.0) -> OrcGrid:
+              weno_eps: float = 1e-6, p_inf: float = 1.0, bc_penalty: float = 1.0,
+              weno_order: int = 5) -> OrcGrid:
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     g = OrcGrid()
@@ -111,6 +115,7 @@ def make_grid(nx: int, ny: Optional[int] = None, nz: Optional[int] = None, *, ga
     g.weno_eps = weno_eps
     g.p_inf = p_inf
     g.bc_penalty = bc_penalty
+    g.weno_order = weno_order
     return g
 
 
@@ -119,7 +124,7 @@ def grid_from_params(sp, N: int) -> OrcGrid:
     # the far field of the characteristic boundary is the liquid pressure p_liq = p_ref
     return make_grid(N, gamma=tuple(sp.gamma), pc_nd=(sp.pc[0] / u.p_ref, sp.pc[1] / u.p_ref),
                      bc=sp.bc, cfl=sp.cfl, weno_eps=sp.weno_eps, p_inf=1.0,
-                     bc_penalty=getattr(sp, "bc_penalty", 1.0))
+                     bc_penalty=getattr(sp, "bc_penalty", 1.0), weno_order=getattr(sp, "weno_order", 5))
 
 
 def cells(g: OrcGrid) -> int:
@@ -144,6 +149,10 @@ def cons_to_prim(g: OrcGrid, Q: np.ndarray) -> np.ndarray:
 
 def weno5(a, b, c, d, e, eps=1e-6) -> float:
     return _lib().orc_weno5(a, b, c, d, e, eps)
+
+
+def weno3(a, b, c, eps=1e-6) -> float:
+    return _lib().orc_weno3(a, b, c, eps)
 
 
 def hllc(g: OrcGrid, wl, wr, direction: int):

@@ -91,6 +91,74 @@ def test_weno5_fifth_order_on_smooth_data():
     assert math.log2(e1 / e2) > 4.5
 
 
+# ---------------------------------------------------------------- WENO3 (Jiang & Shu, the third-order option)
+
+def test_weno3_exact_on_linear_data():
+    """Both candidates reproduce a linear function: any weights give the exact face value."""
+    rng = np.random.default_rng(8)
+    for _ in range(50):
+        a, b = rng.normal(size=2) * np.array([1.0, 5.0])
+        v = [a + b * i for i in (-1, 0, 1)]     # averages of a + b x over unit cells
+        assert abs(S.weno3(*v) - (a + 0.5 * b)) < 1e-13 * (abs(a) + abs(b))
+        assert abs(S.weno3(*v[::-1]) - (a - 0.5 * b)) < 1e-13 * (abs(a) + abs(b))
+
+
+def test_weno3_ideal_weights_are_third_order_linear_scheme():
+    """Symmetric data (equal smoothness of both sub-stencils) gives the ideal weights
+    1/3, 2/3, whose combination is exact for the averages of a parabola."""
+    for c in (1.0, -2.5, 7.0):
+        avg = [c * (i * i + 1.0 / 12.0) for i in (-1, 0, 1)]   # averages of c x^2
+        assert abs(S.weno3(*avg) - c * 0.25) < 1e-14 * abs(c)
+
+
+def test_weno3_third_order_on_smooth_monotone_data():
+    def err(n):
+        h = 0.5 / n
+        x = (np.arange(-1, n + 2) + 0.5) * h
+        avg = (np.exp(x + 0.5 * h) - np.exp(x - 0.5 * h)) / h
+        return max(abs(S.weno3(*avg[i - 1:i + 2]) - math.exp(x[i] + 0.5 * h)) for i in range(1, n + 1))
+    e1, e2 = err(40), err(80)
+    assert math.log2(e1 / e2) > 2.6
+
+
+def test_weno3_takes_the_smooth_side_of_a_step():
+    for lo, hi in ((0.0, 1.0), (2.0, -3.0)):
+        v = S.weno3(lo, lo, hi)        # step to the right of the cell: the left stencil
+        assert abs(v - lo) < 1e-6 * abs(hi - lo)
+        v = S.weno3(lo, hi, hi)        # step to the left: the right stencil
+        assert abs(v - hi) < 1e-6 * abs(hi - lo)
+
+
+def test_weno3_solver_keeps_p_and_u_uniform_across_an_interface_and_conserves():
+    """The WENO3 option in the solver: the interface invariant and periodic
+    conservation hold as for WENO5, and the result differs from WENO5."""
+    n = 16
+    g = S.make_grid(n, gamma=GAM, pc_nd=PC, bc=1, weno_order=3)
+    g5 = S.make_grid(n, gamma=GAM, pc_nd=PC, bc=1)
+    x = (np.arange(n) + 0.5) / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    d = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+    a2 = np.clip(0.5 * (1 - np.tanh((d - 0.3) * n)), 1e-6, 1 - 1e-6)
+    Wp = np.zeros((7, n, n, n))
+    Wp[0] = (1 - a2) * 1.0
+    Wp[1] = a2 * 0.005
+    Wp[2], Wp[3], Wp[4] = 0.5, -0.25, 0.125
+    Wp[5] = 1.0
+    Wp[6] = a2
+    Q = S.prim_to_cons(g, Wp.reshape(7, -1)).reshape(7, n, n, n)
+    dt = 0.3 * g.h / S.max_speed(g, Q)
+    Q3, Q5 = Q, Q
+    for _ in range(6):
+        Q3 = S.rk3_step(g, Q3, dt)
+        Q5 = S.rk3_step(g5, Q5, dt)
+    Wn = S.cons_to_prim(g, Q3.reshape(7, -1))
+    assert np.max(np.abs(Wn[5] - 1.0)) < 1e-12
+    assert np.max(np.abs(Wn[2] - 0.5)) < 1e-12
+    scale = np.array([1.0, 0.005, 1.0, 1.0, 1.0, 40.0])
+    assert np.all(np.abs(S.totals(g, Q3) - S.totals(g, Q)) <= 1e-13 * scale)
+    assert np.max(np.abs(Q3[6] - Q5[6])) > 1e-4
+
+
 # ---------------------------------------------------------------- HLLC
 
 def _flux_text(w, d, gamma, pc):

@@ -55,6 +55,7 @@ class SolverParams:
     bc: int = 0                    # 0 transmissive, 1 periodic, 2 characteristic far field at p_liq
     bc_penalty: float = 1.0        # kappa of the characteristic boundary (0 = transmissive)
     weno_eps: float = 1e-6
+    weno_order: int = 5            # 5: WENO5, 3: WENO3 (Jiang & Shu)
     max_steps: int = 100000
     domain_L: float = DOMAIN_L
     sensors: Tuple[Tuple[float, float, float, float], ...] = ()   # (x, y, z, r) in m
