@@ -109,6 +109,7 @@ typedef struct {
     double bc_penalty;  /* OFM_BC_CHARACTERISTIC: weight in [0, 1] of the far field in the incoming
                            characteristic (0 = transmissive, 1 = no reflection of a plane wave
                            leaving along the normal and full penalty); ignored otherwise */
+    int weno_order;     /* reconstruction (Jiang & Shu, Sec. 2.2): 5 (or 0) = WENO5, 3 = WENO3 */
 } ofm_solver_config;
 
 /* Per-sample quantities of interest (Section 3.2). */

@@ -24,6 +24,7 @@ def solver_config(sp, precision: str = "fp64") -> nv.ofm_solver_config:
     c.p_cloud = getattr(sp, "p_cloud", 0.0)
     c.ramp_radius = getattr(sp, "ramp_radius", 0.0)
     c.bc_penalty = getattr(sp, "bc_penalty", 1.0)
+    c.weno_order = getattr(sp, "weno_order", 5)
     c.cfl = sp.cfl
     c.t_end = sp.t_end
     c.weno_eps = sp.weno_eps

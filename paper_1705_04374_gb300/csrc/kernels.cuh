@@ -105,6 +105,30 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e, T eps) {
     }
 }
 
+// WENO3 (Jiang & Shu, the third-order option): value at the right face of
+// the cell holding b from the averages a, b, c; candidates (3b - a)/2 and
+// (b + c)/2, smoothness (b - a)^2 and (c - b)^2, ideal weights (1/3, 2/3).
+// Double precision in the FP64 reference's order; single precision with the
+// weights multiplied by 3 (eps + beta_0)^2 (eps + beta_1)^2 and one division.
+template <typename T>
+__device__ __forceinline__ T weno3(T a, T b, T c, T eps) {
+    const T q0 = T(0.5) * (T(3) * b - a);
+    const T q1 = T(0.5) * (b + c);
+    const T b0 = (b - a) * (b - a);
+    const T b1 = (c - b) * (c - b);
+    if constexpr (std::is_same<T, double>::value) {
+        const T w0 = T(1.0 / 3.0) / ((eps + b0) * (eps + b0));
+        const T w1 = T(2.0 / 3.0) / ((eps + b1) * (eps + b1));
+        return (w0 * q0 + w1 * q1) / (w0 + w1);
+    } else {
+        T e0 = eps + b0, e1 = eps + b1;
+        e0 *= e0;
+        e1 *= e1;
+        const T w0 = e1, w1 = T(2) * e0;
+        return (w0 * q0 + w1 * q1) / (w0 + w1);
+    }
+}
+
 // Face-state admissibility: alpha2 in [0,1], partial densities > 0 and
 // p + Pi/(Gamma+1) > 0 (positive squared sound speed).  An inadmissible
 // reconstructed state falls back to its cell's value (first order).
@@ -577,13 +601,19 @@ __device__ __forceinline__ void hllc_frame(const float* wl, const float* wr, flo
 // i6); vo[v] is the staged offset of face-frame variable v (slot 2 the normal
 // velocity, 3 and 4 the tangential ones), so the states are reconstructed
 // directly in the face frame.  Returns F in the face frame (see hllc_frame).
+template <int ORD>
 __device__ __forceinline__ void face_fp32(const Eos<float>& e, const float* __restrict__ sW, const int* i6,
                                           const int (&vo)[7], float* F) {
     float wl[7], wr[7];
 #pragma unroll
     for (int v = 0; v < 7; ++v) {
         const float* P = sW + vo[v];
-        weno5_pair(P[i6[0]], P[i6[1]], P[i6[2]], P[i6[3]], P[i6[4]], P[i6[5]], 4.0f * e.eps, wl[v], wr[v]);
+        if constexpr (ORD == 3) {
+            wl[v] = weno3(P[i6[1]], P[i6[2]], P[i6[3]], e.eps);
+            wr[v] = weno3(P[i6[4]], P[i6[3]], P[i6[2]], e.eps);
+        } else {
+            weno5_pair(P[i6[0]], P[i6[1]], P[i6[2]], P[i6[3]], P[i6[4]], P[i6[5]], 4.0f * e.eps, wl[v], wr[v]);
+        }
     }
     float GL, PiL, GR, PiR;
     if (!admissible_f(e, wl, GL, PiL)) {
@@ -686,16 +716,22 @@ __device__ __forceinline__ void face_run_fp32(const Eos<float>& e, const float* 
 }
 
 // One face in double precision, in the FP64 reference's operation order.
-template <int DIR>
+template <int DIR, int ORD>
 __device__ __forceinline__ void face_fp64(const Eos<double>& e, const double* __restrict__ sW, const int* i6,
                                           double* F) {
     double wl[7], wr[7];
 #pragma unroll
     for (int v = 0; v < 7; ++v) {
         const double* P = sW + v * NCROSS;
-        const double m2 = P[i6[0]], m1 = P[i6[1]], c0 = P[i6[2]], p1 = P[i6[3]], p2 = P[i6[4]], p3 = P[i6[5]];
-        wl[v] = weno5(m2, m1, c0, p1, p2, e.eps);
-        wr[v] = weno5(p3, p2, p1, c0, m1, e.eps);
+        const double m1 = P[i6[1]], c0 = P[i6[2]], p1 = P[i6[3]], p2 = P[i6[4]];
+        if constexpr (ORD == 3) {
+            wl[v] = weno3(m1, c0, p1, e.eps);
+            wr[v] = weno3(p2, p1, c0, e.eps);
+        } else {
+            const double m2 = P[i6[0]], p3 = P[i6[5]];
+            wl[v] = weno5(m2, m1, c0, p1, p2, e.eps);
+            wr[v] = weno5(p3, p2, p1, c0, m1, e.eps);
+        }
     }
     if (!admissible(e, wl)) {
 #pragma unroll
@@ -882,25 +918,25 @@ __device__ __forceinline__ void tile_convert(const Eos<T>& e, T* sW) {
 
 // One face of direction dir from the stencil i6, its 8 values (7 fluxes
 // and the face velocity) written to dst[v * stride] in the staged variable
-// order.
-template <typename T>
+// order; ORD = 5 (WENO5) or 3 (WENO3) reconstruction.
+template <typename T, int ORD>
 __device__ __forceinline__ void face_store(const Eos<T>& e, const T* __restrict__ sW, const int* i6, int dir,
                                            T* __restrict__ dst, int stride) {
     T F[8];
     if constexpr (std::is_same<T, double>::value) {
         if (dir == 0)
-            face_fp64<0>(e, sW, i6, F);
+            face_fp64<0, ORD>(e, sW, i6, F);
         else if (dir == 1)
-            face_fp64<1>(e, sW, i6, F);
+            face_fp64<1, ORD>(e, sW, i6, F);
         else
-            face_fp64<2>(e, sW, i6, F);
+            face_fp64<2, ORD>(e, sW, i6, F);
 #pragma unroll
         for (int v = 0; v < 8; ++v) dst[v * stride] = F[v];
     } else {
         const int r1 = dir == 0 ? 3 : (dir == 1 ? 4 : 2);   // staged row of the first tangential velocity
         const int r2 = dir == 0 ? 4 : (dir == 1 ? 2 : 3);   // and of the second
         const int vo[7] = {0, NCROSS, (2 + dir) * NCROSS, r1 * NCROSS, r2 * NCROSS, 5 * NCROSS, 6 * NCROSS};
-        face_fp32(e, sW, i6, vo, F);
+        face_fp32<ORD>(e, sW, i6, vo, F);
         dst[0] = F[0];
         dst[stride] = F[1];
         dst[(2 + dir) * stride] = F[2];
@@ -921,7 +957,7 @@ struct TileRhs {
     T divu[CELLS_PER_THREAD];
 };
 
-template <typename T>
+template <typename T, int ORD>
 __device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>& c, const T* __restrict__ sW,
                                            T* __restrict__ sF, const int* __restrict__ sRow, TileRhs<T>& R) {
     const T invh = T(1) / (T)c.bw.G->h;  // 1/h, formed as the FP64 reference forms it
@@ -948,12 +984,12 @@ __device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>&
             i6[k] = dir == 0 ? sRow[(b + HALO) * BX + a + HALO] + TS - 3 + k
                              : (dir == 1 ? sRow[(b + HALO) * BX + TS - 3 + k + HALO] + a
                                          : sRow[(TS - 3 + k + HALO) * BX + b + HALO] + a);
-        face_store(e, sW, i6, dir, sFb + dir * 8 * TS * TS + line, TS * TS);
+        face_store<T, ORD>(e, sW, i6, dir, sFb + dir * 8 * TS * TS + line, TS * TS);
     }
 #pragma unroll 1
     for (int dir = 0; dir < 3; ++dir) {
         bool by_runs = false;
-        if constexpr (std::is_same<T, float>::value && NEAR_RUN > 1) {
+        if constexpr (std::is_same<T, float>::value && NEAR_RUN > 1 && ORD == 5) {
             // runs of NEAR_RUN consecutive near faces along each line, one per thread
             constexpr int NR = TS / NEAR_RUN;   // runs per line
             for (int t = threadIdx.x; t < TS * TS * NR; t += NT) {
@@ -989,7 +1025,7 @@ __device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>&
                 i6[k] = dir == 0 ? sRow[(z + HALO) * BX + y + HALO] + x - 3 + k
                                  : (dir == 1 ? sRow[(z + HALO) * BX + y - 3 + k + HALO] + x
                                              : sRow[(z - 3 + k + HALO) * BX + y + HALO] + x);
-            face_store(e, sW, i6, dir, sF + c, NCELL);
+            face_store<T, ORD>(e, sW, i6, dir, sF + c, NCELL);
         }
         __syncthreads();
 #pragma unroll
@@ -1085,19 +1121,19 @@ __device__ __forceinline__ void tile_update(const Params<T>& P, const TileCtx<T>
 
 
 // One tile: faces, source, update.
-template <typename T, int STAGE>
+template <typename T, int STAGE, int ORD>
 __device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& c, long long tile_index,
                                           const T* __restrict__ sW, T* __restrict__ sF,
                                           const int* __restrict__ sRow) {
     TileRhs<T> R;
-    tile_faces<T>(P, c, sW, sF, sRow, R);
+    tile_faces<T, ORD>(P, c, sW, sF, sRow, R);
     T pc[CELLS_PER_THREAD], ac[CELLS_PER_THREAD];
     tile_cell_pa(sW, pc, ac);
     tile_update<T, STAGE>(P, c, tile_index, R, pc, ac);
 }
 
-// One RK stage, one block per tile.
-template <typename T, int STAGE>
+// One RK stage, one block per tile (ORD: WENO order, 5 or 3).
+template <typename T, int STAGE, int ORD>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
     stage_kernel(const __grid_constant__ Params<T> P, int parity) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1117,7 +1153,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
         tile_char_bc(P, c.bw, sW);
     }
     __syncthreads();
-    tile_body<T, STAGE>(P, c, (long long)blockIdx.x, sW, sF, sRow);
+    tile_body<T, STAGE, ORD>(P, c, (long long)blockIdx.x, sW, sF, sRow);
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -1144,7 +1180,7 @@ __device__ __forceinline__ long long next_active(const Params<T>& P, long long t
 // issues the next tile's halo copies and then performs the current tile's
 // update, so the update's global loads and the next tile's copies are in
 // flight together.  Same arithmetic as stage_kernel.
-template <typename T, int STAGE>
+template <typename T, int STAGE, int ORD>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
     stage_kernel_persistent(const __grid_constant__ Params<T> P, int parity) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1169,7 +1205,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
         }
         __syncthreads();
         TileRhs<T> R;
-        tile_faces<T>(P, c, sW, sF, sRow, R);
+        tile_faces<T, ORD>(P, c, sW, sF, sRow, R);
         T pc[CELLS_PER_THREAD], ac[CELLS_PER_THREAD];
         tile_cell_pa(sW, pc, ac);
         __syncthreads();   // every read of sW is done
@@ -1382,16 +1418,25 @@ __global__ void __launch_bounds__(256) totals_kernel(const __grid_constant__ Par
 
 }  // namespace
 
+template <typename T, int ORD>
+int set_smem_attrs_order() {
+    const int bytes = (int)smem_bytes(sizeof(T));
+    CUDA_TRY(cudaFuncSetAttribute(stage_kernel<T, 0, ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    CUDA_TRY(cudaFuncSetAttribute(stage_kernel<T, 1, ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    CUDA_TRY(cudaFuncSetAttribute(stage_kernel<T, 2, ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_persistent<T, 0, ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  bytes));
+    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_persistent<T, 1, ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  bytes));
+    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_persistent<T, 2, ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  bytes));
+    return OFM_OK;
+}
+
 template <typename T>
 int set_smem_attrs() {
-    const int bytes = (int)smem_bytes(sizeof(T));
-    CUDA_TRY(cudaFuncSetAttribute(stage_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    CUDA_TRY(cudaFuncSetAttribute(stage_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    CUDA_TRY(cudaFuncSetAttribute(stage_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_persistent<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_persistent<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    CUDA_TRY(cudaFuncSetAttribute(stage_kernel_persistent<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    return OFM_OK;
+    const int rc = set_smem_attrs_order<T, 5>();
+    return rc != OFM_OK ? rc : set_smem_attrs_order<T, 3>();
 }
 
 // Grid of the persistent variant: resident blocks per SM (three in single,
@@ -1405,13 +1450,21 @@ unsigned persistent_grid(const Params<T>& P) {
     return (unsigned)(P.total_blocks < want ? P.total_blocks : want);
 }
 
+template <typename T, int STAGE, int ORD>
+void launch_one_stage_order(const Params<T>& P, int variant, int parity, cudaStream_t st) {
+    if (variant == OFM_VARIANT_PERSISTENT)
+        stage_kernel_persistent<T, STAGE, ORD><<<persistent_grid(P), NT, smem_bytes(sizeof(T)), st>>>(P, parity);
+    else
+        stage_kernel<T, STAGE, ORD><<<(unsigned)P.total_blocks, NT, smem_bytes(sizeof(T)), st>>>(P, parity);
+}
+
 template <typename T, int STAGE>
 void launch_one_stage(const Params<T>& P, int variant, int parity, cudaStream_t st) {
     if (P.total_blocks <= 0) return;  // every group finished
-    if (variant == OFM_VARIANT_PERSISTENT)
-        stage_kernel_persistent<T, STAGE><<<persistent_grid(P), NT, smem_bytes(sizeof(T)), st>>>(P, parity);
+    if (P.weno_order == 3)
+        launch_one_stage_order<T, STAGE, 3>(P, variant, parity, st);
     else
-        stage_kernel<T, STAGE><<<(unsigned)P.total_blocks, NT, smem_bytes(sizeof(T)), st>>>(P, parity);
+        launch_one_stage_order<T, STAGE, 5>(P, variant, parity, st);
 }
 
 template <typename T>

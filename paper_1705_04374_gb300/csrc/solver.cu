@@ -190,6 +190,7 @@ void fill_params(ofm_batch* b, Params<T>& P) {
     }
     P.bc = c.bc;
     P.bc_penalty = c.bc_penalty;
+    P.weno_order = c.weno_order == 3 ? 3 : 5;
     P.nb = b->nb;
     P.n_sens = c.n_sensors;
     P.n_out = c.n_out_times;
@@ -288,6 +289,8 @@ extern "C" int ofm_solver_create(ofm_solver** out, const ofm_solver_config* c) {
         return fail(OFM_EINVAL, "ofm_solver_create: unknown boundary condition");
     if (c->bc == OFM_BC_CHARACTERISTIC && !(c->bc_penalty >= 0.0 && c->bc_penalty <= 1.0))
         return fail(OFM_EINVAL, "ofm_solver_create: bc_penalty must lie in [0, 1]");
+    if (c->weno_order != 0 && c->weno_order != 3 && c->weno_order != 5)
+        return fail(OFM_EINVAL, "ofm_solver_create: weno_order must be 3 or 5");
     if (c->n_sensors < 0 || c->n_sensors > OFM_MAX_SENSORS || c->n_out_times < 0 || c->max_steps < 1)
         return fail(OFM_EINVAL, "ofm_solver_create: bad sensor / output / step settings");
     ofm_solver* s = new (std::nothrow) ofm_solver;

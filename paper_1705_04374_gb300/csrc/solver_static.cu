@@ -149,6 +149,7 @@ void static_params(const ofm_solver* s, int N, int M, int nb, unsigned char* ws,
     }
     P.bc = c.bc;
     P.bc_penalty = c.bc_penalty;
+    P.weno_order = c.weno_order == 3 ? 3 : 5;
     P.nb = nb;
     P.n_sens = c.n_sensors;
     P.n_out = c.n_out_times;

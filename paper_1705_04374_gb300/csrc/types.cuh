@@ -98,6 +98,7 @@ struct Params {
     double t_end, cfl, p_gas, p_liq, rho1, rho2;
     double p_cloud, ramp_r0;   // cloud pressure ramp of the initial condition (ramp_r0 = 0: off)
     double bc_penalty;         // characteristic boundary: far-field weight (far field at p_liq)
+    int weno_order;            // 5 (WENO5) or 3 (WENO3)
 };
 
 // Low-storage TVD RK3 (Gottlieb & Shu 1998), Williamson 2N form.

@@ -40,7 +40,7 @@ class ofm_solver_config(C.Structure):
                 ("precision", C.c_int), ("bc", C.c_int), ("max_steps", C.c_int),
                 ("n_sensors", C.c_int), ("sensors", (C.c_double * 4) * OFM_MAX_SENSORS),
                 ("n_out_times", C.c_int), ("p_cloud", C.c_double), ("ramp_radius", C.c_double),
-                ("bc_penalty", C.c_double)]
+                ("bc_penalty", C.c_double), ("weno_order", C.c_int)]
 
 
 class ofm_qoi(C.Structure):

@@ -151,6 +151,44 @@ def test_one_step_characteristic_boundary(precision, tol, kappa, variant):
     b.close()
 
 
+@pytest.mark.parametrize("precision,tol,variant,N", [("fp64", TOL_STEP_FP64, 0, 16), ("fp64", TOL_STEP_FP64, 1, 24),
+                                                      ("fp32", TOL_STEP_FP32, 0, 24), ("fp32", TOL_STEP_FP32, 1, 16)])
+def test_one_step_weno3(precision, tol, variant, N):
+    """The WENO3 option: one step of both stage-kernel variants against the oracle."""
+    w = W.with_solver(W.tiny(N, 4), weno_order=3)
+    sp = w.solver
+    ids = [0, 5]
+    s, groups, b = gpu_batch(sp, precision, [(N, ids)], w.cloud)
+    b.set_variant(variant)
+    b.init()
+    b.run(1)
+    for i, sid in enumerate(ids):
+        bub = ocloud.sample_cloud(w.cloud, W.BASE_SEED, sid)
+        ref = oracle_one_step(sp, N, bub)
+        got = b.state(0, i)
+        assert np.all(rel_l1(got, ref) <= tol), (sid, rel_l1(got, ref))
+        ref5 = oracle_one_step(W.with_solver(w, weno_order=5).solver, N, bub)
+        assert np.max(rel_l1(got, ref5)) > 100 * tol   # the third-order path did run
+    b.close()
+
+
+def test_weno3_qois_at_t_end_fp64():
+    w = W.with_solver(W.tiny(16, 4), weno_order=3)
+    sp = w.solver
+    ids = [0, 1]
+    s, groups, b = gpu_batch(sp, "fp64", [(16, ids)], w.cloud)
+    b.init()
+    while b.run(64) > 0:
+        pass
+    b.qoi()
+    got = groups[0].qoi_dicts(len(sp.sensors))
+    ref = oracle_qois(sp, 16, w.cloud, ids)
+    for i in range(2):
+        compare_qoi(got[i], groups[0].hist[i], ref[i][0], ref[i][1], TOL_QOI_FP64, len(sp.sensors),
+                    ag=groups[0].alpha_hist[i])
+    b.close()
+
+
 def test_characteristic_boundary_qois_at_t_end_fp64():
     from dataclasses import replace
     w = W.tiny(16, 4)

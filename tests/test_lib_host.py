@@ -131,6 +131,8 @@ def test_invalid_arguments_are_rejected_on_the_host():
     for bc, kappa in ((3, 1.0), (nv.OFM_BC_CHARACTERISTIC, 1.5), (nv.OFM_BC_CHARACTERISTIC, -0.1)):
         cfg = api.solver_config(W.SolverParams(bc=bc, bc_penalty=kappa), "fp64")
         assert L.ofm_solver_create(C.byref(h), C.byref(cfg)) == nv.OFM_EINVAL, (bc, kappa)
+    cfg = api.solver_config(W.SolverParams(weno_order=4), "fp64")
+    assert L.ofm_solver_create(C.byref(h), C.byref(cfg)) == nv.OFM_EINVAL
     cfg = api.solver_config(W.SolverParams(bc=nv.OFM_BC_CHARACTERISTIC, bc_penalty=0.25), "fp64")
     assert L.ofm_solver_create(C.byref(h), C.byref(cfg)) == nv.OFM_OK
     L.ofm_solver_destroy(h)
