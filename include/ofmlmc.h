@@ -344,6 +344,12 @@ typedef struct {
 int ofm_level_moments_of(const double* pairs, int64_t M, ofm_level_moments* out);
 int ofm_merge_moments(const ofm_level_moments* a, const ofm_level_moments* b, ofm_level_moments* out);
 int ofm_estimate_moments(int L, const ofm_level_moments* moments, const double* W, ofm_estimate_out* out);
+/* ofm_estimate_fitted from L+1 summaries (level 0 n >= 2, levels l >= 1
+ * n >= 1; V[q_l - q_{l-1}] = (m2_f + m2_c - 2 c_fc)/(n - 1)); equal to
+ * ofm_estimate_fitted on the union of the pairs up to round-off.  V_fit as
+ * there (may be NULL). */
+int ofm_estimate_moments_fitted(int L, const ofm_level_moments* moments, const double* W, ofm_estimate_out* out,
+                                double* V_fit);
 
 /* Eq. (M-tol) (mode OFM_MODE_TOL, target = tau, constraint eps_OF <= tau) or
  * Eq. (M-budget) (OFM_MODE_BUDGET, target = budget) with the step-7 rule that

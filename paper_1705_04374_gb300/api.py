@@ -292,16 +292,23 @@ def merge_moments(a, b) -> tuple:
     return (out.n, out.mean_f, out.mean_c, out.m2_f, out.m2_c, out.c_fc)
 
 
-def estimate_moments(moments, W) -> dict:
-    """ofm_estimate_moments on per-level summaries."""
+def estimate_moments(moments, W, fit: bool = False) -> dict:
+    """ofm_estimate_moments (or, with fit, ofm_estimate_moments_fitted) on per-level summaries."""
     L = len(moments) - 1
     arr = (nv.ofm_level_moments * (L + 1))(*[_moments_c(m) for m in moments])
     Wc = (C.c_double * (L + 1))(*W)
     out = nv.ofm_estimate_out()
-    nv.check(nv.lib().ofm_estimate_moments(L, arr, Wc, C.byref(out)), "ofm_estimate_moments")
     n = L + 1
-    return dict(alpha=np.array(out.alpha[:n]), sigma2=np.array(out.sigma2[:n]), cov=np.array(out.cov[:n]),
-                sigma_tilde2=np.array(out.sigma_tilde2[:n]), mean=out.mean, eps2=out.eps2)
+    res = {}
+    if fit:
+        vf = (C.c_double * n)()
+        nv.check(nv.lib().ofm_estimate_moments_fitted(L, arr, Wc, C.byref(out), vf), "ofm_estimate_moments_fitted")
+        res["V_fit"] = np.array(vf[:n])
+    else:
+        nv.check(nv.lib().ofm_estimate_moments(L, arr, Wc, C.byref(out)), "ofm_estimate_moments")
+    res.update(alpha=np.array(out.alpha[:n]), sigma2=np.array(out.sigma2[:n]), cov=np.array(out.cov[:n]),
+               sigma_tilde2=np.array(out.sigma_tilde2[:n]), mean=out.mean, eps2=out.eps2)
+    return res
 
 
 def optimal_samples(sigma_tilde2, W, target: float, mode: str = "tol", M_done=None) -> np.ndarray:

@@ -315,11 +315,18 @@ extern "C" int ofm_merge_moments(const ofm_level_moments* a, const ofm_level_mom
     return OFM_OK;
 }
 
-extern "C" int ofm_estimate_moments(int L, const ofm_level_moments* m, const double* W, ofm_estimate_out* out) {
-    if (L < 0 || L >= OFM_MAX_LEVELS || !m || !W || !out) return fail(OFM_EINVAL, "ofm_estimate_moments: bad arguments");
+namespace {
+
+// ofm_estimate_moments, with or without step 3's fit (as estimate_core).
+int estimate_moments_core(int L, const ofm_level_moments* m, const double* W, ofm_estimate_out* out, bool fit,
+                          double* V_fit_out) {
+    const char* who = fit ? "ofm_estimate_moments_fitted" : "ofm_estimate_moments";
+    if (L < 0 || L >= OFM_MAX_LEVELS || !m || !W || !out) return fail(OFM_EINVAL, "%s: bad arguments", who);
+    if (fit && L < 1) return fail(OFM_EINVAL, "%s: the fit needs L >= 1", who);
     for (int l = 0; l <= L; ++l) {
-        if (m[l].n < 2) return fail(OFM_EINVAL, "ofm_estimate_moments: level %d needs >= 2 samples", l);
-        if (!(W[l] > 0.0)) return fail(OFM_EINVAL, "ofm_estimate_moments: W[%d] must be > 0", l);
+        const int64_t need = (fit && l > 0) ? 1 : 2;
+        if (m[l].n < need) return fail(OFM_EINVAL, "%s: level %d needs >= %lld samples", who, l, (long long)need);
+        if (!(W[l] > 0.0)) return fail(OFM_EINVAL, "%s: W[%d] must be > 0", who, l);
     }
     std::memset(out, 0, sizeof(*out));
     for (int l = 0; l <= L; ++l) {
@@ -329,8 +336,28 @@ extern "C" int ofm_estimate_moments(int L, const ofm_level_moments* m, const dou
             const ofm_level_moments up{m[l + 1].n, m[l + 1].mean_c, 0.0, m[l + 1].m2_c, 0.0, 0.0};
             ofm_merge_moments(&pooled, &up, &pooled);
         }
-        out->sigma2[l] = pooled.m2_f / (double)(pooled.n - 1);
-        out->cov[l] = l > 0 ? m[l].c_fc / (double)(m[l].n - 1) : 0.0;
+        out->sigma2[l] = pooled.n >= 2 ? pooled.m2_f / (double)(pooled.n - 1) : out->sigma2[l - 1];
+        out->cov[l] = (l > 0 && !fit) ? m[l].c_fc / (double)(m[l].n - 1) : 0.0;
+    }
+    if (fit) {
+        int64_t M[OFM_MAX_LEVELS];
+        double V[OFM_MAX_LEVELS];
+        for (int l = 0; l <= L; ++l) {
+            M[l] = m[l].n;
+            // V[q_l - q_{l-1}] from the co-moments of pair l
+            V[l] = (l > 0 && m[l].n >= 2) ? (m[l].m2_f + m[l].m2_c - 2.0 * m[l].c_fc) / (double)(m[l].n - 1) : 0.0;
+        }
+        double a = 0.0, b = 0.0;
+        int rc = fit_line(L, M, V, &a, &b);
+        if (rc != OFM_OK) return rc;
+        for (int l = 1; l <= L; ++l) {
+            const double sl = std::sqrt(out->sigma2[l]), sm = std::sqrt(out->sigma2[l - 1]);
+            const double lo = (sl - sm) * (sl - sm), hi = (sl + sm) * (sl + sm);
+            const double vf = std::min(std::max(std::exp(a + b * (double)l), lo), hi);
+            out->cov[l] = 0.5 * (out->sigma2[l] + out->sigma2[l - 1] - vf);
+            if (V_fit_out) V_fit_out[l] = vf;
+        }
+        if (V_fit_out) V_fit_out[0] = 0.0;
     }
     int rc = solve_alpha(L, out->sigma2, out->cov, W, out->alpha);
     if (rc != OFM_OK) return rc;
@@ -342,7 +369,10 @@ extern "C" int ofm_estimate_moments(int L, const ofm_level_moments* m, const dou
             mean += a * m[0].mean_f;
         } else {
             const double b = out->alpha[l - 1];
-            out->sigma_tilde2[l] = (a * a * m[l].m2_f + b * b * m[l].m2_c - 2.0 * a * b * m[l].c_fc) / n1;
+            if (m[l].n >= 2)
+                out->sigma_tilde2[l] = (a * a * m[l].m2_f + b * b * m[l].m2_c - 2.0 * a * b * m[l].c_fc) / n1;
+            else  // from the fitted second moments
+                out->sigma_tilde2[l] = a * a * out->sigma2[l] + b * b * out->sigma2[l - 1] - 2.0 * a * b * out->cov[l];
             mean += a * m[l].mean_f - b * m[l].mean_c;
         }
         eps2 += out->sigma_tilde2[l] / (double)m[l].n;
@@ -350,6 +380,17 @@ extern "C" int ofm_estimate_moments(int L, const ofm_level_moments* m, const dou
     out->mean = mean;
     out->eps2 = eps2;
     return OFM_OK;
+}
+
+}  // namespace
+
+extern "C" int ofm_estimate_moments(int L, const ofm_level_moments* m, const double* W, ofm_estimate_out* out) {
+    return estimate_moments_core(L, m, W, out, false, nullptr);
+}
+
+extern "C" int ofm_estimate_moments_fitted(int L, const ofm_level_moments* m, const double* W, ofm_estimate_out* out,
+                                           double* V_fit) {
+    return estimate_moments_core(L, m, W, out, true, V_fit);
 }
 
 extern "C" int ofm_warmup_samples(int L, const double* W, int64_t* M_out) {

@@ -141,6 +141,8 @@ SIGNATURES = {
     "ofm_level_moments_of": (C.c_int, [_P(C.c_double), C.c_int64, _P(ofm_level_moments)]),
     "ofm_merge_moments": (C.c_int, [_P(ofm_level_moments), _P(ofm_level_moments), _P(ofm_level_moments)]),
     "ofm_estimate_moments": (C.c_int, [C.c_int, _P(ofm_level_moments), _P(C.c_double), _P(ofm_estimate_out)]),
+    "ofm_estimate_moments_fitted": (C.c_int, [C.c_int, _P(ofm_level_moments), _P(C.c_double),
+                                              _P(ofm_estimate_out), _P(C.c_double)]),
     "ofm_probe_fma_tflops": (C.c_int, [C.c_int, _P(C.c_double), _vp]),
     "ofm_optimal_samples": (C.c_int, [C.c_int, _P(C.c_double), _P(C.c_double), _P(C.c_int64),
                                       C.c_double, C.c_int, _P(C.c_int64)]),

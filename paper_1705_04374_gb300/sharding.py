@@ -51,15 +51,16 @@ def pair_shard(M: int, rank: int, world: int) -> range:
     return range(rank, M, world)
 
 
-def distributed_estimate(local_pairs, W, world: int, device="cpu") -> dict:
+def distributed_estimate(local_pairs, W, world: int, device="cpu", fit: bool = False) -> dict:
     """The OF-MLMC estimate of all ranks' pairs: each rank summarises its own
     pairs per level (ofm_level_moments_of), the summaries are all-gathered
     (6 doubles per level and rank), combined in rank order (ofm_merge_moments)
-    and evaluated (ofm_estimate_moments); every rank returns the same result."""
+    and evaluated (ofm_estimate_moments, or with fit the fitted estimator);
+    every rank returns the same result."""
     from . import api
     local = [api.level_moments(p) for p in local_pairs]
     if world <= 1:
-        return api.estimate_moments(local, W)
+        return api.estimate_moments(local, W, fit=fit)
     import torch
     import torch.distributed as dist
     t = torch.tensor([[float(x) for x in m] for m in local], dtype=torch.float64, device=device)
@@ -69,4 +70,4 @@ def distributed_estimate(local_pairs, W, world: int, device="cpu") -> dict:
     for part in parts:
         rows = [(int(r[0]), *[float(x) for x in r[1:]]) for r in part.cpu().tolist()]
         merged = rows if merged is None else [api.merge_moments(a, b) for a, b in zip(merged, rows)]
-    return api.estimate_moments(merged, W)
+    return api.estimate_moments(merged, W, fit=fit)

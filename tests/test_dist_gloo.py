@@ -83,6 +83,9 @@ def _estimator_rank(rank, port, out_dir):
         est = sharding.distributed_estimate(local, [1.0, 17.0, 272.0], WORLD)
         np.save(os.path.join(out_dir, f"est{rank}.npy"),
                 np.concatenate([est["alpha"], est["sigma2"], est["cov"], est["sigma_tilde2"], [est["mean"], est["eps2"]]]))
+        fit = sharding.distributed_estimate(local, [1.0, 17.0, 272.0], WORLD, fit=True)
+        np.save(os.path.join(out_dir, f"fit{rank}.npy"),
+                np.concatenate([fit["alpha"], fit["cov"], fit["sigma_tilde2"], fit["V_fit"], [fit["mean"], fit["eps2"]]]))
     finally:
         dist.destroy_process_group()
 
@@ -98,5 +101,11 @@ def test_two_gloo_ranks_estimate_equals_single_process(tmp_path):
     e0, e1 = np.load(tmp_path / "est0.npy"), np.load(tmp_path / "est1.npy")
     assert np.array_equal(e0, e1)                      # every rank holds the same numbers
     assert np.allclose(e0, want, rtol=1e-11, atol=1e-14)
+    # step 3's variance fit from the combined summaries
+    rf = api.estimate(pairs, [1.0, 17.0, 272.0], fit=True)
+    want = np.concatenate([rf["alpha"], rf["cov"], rf["sigma_tilde2"], rf["V_fit"], [rf["mean"], rf["eps2"]]])
+    f0, f1 = np.load(tmp_path / "fit0.npy"), np.load(tmp_path / "fit1.npy")
+    assert np.array_equal(f0, f1)
+    assert np.allclose(f0, want, rtol=1e-11, atol=1e-14)
     shards = [set(sharding.pair_shard(41, r, WORLD)) for r in range(WORLD)]
     assert not (shards[0] & shards[1]) and shards[0] | shards[1] == set(range(41))

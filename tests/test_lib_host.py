@@ -96,6 +96,26 @@ def test_fitted_estimator_matches_oracle():
         assert np.all(a["sigma_tilde2"] >= 0.0)
 
 
+def test_fitted_summary_estimator_matches_oracle_on_the_union():
+    """ofm_estimate_moments_fitted on per-part summaries merged pairwise equals
+    the oracle's fitted estimator on all pairs (one finest pair included)."""
+    Wc = [1.0, 17.0, 272.0, 4352.0]
+    for M in ([300, 50, 9, 3], [300, 50, 9, 1]):
+        pairs = W.toy_levels(M, 3, 0.4, 0.7, seed=31)
+        moms = []
+        for p in pairs:
+            cut = p.shape[0] // 2
+            a, b = api.level_moments(p[:cut]), api.level_moments(p[cut:])
+            moms.append(api.merge_moments(a, b))
+        got = api.estimate_moments(moms, Wc, fit=True)
+        ref = E.estimate_fitted(pairs, Wc)
+        for k in ("alpha", "sigma2", "cov", "sigma_tilde2"):
+            assert np.allclose(got[k], ref[k], rtol=1e-10, atol=1e-13), (M, k)
+        assert np.allclose(got["V_fit"][1:], ref["V_fit"][1:], rtol=1e-10, atol=0)
+        assert abs(got["mean"] - ref["mean"]) < 1e-10 * max(1.0, abs(ref["mean"]))
+        assert abs(got["eps2"] - ref["eps2"]) < 1e-10 * ref["eps2"]
+
+
 def test_optimal_samples_rejects_invalid_variances_and_overflow():
     for st2 in ([1.0, -0.1], [1.0, float("nan")]):
         with pytest.raises(nv.OfmError):
