@@ -484,16 +484,82 @@ def cmd_epsval(quick, min_samples=16):
                 empirical_rmse_less_reference=math.sqrt(max(mse - ref["est"]["eps2"], 0.0)))
 
 
+# ------------------------------------------------------------------------------ orders
+
+def cmd_orders(quick):
+    """WENO5 against the paper's third-order option (WENO3) on the ensemble workload (20-bubble
+    clouds on 64^3 to t_end, FP32 stencil): throughput of each, and how far the third-order
+    QoIs sit from the fifth-order ones on the same clouds."""
+    from dataclasses import replace
+    n = 64 if quick else 256
+    w = W.cfg2("fp32")
+    ids = level_ids(0, 0, n)
+    out = dict(experiment="orders", grid=64, samples=n, bubbles=20)
+    res = {}
+    for order in (5, 3):
+        sp = replace(w.solver, weno_order=order)
+        s32 = api.Solver(sp, "fp32")
+        solve_groups(s32, w.cloud, [(64, ids[:8])])             # warm-up (graphs, first launches)
+        (q,), secs, cells = solve_groups(s32, w.cloud, [(64, ids)])
+        res[order] = q
+        out[f"weno{order}"] = dict(gpu_seconds=secs, cell_updates_per_s=cells / secs,
+                                   steps_mean=float(np.mean([d["n_steps"] for d in q])),
+                                   p_peak_mean=float(np.mean([d["p_peak"] for d in q])),
+                                   p_c_mean=float(np.mean([d["sensor_peak"][0] for d in q])))
+    d_peak = [abs(a["p_peak"] - b["p_peak"]) / b["p_peak"] for a, b in zip(res[3], res[5])]
+    d_pc = [abs(a["sensor_peak"][0] - b["sensor_peak"][0]) / b["sensor_peak"][0] for a, b in zip(res[3], res[5])]
+    out["weno3_vs_weno5"] = dict(speedup=out["weno3"]["cell_updates_per_s"] / out["weno5"]["cell_updates_per_s"],
+                                 p_peak_rel_diff_mean=float(np.mean(d_peak)), p_peak_rel_diff_max=float(np.max(d_peak)),
+                                 p_c_rel_diff_mean=float(np.mean(d_pc)), p_c_rel_diff_max=float(np.max(d_pc)))
+    return out
+
+
+# ------------------------------------------------------------------------------ fitwarm
+
+def cmd_fitwarm(quick):
+    """Step 3's variance fit with the finest level started from one pair (the appendix on
+    M_L = 1) against the plain warm-up of two pairs per level: 4 levels 8^3..64^3, 20-bubble
+    clouds, centre-sensor peak pressure, FP32, tolerance mode; R seeded runs each.  Reports
+    the warm-up cost, the total cost, the final error estimate and the estimates."""
+    w = W.tiny(16, 20)
+    cloud = W.cloud_uniform(20)
+    levels = [8, 16, 32, 64]
+    R = 3 if quick else 6
+    tau = 6.0e5
+    s32 = api.Solver(w.solver, "fp32")
+    out = dict(experiment="fitwarm", levels=levels, bubbles=20, tau=tau, repeats=R)
+    for name, fit in (("plain", False), ("fit", True)):
+        runs = []
+        for r in range(R):
+            warm, _, _ = api.run_ofmlmc(s32, cloud, levels, target=tau, qoi=QOI, seed=W.BASE_SEED + 500 + r,
+                                        max_iterations=1, max_cell_steps=4e10, fit_variances=fit)
+            res, _, _ = api.run_ofmlmc(s32, cloud, levels, target=tau, qoi=QOI, seed=W.BASE_SEED + 500 + r,
+                                       max_iterations=6, max_cell_steps=4e10, fit_variances=fit)
+            runs.append(dict(warmup_M=warm["M"], warmup_cell_steps=warm["cell_steps"], M=res["M"],
+                             iterations=res["iterations"], cell_steps=res["cell_steps"],
+                             gpu_seconds=res["gpu_seconds"], eps=math.sqrt(res["est"]["eps2"]),
+                             mean=res["est"]["mean"], capped=res["capped"]))
+        out[name] = dict(runs=runs,
+                         warmup_cell_steps_mean=float(np.mean([x["warmup_cell_steps"] for x in runs])),
+                         cell_steps_mean=float(np.mean([x["cell_steps"] for x in runs])),
+                         gpu_seconds_mean=float(np.mean([x["gpu_seconds"] for x in runs])),
+                         eps_mean=float(np.mean([x["eps"] for x in runs])),
+                         mean_of_estimates=float(np.mean([x["mean"] for x in runs])),
+                         spread_of_estimates=float(np.std([x["mean"] for x in runs], ddof=1)))
+    return out
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["uneven3", "surrogate", "rmse", "cfg5", "epsval", "paper500"])
+    ap.add_argument("what", choices=["uneven3", "surrogate", "rmse", "cfg5", "epsval", "paper500", "orders",
+                                     "fitwarm"])
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--min-samples", type=int, default=16, help="epsval: pairs every level starts with")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     fn = {"uneven3": cmd_uneven3, "surrogate": cmd_surrogate, "rmse": cmd_rmse, "cfg5": cmd_cfg5,
-          "epsval": cmd_epsval, "paper500": cmd_paper500}[a.what]
+          "epsval": cmd_epsval, "paper500": cmd_paper500, "orders": cmd_orders, "fitwarm": cmd_fitwarm}[a.what]
     print(json.dumps(fn(a.quick, a.min_samples) if a.what == "epsval" else fn(a.quick)), flush=True)
 
 
