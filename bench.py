@@ -359,7 +359,8 @@ def run_ours(args):
     if hbm_peak is None:
         hbm_peak = HBM_FALLBACK_GBS
     es = 4 if args.precision == "fp32" else 8
-    bytes_per_cell_stage = (21 + 28 + 28) / 3.0 * es   # Q, dQ in; Q', dQ out (stage 1 skips dQ in)
+    # words per cell: stage 1 Q in, Q' and dQ out; stage 2 Q, dQ in, Q', dQ out; stage 3 Q, dQ in, Q' out
+    bytes_per_cell_stage = (21 + 28 + 21) / 3.0 * es
     traffic_rec = load_json(TRAFFIC_FILE) or {}
     traffic = None
     if traffic_rec.get("kernel_hash") == kernel_hash() and traffic_rec.get("precision") == args.precision:

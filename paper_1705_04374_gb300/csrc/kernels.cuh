@@ -1106,7 +1106,9 @@ __device__ __forceinline__ void tile_update(const Params<T>& P, const TileCtx<T>
                 const T q = Qin[v * n3 + gi];
                 T d = dt * rhs[k][v];
                 if (STAGE > 0) d = A * dQ[v * n3 + gi] + d;
-                dQ[v * n3 + gi] = d;
+                // the last stage's register is dead: the next step's first stage (A = 0)
+                // overwrites it without reading it
+                if (STAGE < 2) dQ[v * n3 + gi] = d;
                 qn[v] = q + B * d;
                 Qout[v * n3 + gi] = qn[v];
             }

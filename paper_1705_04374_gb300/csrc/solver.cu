@@ -10,7 +10,8 @@
 //     memory as primitives, computes every face flux of the tile once (WENO5
 //     both sides + HLLC) per direction into shared memory, differences them
 //     into per-cell right-hand sides in registers, and applies the 2N update.
-//     Per cell and stage, HBM sees only Q, dQ in and Q', dQ out.
+//     Per cell and stage, HBM sees only Q, dQ in and Q', dQ out (the first stage reads no dQ,
+//     the last writes none).
 //   * The last stage's epilogue evaluates the new state's pressure and sound
 //     speed and reduces, per tile, the max signal speed (for the next CFL
 //     step), the max pressure with its first index, and health bits.  A
