@@ -514,6 +514,26 @@ def cmd_orders(quick):
     return out
 
 
+# ------------------------------------------------------------------------------ boundaries
+
+def cmd_boundaries(quick):
+    """Cost of the characteristic far-field boundary: the ensemble workload (20-bubble clouds
+    on 64^3 to t_end, FP32) with transmissive and with characteristic boundaries."""
+    from dataclasses import replace
+    n = 64 if quick else 256
+    w = W.cfg2("fp32")
+    ids = level_ids(0, 0, n)
+    out = dict(experiment="boundaries", grid=64, samples=n, bubbles=20)
+    for name, bc in (("transmissive", nv.OFM_BC_TRANSMISSIVE), ("characteristic", nv.OFM_BC_CHARACTERISTIC)):
+        s32 = api.Solver(replace(w.solver, bc=bc), "fp32")
+        solve_groups(s32, w.cloud, [(64, ids[:8])])             # warm-up (graphs, first launches)
+        (q,), secs, cells = solve_groups(s32, w.cloud, [(64, ids)])
+        out[name] = dict(gpu_seconds=secs, cell_updates_per_s=cells / secs,
+                         p_peak_mean=float(np.mean([d["p_peak"] for d in q])))
+    out["ratio"] = out["characteristic"]["cell_updates_per_s"] / out["transmissive"]["cell_updates_per_s"]
+    return out
+
+
 # ------------------------------------------------------------------------------ fitwarm
 
 def cmd_fitwarm(quick):
@@ -524,7 +544,7 @@ def cmd_fitwarm(quick):
     w = W.tiny(16, 20)
     cloud = W.cloud_uniform(20)
     levels = [8, 16, 32, 64]
-    R = 3 if quick else 6
+    R = 3 if quick else 16
     tau = 6.0e5
     s32 = api.Solver(w.solver, "fp32")
     out = dict(experiment="fitwarm", levels=levels, bubbles=20, tau=tau, repeats=R)
@@ -553,13 +573,14 @@ def main():
     import torch
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["uneven3", "surrogate", "rmse", "cfg5", "epsval", "paper500", "orders",
-                                     "fitwarm"])
+                                     "fitwarm", "boundaries"])
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--min-samples", type=int, default=16, help="epsval: pairs every level starts with")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     fn = {"uneven3": cmd_uneven3, "surrogate": cmd_surrogate, "rmse": cmd_rmse, "cfg5": cmd_cfg5,
-          "epsval": cmd_epsval, "paper500": cmd_paper500, "orders": cmd_orders, "fitwarm": cmd_fitwarm}[a.what]
+          "epsval": cmd_epsval, "paper500": cmd_paper500, "orders": cmd_orders, "fitwarm": cmd_fitwarm,
+          "boundaries": cmd_boundaries}[a.what]
     print(json.dumps(fn(a.quick, a.min_samples) if a.what == "epsval" else fn(a.quick)), flush=True)
 
 
