@@ -116,6 +116,32 @@ def test_fitted_summary_estimator_matches_oracle_on_the_union():
         assert abs(got["eps2"] - ref["eps2"]) < 1e-10 * ref["eps2"]
 
 
+def test_run_configuration_is_validated_before_any_device_work():
+    """ofm_run refuses bad configurations on the host (no stream or device is touched)."""
+    L = nv.lib()
+    s = api.Solver(W.SolverParams(sensors=W.centre_sensor()), "fp32")
+    cp = api.cloud_params(W.cloud_uniform(4))
+    res = nv.ofm_run_result()
+
+    def run(**kw):
+        cfg = nv.ofm_run_config()
+        base = dict(L=2, mode=nv.OFM_MODE_TOL, target=1.0, qoi=0, seed=1, max_iterations=1, min_samples=2)
+        base.update(kw)
+        levels = base.pop("N", [8, 16, 24])
+        for k, v in base.items():
+            setattr(cfg, k, v)
+        for i, n in enumerate(levels):
+            cfg.N[i] = n
+        return L.ofm_run(s.h, C.byref(cp), C.byref(cfg), None, None, 0, C.byref(res), None)
+
+    assert run(L=1, N=[8, 16], fit_variances=1) == nv.OFM_EINVAL      # the fit needs two difference levels
+    assert b"variance fit" in L.ofm_last_error()
+    assert run(N=[16, 8, 24]) == nv.OFM_EINVAL                          # levels must refine
+    assert run(target=0.0) == nv.OFM_EINVAL
+    assert run(qoi=5) == nv.OFM_EINVAL                                  # one sensor configured
+    assert run(max_iterations=0) == nv.OFM_EINVAL
+
+
 def test_optimal_samples_rejects_invalid_variances_and_overflow():
     for st2 in ([1.0, -0.1], [1.0, float("nan")]):
         with pytest.raises(nv.OfmError):
