@@ -22,7 +22,6 @@ import argparse
 import ctypes as C
 import hashlib
 import json
-import math
 import os
 import subprocess
 import sys

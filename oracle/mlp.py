@@ -10,7 +10,7 @@ numbers.
 from __future__ import annotations
 
 import math
-from typing import Dict, List, Tuple
+from typing import List, Tuple
 
 import numpy as np
 from scipy.special import erf

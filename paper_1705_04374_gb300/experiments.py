@@ -27,7 +27,6 @@ module only orders the calls and times them with CUDA events.
 from __future__ import annotations
 
 import argparse
-import ctypes as C
 import json
 import math
 import os

@@ -6,7 +6,6 @@ library's kernels (include/ofmlmc.h, MLP section).
 from __future__ import annotations
 
 import ctypes as C
-from typing import Optional, Sequence
 
 import numpy as np
 

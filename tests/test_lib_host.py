@@ -2,7 +2,6 @@
 host-side parts (sampler, estimator, validation) agree with the oracle.
 No device work is requested here."""
 import ctypes as C
-import math
 import os
 import re
 

@@ -10,7 +10,7 @@ the paper uses [0, 100 mm]^3).
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field, replace
+from dataclasses import dataclass, replace
 from typing import List, Tuple
 
 import numpy as np
