@@ -62,11 +62,11 @@ int solve_pairs(ofm_solver* s, const ofm_cloud_params* cloud, const ofm_run_conf
             for (int l = 0; l <= L; ++l) {
                 if (cnt[l] == 0) continue;
                 qf[l].resize(cnt[l]);
-                ofm_group gf{rc->N[l], (int)cnt[l], ids[l].data(), rc->seed, nullptr, qf[l].data(), nullptr};
+                ofm_group gf{rc->N[l], (int)cnt[l], ids[l].data(), rc->seed, nullptr, qf[l].data(), nullptr, nullptr};
                 g.push_back(gf);
                 if (l > 0) {
                     qc[l].resize(cnt[l]);
-                    ofm_group gc{rc->N[l - 1], (int)cnt[l], ids[l].data(), rc->seed, nullptr, qc[l].data(), nullptr};
+                    ofm_group gc{rc->N[l - 1], (int)cnt[l], ids[l].data(), rc->seed, nullptr, qc[l].data(), nullptr, nullptr};
                     g.push_back(gc);
                 }
             }

@@ -691,7 +691,7 @@ static int locate(ofm_batch* b, int group, int sample, size_t bytes, size_t* off
 
 extern "C" int ofm_batch_copy_state(ofm_batch* b, int group, int sample, void* host_buf, size_t bytes) {
     ofm::clear_error();
-    size_t off, n;
+    size_t off = 0, n = 0;
     int rc = locate(b, group, sample, bytes, &off, &n);
     if (rc != OFM_OK) return rc;
     if (!host_buf) return fail(OFM_EINVAL, "NULL buffer");
@@ -712,7 +712,7 @@ extern "C" int ofm_batch_copy_state(ofm_batch* b, int group, int sample, void* h
 
 extern "C" int ofm_batch_set_state(ofm_batch* b, int group, int sample, const void* host_buf, size_t bytes) {
     ofm::clear_error();
-    size_t off, n;
+    size_t off = 0, n = 0;
     int rc = locate(b, group, sample, bytes, &off, &n);
     if (rc != OFM_OK) return rc;
     if (!host_buf) return fail(OFM_EINVAL, "NULL buffer");

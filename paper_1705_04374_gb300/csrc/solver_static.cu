@@ -89,10 +89,12 @@ StaticLayout static_layout(const ofm_solver* s, int N, int M, int nb, size_t n_s
     L.kout = take(Ms * 4);
     L.qoi = take(Ms * sizeof(DevQoi));
     L.sold = take(Ms * OFM_MAX_SENSORS * 8);
-    L.hist = take((Ms * s->cfg.n_sensors * s->cfg.n_out_times ? Ms * s->cfg.n_sensors * s->cfg.n_out_times : 1) * 8);
+    const size_t n_hist = Ms * s->cfg.n_sensors * s->cfg.n_out_times;
+    L.hist = take((n_hist > 0 ? n_hist : 1) * 8);
     L.active = take(16);
     L.gact = take(16);
-    L.bub = take((Ms * nb ? Ms * nb : 1) * 32);
+    const size_t n_bub = Ms * nb;
+    L.bub = take((n_bub > 0 ? n_bub : 1) * 32);
     L.total = at;
     return L;
 }
