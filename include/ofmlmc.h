@@ -92,7 +92,7 @@ typedef struct {
     double p_liq;     /* initial liquid pressure [Pa] (also the pressure unit) */
     double cfl;       /* Courant number (0.3 in the paper) */
     double t_end;     /* end time [s] */
-    double weno_eps;  /* WENO5 epsilon (non-dimensional) */
+    double weno_eps;  /* WENO epsilon of the nonlinear weights (non-dimensional) */
     double domain_L;  /* m */
     int precision;    /* OFM_FP64 or OFM_FP32 (FP32 stencil, FP64 reductions) */
     int bc;           /* OFM_BC_* */
@@ -188,9 +188,10 @@ int ofm_batch_workspace_bytes(const ofm_solver* solver, const ofm_cloud_params* 
  *   (CUDA-graph-captured chunks); *n_active receives the number of samples
  *   that have not reached t_end (0 when all are done).  Synchronises with the
  *   batch's internal stream once per chunk.
- * ofm_batch_qoi:    copies the QoI records (and sensor histories if the group
- *   has a sensor_hist buffer) to the groups' host arrays; returns OFM_ENUMERIC
- *   if any sample's status is non-zero.
+ * ofm_batch_qoi:    copies the QoI records (and the pressure and gas-fraction
+ *   sensor histories of the groups that have sensor_hist / alpha_hist buffers)
+ *   to the groups' host arrays; returns OFM_ENUMERIC if any sample's status is
+ *   non-zero.
  * ofm_batch_copy_state / ofm_batch_set_state: read / overwrite the current
  *   state Q[7][N][N][N] (x fastest, non-dimensional, storage precision) of one
  *   sample; `host_buf` is a host pointer of exactly 7 N^3 elements.  Setting a
