@@ -649,3 +649,52 @@ def test_characteristic_boundary_lets_an_acoustic_pulse_leave():
         left[bc] = energy(_prim(g, Qt)) / energy(Wp)
     assert left[2] < 1e-3
     assert left[2] < 0.5 * left[0]
+
+
+def test_sensor_histories_are_the_step_values_interpolated_onto_the_output_times():
+    """The histories of Sec. 3.2's sensors: a time loop written here (CFL steps
+    of the oracle's RK3, the last one clipped to t_end), the sensor means taken
+    with numpy over the cells whose centre lies within max(r, h), and numpy's
+    linear interpolation onto t_k = k t_end/(K - 1), against the oracle's solve."""
+    sp = W.SolverParams(sensors=(W.centre_sensor()[0], (0.03, 0.05, 0.06, 0.012)), n_out_times=17)
+    n = 16
+    b = cloud.sample_cloud(W.cloud_uniform(4), W.BASE_SEED, 2)
+    q, hist, _ = S.solve(sp, n, b)
+    g = S.grid_from_params(sp, n)
+    u = S.Units(sp.domain_L, sp.p_liq)
+    t_end = sp.t_end / u.t_ref
+    x = (np.arange(n) + 0.5) / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    masks = []
+    for sx, sy, sz, r in sp.sensors:
+        R = max(r / sp.domain_L, 1.0 / n)
+        d2 = (X - sx / sp.domain_L) ** 2 + (Y - sy / sp.domain_L) ** 2 + (Z - sz / sp.domain_L) ** 2
+        masks.append(d2 <= R * R)
+
+    def sensors(Q):
+        Wp = S.cons_to_prim(g, Q.reshape(7, -1)).reshape(7, n, n, n)
+        return [Wp[5][m].mean() for m in masks], [Wp[6][m].mean() for m in masks]
+
+    Q = S.init_cloud(sp, n, b)
+    t, times = 0.0, [0.0]
+    p0, a0 = sensors(Q)
+    ps, als = [p0], [a0]
+    while t < t_end:
+        dt = sp.cfl * g.h / S.max_speed(g, Q)
+        last = t + dt >= t_end
+        if last:
+            dt = t_end - t
+        Q = S.rk3_step(g, Q, dt)
+        t = t_end if last else t + dt
+        times.append(t)
+        p, a = sensors(Q)
+        ps.append(p)
+        als.append(a)
+    assert len(times) - 1 == q["n_steps"]
+    tk = np.arange(sp.n_out_times) * t_end / (sp.n_out_times - 1)
+    ps, als = np.array(ps), np.array(als)
+    for s in range(2):
+        want_p = np.interp(tk, times, ps[:, s]) * sp.p_liq
+        want_a = np.interp(tk, times, als[:, s])
+        assert np.allclose(hist[s], want_p, rtol=1e-12, atol=0)
+        assert np.allclose(q["alpha_hist"][s], want_a, rtol=1e-12, atol=0)
