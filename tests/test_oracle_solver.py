@@ -652,10 +652,12 @@ def test_characteristic_boundary_lets_an_acoustic_pulse_leave():
 
 
 def test_sensor_histories_are_the_step_values_interpolated_onto_the_output_times():
-    """The histories of Sec. 3.2's sensors: a time loop written here (CFL steps
-    of the oracle's RK3, the last one clipped to t_end), the sensor means taken
-    with numpy over the cells whose centre lies within max(r, h), and numpy's
-    linear interpolation onto t_k = k t_end/(K - 1), against the oracle's solve."""
+    """The QoI bookkeeping of a solve against a time loop written here (CFL
+    steps of the oracle's RK3, the last one clipped to t_end): sensor means
+    taken with numpy over the cells whose centre lies within max(r, h), their
+    histories by numpy's linear interpolation onto t_k = k t_end/(K - 1), the
+    peak pressure with its first (x-fastest) cell and first time, the sensor
+    peaks, and the gas-fraction minima with their first times."""
     sp = W.SolverParams(sensors=(W.centre_sensor()[0], (0.03, 0.05, 0.06, 0.012)), n_out_times=17)
     n = 16
     b = cloud.sample_cloud(W.cloud_uniform(4), W.BASE_SEED, 2)
@@ -673,12 +675,13 @@ def test_sensor_histories_are_the_step_values_interpolated_onto_the_output_times
 
     def sensors(Q):
         Wp = S.cons_to_prim(g, Q.reshape(7, -1)).reshape(7, n, n, n)
-        return [Wp[5][m].mean() for m in masks], [Wp[6][m].mean() for m in masks]
+        return [Wp[5][m].mean() for m in masks], [Wp[6][m].mean() for m in masks], Wp[5].ravel()
 
     Q = S.init_cloud(sp, n, b)
     t, times = 0.0, [0.0]
-    p0, a0 = sensors(Q)
+    p0, a0, pf = sensors(Q)
     ps, als = [p0], [a0]
+    peak, peak_i, peak_t = pf.max(), int(np.argmax(pf)), 0.0     # first maximum, x fastest
     while t < t_end:
         dt = sp.cfl * g.h / S.max_speed(g, Q)
         last = t + dt >= t_end
@@ -687,10 +690,19 @@ def test_sensor_histories_are_the_step_values_interpolated_onto_the_output_times
         Q = S.rk3_step(g, Q, dt)
         t = t_end if last else t + dt
         times.append(t)
-        p, a = sensors(Q)
+        p, a, pf = sensors(Q)
         ps.append(p)
         als.append(a)
+        if pf.max() > peak:                                        # a later equal value keeps the first
+            peak, peak_i, peak_t = pf.max(), int(np.argmax(pf)), t
     assert len(times) - 1 == q["n_steps"]
+    assert abs(q["p_peak"] - peak * sp.p_liq) <= 1e-12 * q["p_peak"]
+    assert q["peak_index"] == peak_i and abs(q["p_peak_t"] - peak_t * u.t_ref) <= 1e-12 * u.t_ref
+    ps_a, als_a = np.array(ps), np.array(als)
+    assert np.allclose(q["sensor_peak"], ps_a.max(axis=0) * sp.p_liq, rtol=1e-12, atol=0)
+    assert np.allclose(q["sensor_alpha_min"], als_a.min(axis=0), rtol=1e-12, atol=0)
+    first_min = [times[int(np.argmin(als_a[:, s]))] * u.t_ref for s in range(2)]
+    assert np.allclose(q["sensor_alpha_min_t"], first_min, rtol=1e-12, atol=0)
     tk = np.arange(sp.n_out_times) * t_end / (sp.n_out_times - 1)
     ps, als = np.array(ps), np.array(als)
     for s in range(2):
