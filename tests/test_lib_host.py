@@ -279,3 +279,25 @@ def test_binding_structs_match_the_c_header(tmp_path):
         assert got[(name, "size")] == C.sizeof(cls), name
         for f in cls._fields_:
             assert got[(name, f[0])] == getattr(cls, f[0]).offset, (name, f[0])
+
+
+def test_product_code_never_touches_the_oracle():
+    """The oracle is test infrastructure: no module of the package imports it,
+    no CUDA or C++ source of the library calls or loads it, the public header
+    declares none of it, and the library does not link it."""
+    root = os.path.dirname(os.path.dirname(__file__))
+    pkg = os.path.join(root, "paper_1705_04374_gb300")
+    py_use = re.compile(r"^\s*(import\s+oracle|from\s+oracle\b)|liborc|oracle\.(solver|estimator|mlp|cloud)", re.M)
+    c_use = re.compile(r"liborc|\borc_\w+\s*\(|#include\s+[<\"][^>\"]*oracle")
+    offenders = []
+    for d, _, files in os.walk(pkg):
+        for f in files:
+            path = os.path.join(d, f)
+            if f.endswith(".py") and py_use.search(open(path).read()):
+                offenders.append(path)
+            elif f.endswith((".cu", ".cuh", ".cpp", ".h")) and c_use.search(open(path).read()):
+                offenders.append(path)
+    assert not offenders, offenders
+    assert "orc_" not in open(HEADER).read()
+    lib = nv.lib()
+    assert not hasattr(lib, "orc_solve") and not hasattr(lib, "orc_rk3_step")
