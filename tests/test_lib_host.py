@@ -301,3 +301,15 @@ def test_product_code_never_touches_the_oracle():
     assert "orc_" not in open(HEADER).read()
     lib = nv.lib()
     assert not hasattr(lib, "orc_solve") and not hasattr(lib, "orc_rk3_step")
+
+
+def test_oracle_shares_no_code_with_the_library():
+    """The oracle neither imports the package nor includes its headers or sources."""
+    root = os.path.dirname(os.path.dirname(__file__))
+    odir = os.path.join(root, "oracle")
+    for f in os.listdir(odir):
+        path = os.path.join(odir, f)
+        if f.endswith(".py"):
+            assert not re.search(r"paper_1705_04374_gb300|ofmlmc", open(path).read()), f
+        elif f.endswith((".c", ".h")):
+            assert not re.search(r"#include\s+[<\"][^>\"]*(ofmlmc|csrc|paper_1705)", open(path).read()), f
