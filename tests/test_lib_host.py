@@ -315,3 +315,13 @@ def test_oracle_shares_no_code_with_the_library():
             assert "libofmlmc" not in text, f
         elif f.endswith((".c", ".h")):
             assert not re.search(r"#include\s+[<\"][^>\"]*(ofmlmc|csrc|paper_1705)", open(path).read()), f
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library the binding raises; there is no fallback path."""
+    monkeypatch.setattr(nv, "_lib", None)
+    monkeypatch.setattr(nv, "LIB_PATH", str(tmp_path / "libofmlmc.so"))
+    with pytest.raises(ImportError):
+        nv.lib()
+    with pytest.raises(ImportError):
+        api.Solver(W.SolverParams())
