@@ -23,6 +23,7 @@ import ctypes as C
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -219,10 +220,16 @@ def load_json(path):
 
 
 def kernel_hash():
+    """Hash of the stage-kernel sources without comments and blank lines: a
+    recorded ncu traffic figure stays valid across comment edits only."""
     h = hashlib.sha256()
     for path in KERNEL_SRC:
-        with open(path, "rb") as f:
-            h.update(f.read())
+        with open(path) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        text = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(text.encode())
     return h.hexdigest()[:16]
 
 

@@ -1,11 +1,12 @@
 // Device code of the solver, included once per precision (see types.cuh).
 //
 // The method (Sukys et al. 2017, Sections 2.1-2.2 and 3.1-3.2): the five-
-// equation two-phase model with a stiffened-gas isobaric closure, WENO5
-// reconstruction of primitive variables, an HLLC flux with an upwind alpha2
-// flux and a face velocity for the K div(u) source, a 3-stage low-storage RK
-// update and a CFL time step from a max over all cells, plus on-device
-// reductions of the quantities of interest.
+// equation two-phase model with a stiffened-gas isobaric closure, WENO5 (or
+// the third-order WENO3) reconstruction of primitive variables, an HLLC flux
+// with an upwind alpha2 flux and a face velocity for the K div(u) source, a
+// 3-stage low-storage RK update and a CFL time step from a max over all
+// cells, transmissive, periodic or characteristic far-field ghost cells, plus
+// on-device reductions of the quantities of interest.
 //
 // In double precision the arithmetic follows the FP64 reference's operation
 // order exactly and this file is compiled without FMA contraction, so both

@@ -8,7 +8,7 @@
 //   * One fused kernel per RK stage.  A block owns an 8x8x8 tile: it stages
 //     the tile plus a 3-cell halo along each axis (no corners) into shared
 //     memory as primitives, computes every face flux of the tile once (WENO5
-//     both sides + HLLC) per direction into shared memory, differences them
+//     or WENO3 both sides + HLLC) per direction into shared memory, differences them
 //     into per-cell right-hand sides in registers, and applies the 2N update.
 //     Per cell and stage, HBM sees only Q, dQ in and Q', dQ out (the first stage reads no dQ,
 //     the last writes none).
