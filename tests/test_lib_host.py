@@ -207,6 +207,25 @@ def test_workspace_size_accounts_for_three_state_buffers():
         assert state <= n.value < state * 1.05
 
 
+def test_workspace_holds_both_sensor_histories():
+    """Each sample's pressure and gas-fraction histories (n_sensors x n_out_times
+    doubles each) are part of the workspace."""
+    L = nv.lib()
+    cp = api.cloud_params(W.cloud_uniform(4))
+
+    def bytes_for(n_out):
+        sp = W.SolverParams(sensors=W.eight_sensors(0.03), n_out_times=n_out)
+        s = api.Solver(sp, "fp32")
+        garr = (nv.ofm_group * 1)(api.make_group(sp, 16, list(range(5)), 1).c)
+        n = C.c_size_t()
+        nv.check(L.ofm_batch_workspace_bytes(s.h, C.byref(cp), garr, 1, C.byref(n)), "ws")
+        return n.value
+
+    grow = bytes_for(1001) - bytes_for(1)
+    hist = 5 * 8 * 1000 * 8                     # samples x sensors x added output times x 8 bytes
+    assert 2 * hist <= grow <= 2 * hist + 4096  # two histories, allocation rounding
+
+
 def test_surrogate_cv_host_matches_oracle():
     from paper_1705_04374_gb300 import surrogate as S
     rng = np.random.default_rng(0)
