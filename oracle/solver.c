@@ -220,6 +220,14 @@ static int admissible(const orc_grid* g, const double* w) {
     return 1;
 }
 
+int orc_admissible(const orc_grid* g, const double* w) { return admissible(g, w); }
+
+/* Test hook: face sides that fell back to their cell's primitives in this
+ * thread since the last reset (one count per inadmissible face state). */
+static _Thread_local long orc_fallbacks = 0;
+long orc_fallback_count(void) { return orc_fallbacks; }
+void orc_fallback_reset(void) { orc_fallbacks = 0; }
+
 /* ------------------------------------------------------------------ */
 /* HLLC (Toro et al. 1994) for the five-equation system, direction dir.  */
 /* Reading of the alpha2 treatment (Johnsen & Colonius adaptation, not   */
@@ -468,10 +476,14 @@ int orc_rhs(const orc_grid* g, const double* Q, double* R) {
                             wcl[v] = c0;
                             wcr[v] = p1;
                         }
-                        if (!admissible(g, wl))
+                        if (!admissible(g, wl)) {
                             for (int v = 0; v < NV; ++v) wl[v] = wcl[v];
-                        if (!admissible(g, wr))
+                            ++orc_fallbacks;
+                        }
+                        if (!admissible(g, wr)) {
                             for (int v = 0; v < NV; ++v) wr[v] = wcr[v];
+                            ++orc_fallbacks;
+                        }
                         double F[NV], uf;
                         orc_hllc(g, wl, wr, dir, F, &uf);
                         for (int v = 0; v < NV; ++v) Fl[8 * f + v] = F[v];

@@ -76,6 +76,9 @@ def _lib(count: bool = False) -> C.CDLL:
         lib.orc_advance.argtypes = [G, _D, C.c_double, C.c_int, C.POINTER(C.c_int)]
         lib.orc_advance.restype = C.c_int
         lib.orc_flop_count.restype = C.c_double
+        lib.orc_admissible.argtypes = [G, _D]
+        lib.orc_admissible.restype = C.c_int
+        lib.orc_fallback_count.restype = C.c_long
         _LIBS[name] = lib
     return _LIBS[name]
 
@@ -204,6 +207,22 @@ def advance(g: OrcGrid, Q: np.ndarray, t_end: float, max_steps: int = 100000):
     if rc != 0:
         raise RuntimeError(f"orc_advance rc={rc}")
     return Q, n.value
+
+
+def admissible(g: OrcGrid, w) -> bool:
+    """The face-state test of the positivity fallback (reading of Sec. 2.2)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    return bool(_lib().orc_admissible(C.byref(g), _p(w)))
+
+
+def fallback_count() -> int:
+    """Face states that fell back to their cell's primitives in this thread
+    since the last fallback_reset() (test hook)."""
+    return int(_lib().orc_fallback_count())
+
+
+def fallback_reset() -> None:
+    _lib().orc_fallback_reset()
 
 
 def flop_count() -> float:

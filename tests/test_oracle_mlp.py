@@ -3,6 +3,7 @@ surrogate control variate (unbiasedness with a bad surrogate, variance)."""
 import math
 
 import numpy as np
+import pytest
 
 from oracle import estimator as E
 from oracle import mlp
@@ -20,6 +21,74 @@ def test_gelu_matches_its_definition_and_derivative():
     h = 1e-6
     fd = (mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h)
     assert np.allclose(mlp.gelu_grad(x), fd, atol=1e-8)
+
+
+def test_forward_of_a_network_with_identity_or_off_hidden_units():
+    """Every hidden pre-activation here is >= 47 or <= -59, where exact-erf
+    GELU is the identity or zero in FP64 (erf(x/sqrt 2) rounds to +-1), and
+    the output layer is linear, so the output is integer arithmetic done by
+    hand:
+      layer 1, rows (1, 2) and (-1, 3): z = (67, -61, 70), (68, -59, 65) -> h = (67, 0, 70), (68, 0, 65)
+      layer 2: z = (47, -160), (53, -170) -> h = (47, 0), (53, 0)
+      output:  2*47 - 100 = -6,  2*53 - 100 = 6.
+    A dropped bias, GELU on the output layer (GELU(-6) ~ -6e-9), a missing
+    GELU on a hidden layer or a transposed operand changes the result.  All
+    numbers are exact in BF16, so the BF16-operand forward gives the same."""
+    P = [(np.array([[1.0, -1.0, 2.0], [3.0, 0.0, -1.0]]), np.array([60.0, -60.0, 70.0])),
+         (np.array([[1.0, 0.0], [5.0, 1.0], [-1.0, 2.0]]), np.array([50.0, -300.0])),
+         (np.array([[2.0], [7.0]]), np.array([-100.0]))]
+    X = np.array([[1.0, 2.0], [-1.0, 3.0]])
+    for lowp in (False, True):
+        y, (acts, pres) = mlp.forward(P, X, lowp=lowp)
+        assert np.array_equal(y, [[-6.0], [6.0]])
+        assert np.array_equal(acts[1], [[67.0, 0.0, 70.0], [68.0, 0.0, 65.0]])
+        assert np.array_equal(pres[1], [[47.0, -160.0], [53.0, -170.0]])
+
+
+def test_forward_gelu_at_one_is_the_normal_cdf():
+    """A hidden unit with pre-activation +-1: GELU(x) = x Phi(x), with the
+    tabulated standard normal CDF Phi(1) = 0.8413447460685429."""
+    P = [(np.array([[1.0, -1.0]]), np.zeros(2)), (np.array([[1.0], [1.0]]), np.array([0.25]))]
+    y, _ = mlp.forward(P, np.array([[1.0]]))
+    phi1 = 0.8413447460685429
+    assert abs(y[0, 0] - (phi1 - (1.0 - phi1) + 0.25)) < 1e-15
+
+
+def test_bf16_rounding_of_listed_bit_patterns():
+    """Round to nearest, ties to even, on FP32 bit patterns (IEEE 754
+    roundTiesToEven onto the 8-bit-significand format)."""
+    cases = {
+        0x3F800000: 0x3F80,   # 1.0
+        0x3F807FFF: 0x3F80,   # just below the midpoint of 1.0 and 1 + 2^-7
+        0x3F808000: 0x3F80,   # midpoint, lower neighbour even
+        0x3F808001: 0x3F81,   # just above the midpoint
+        0x3F818000: 0x3F82,   # midpoint, upper neighbour even
+        0xBF818000: 0xBF82,   # the same, negative
+        0x7F7F7FFF: 0x7F7F,   # largest finite BF16
+        0x7F7F8000: 0x7F80,   # midpoint of the largest finite and infinity: to infinity (even)
+        0x00008000: 0x0000,   # subnormal midpoint, lower neighbour (zero) even
+        0x00018000: 0x0002,   # subnormal midpoint, upper neighbour even
+        0x80000000: 0x8000,   # -0
+    }
+    bits = np.array(list(cases), dtype=np.uint32)
+    got = mlp.bf16(bits.view(np.float32)).astype(np.float32).view(np.uint32)
+    want = np.array(list(cases.values()), dtype=np.uint32) << 16
+    assert np.array_equal(got, want), [hex(v) for v in got]
+
+
+def test_bf16_matches_torch_conversion():
+    """Against PyTorch's own FP32 -> BF16 conversion on normal, subnormal and
+    near-overflow values (NaN excluded)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    u = rng.integers(0, 2 ** 32, size=200000, dtype=np.uint64).astype(np.uint32)
+    u = np.concatenate([u, rng.integers(0, 2 ** 24, size=5000).astype(np.uint32),
+                        0x7F7F0000 + rng.integers(0, 2 ** 16, size=5000).astype(np.uint32)])
+    f = u.view(np.float32)
+    f = f[~np.isnan(f)]
+    ref = torch.from_numpy(f.copy()).to(torch.bfloat16).to(torch.float32).numpy()
+    got = mlp.bf16(f).astype(np.float32)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
 
 
 def test_backward_matches_finite_differences():

@@ -229,6 +229,126 @@ def test_hllc_mirror_symmetry():
         assert abs(ufm + uf) < 1e-12
 
 
+# ---------------------------------------------------------------- positivity fallback (reading of Sec. 2.2)
+
+def test_face_admissibility_clauses_and_their_directions():
+    """Each clause of the face-state test on its own, on both sides of its
+    threshold.  The pressure clause is the positivity of the frozen squared
+    sound speed; in the pure-phase limits that is the textbook stiffened-gas
+    condition p + p_c > 0 (liquid) and p > 0 (ideal gas)."""
+    g = S.make_grid(4, gamma=GAM, pc_nd=PC)
+    base = np.array([0.5, 0.0025, 0.1, -0.2, 0.3, 1.0, 0.5])
+    assert S.admissible(g, base)
+
+    def with_(i, v, w=base):
+        w = w.copy()
+        w[i] = v
+        return w
+    # alpha2 in [0, 1], both ends included
+    assert S.admissible(g, with_(6, 0.0)) and S.admissible(g, with_(6, 1.0))
+    assert not S.admissible(g, with_(6, -1e-9)) and not S.admissible(g, with_(6, 1.0 + 1e-9))
+    # partial densities strictly positive
+    for i in (0, 1):
+        assert S.admissible(g, with_(i, 1e-12))
+        assert not S.admissible(g, with_(i, 0.0)) and not S.admissible(g, with_(i, -1e-9))
+    # liquid (alpha2 = 0): p + p_c > 0
+    liq = with_(6, 0.0)
+    assert S.admissible(g, with_(5, -PC[0] * (1.0 - 1e-9), liq))
+    assert not S.admissible(g, with_(5, -PC[0] * (1.0 + 1e-9), liq))
+    assert S.admissible(g, with_(5, -0.5 * PC[0], liq))            # tension below p_c is fine
+    # gas (alpha2 = 1): p > 0
+    gas = with_(6, 1.0)
+    assert S.admissible(g, with_(5, 1e-9, gas))
+    assert not S.admissible(g, with_(5, 0.0, gas)) and not S.admissible(g, with_(5, -1e-9, gas))
+    # velocities never matter
+    assert S.admissible(g, np.array([0.5, 0.0025, -40.0, 25.0, 1e3, 1.0, 0.5]))
+
+
+def _bump_state(nx):
+    """1D primitives: a sharp two-cell alpha2 bump (1e-6 outside, 1 - 1e-6 inside)
+    on smooth partial densities, velocities and pressure."""
+    x = (np.arange(nx) + 0.5) / nx
+    two_pi = 2.0 * math.pi
+    Wp = np.zeros((7, nx))
+    Wp[0] = 1.0 + 0.1 * np.sin(two_pi * x)
+    Wp[1] = 0.005 * (1.0 + 0.1 * np.cos(two_pi * x))
+    Wp[2] = 0.05 * np.sin(two_pi * x)
+    Wp[3] = 0.02 * np.cos(two_pi * x)
+    Wp[4] = -0.01 * np.sin(2.0 * two_pi * x)
+    Wp[5] = 1.0 + 0.1 * np.cos(two_pi * x)
+    Wp[6] = 1e-6
+    Wp[6, nx // 2 - 1:nx // 2 + 1] = 1.0 - 1e-6
+    return Wp
+
+
+def _x_rhs_composed(g, Wp, fallback_all=True):
+    """Rows 0-6 of the right-hand side of a 1D state along x, composed face by
+    face from the pinned WENO5 and HLLC routines and this test's own face
+    test (alpha2 in [0, 1], partial densities > 0, p > 0; p + Pi/(Gamma+1) > 0
+    follows from p > 0 since Pi >= 0).  An inadmissible face state takes its
+    cell's primitives: all seven (fallback_all) or only alpha2.  Returns the
+    rows and the number of face states that fell back."""
+    nx = Wp.shape[1]
+    h = g.h
+    cl = lambda i: min(max(i, 0), nx - 1)                     # transmissive ghosts
+    P = lambda v, i: Wp[v, cl(i)]
+
+    def ok(w):
+        return 0.0 <= w[6] <= 1.0 and w[0] > 0.0 and w[1] > 0.0 and w[5] > 0.0
+    F = np.zeros((nx + 1, 7))
+    uf = np.zeros(nx + 1)
+    n_fb = 0
+    for f in range(nx + 1):
+        wl = np.array([S.weno5(P(v, f - 3), P(v, f - 2), P(v, f - 1), P(v, f), P(v, f + 1)) for v in range(7)])
+        wr = np.array([S.weno5(P(v, f + 2), P(v, f + 1), P(v, f), P(v, f - 1), P(v, f - 2)) for v in range(7)])
+        assert min(wl[5], wr[5]) > 0.5                          # the pressure clause is never marginal here
+        for w, c in ((wl, f - 1), (wr, f)):
+            if not ok(w):
+                n_fb += 1
+                if fallback_all:
+                    w[:] = Wp[:, cl(c)]
+                else:
+                    w[6] = Wp[6, cl(c)]
+        F[f], uf[f] = S.hllc(g, wl, wr, 0)
+    R = -(F[1:] - F[:-1]).T * (1.0 / h)
+    # alpha2 row: + (alpha2 + K) div u with K of Eq. (var_K), rho_k c_k^2 = g_k (p + pc_k)
+    a2 = np.clip(Wp[6], 0.0, 1.0)
+    z1, z2 = GAM[0] * (Wp[5] + PC[0]), GAM[1] * (Wp[5] + PC[1])
+    K = (1 - a2) * a2 * (z1 - z2) / ((1 - a2) * z2 + a2 * z1)
+    R[6] += (Wp[6] + K) * (uf[1:] - uf[:-1]) * (1.0 / h)
+    return R, n_fb
+
+
+def test_rhs_falls_back_to_the_cell_state_for_all_seven_primitives():
+    """WENO5 overshoots alpha2 above 1 at the faces inside a sharp two-cell
+    bump (the other variables are smooth, so only the alpha2 clause fails).
+    The oracle's right-hand side must equal the one composed with every
+    primitive of such a face state replaced by its cell's, fall back at
+    exactly the same face states, and differ clearly from replacing alpha2
+    alone (so the comparison can tell the two apart)."""
+    nx = 16
+    g = S.make_grid(nx, 1, 1, gamma=GAM, pc_nd=PC)
+    Wp = _bump_state(nx)
+    Q = S.prim_to_cons(g, Wp)
+    S.fallback_reset()
+    R = S.rhs(g, Q).reshape(7, nx)
+    n_oracle = S.fallback_count()
+    Rc, n_fb = _x_rhs_composed(g, Wp)
+    assert n_fb > 0 and n_oracle == n_fb
+    scale = np.max(np.abs(Rc), axis=1, keepdims=True)
+    assert np.all(np.abs(R - Rc) <= 1e-12 * scale)
+    Ralpha, _ = _x_rhs_composed(g, Wp, fallback_all=False)
+    assert np.max(np.abs(Ralpha - Rc) / scale) > 1e-4
+
+
+def test_smooth_state_needs_no_fallback():
+    g = S.make_grid(8, gamma=GAM, pc_nd=PC, bc=1)
+    Q = S.prim_to_cons(g, W.smooth_periodic_primitives(8, seed=5).reshape(7, -1))
+    S.fallback_reset()
+    S.rhs(g, Q)
+    assert S.fallback_count() == 0
+
+
 # ---------------------------------------------------------------- low-storage RK3
 
 def _butcher():
