@@ -8,13 +8,18 @@ A cell-update is one cell advanced by one full 3-stage RK step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
                     [--impl ours|reference]
+    python bench.py --profile-case [--samples 64] [--steps 2] [--precision ..] [--variant 0|1]
 
 value: cell-updates/s over K full solves with the clouds already resident in
 HBM (CUDA events on the launching stream; barrier + synchronize around the
 timed region; max over ranks).  e2e: the same metric through the C ABI call
 ofm_solve_batch with host arrays (cloud upload and QoI download inside the
 timed region).  --impl reference times the FP64 CPU oracle on the host cores
-on a bounded sample of the same workload.
+on a bounded sample of the same workload.  --profile-case runs a small fixed
+case for profiler captures (initial condition, then --steps RK3 steps with one
+launch per stage and CUDA events around each stage kernel; with 64 clouds each
+FP32 state buffer holds 470 MB, larger than the 129 MB L2, and the device
+holds about 1.4 GB) and prints the average stage-kernel time.
 """
 from __future__ import annotations
 
@@ -45,10 +50,13 @@ FLOPS_FILE = os.path.join(ROOT, "paper_1705_04374_gb300", "data", "flops_per_cel
 TRAFFIC_FILE = os.path.join(ROOT, "paper_1705_04374_gb300", "data", "ncu_traffic.json")
 KERNEL_SRC = [os.path.join(ROOT, "paper_1705_04374_gb300", "csrc", f) for f in ("kernels.cuh", "types.cuh")]
 
-# FP32 / FP64 non-tensor peaks from unit counts and the maximum SM clock:
-# 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 at the nominal
-# 1.25 TFLOP/s of the part.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP32 non-tensor peak from unit counts: the device's SM count (queried) x 128
+# FP32 lanes x 2 flops per multiply-add x the maximum SM clock (measured
+# peaks file, else nvidia-smi's clocks.max.sm, else 2070 MHz).  Packed
+# two-lane FP32 instructions (FFMA2) do not raise it: a register FFMA2 chain
+# probe runs at the scalar rate.  FP64 at the nominal 1.25 TFLOP/s of the part.
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_FALLBACK = 2070.0
 FP64_PEAK_TFLOPS = 1.25
 HBM_FALLBACK_GBS = 6800.0
 
@@ -60,8 +68,13 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--samples", type=int, default=M_SAMPLES)
-    return p.parse_args()
+    p.add_argument("--samples", type=int, default=None)
+    p.add_argument("--profile-case", action="store_true")
+    p.add_argument("--variant", type=int, default=0, help="--profile-case: 0 one block per tile, 1 persistent")
+    a = p.parse_args()
+    if a.samples is None:
+        a.samples = 64 if a.profile_case else M_SAMPLES
+    return a
 
 
 def dist_env():
@@ -132,7 +145,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic: seeded random clouds", "config": config_dict("fp64", 0),
+        "data": "synthetic: seeded random clouds", "config": reference_config(cores),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"each step: {cores} of the 512 clouds (one per host thread), one RK3 "
                                    "step from the initial condition on 64^3, plain FP64 C oracle"},
@@ -209,6 +222,29 @@ def config_dict(precision, world, samples=M_SAMPLES):
             "parallelism": f"replicas x{max(world, 1)} (independent samples per GPU)",
             "l2": f"inputs {'larger' if buf_gb > 0.129 else 'smaller'} than L2: 3 state buffers of "
                   f"{buf_gb:.2f} GB ({precision}) per GPU"}
+
+
+def reference_config(cores):
+    """The reference arm's workload: the ensemble's clouds, timed on the CPU
+    as a bounded sample (one RK3 step per cloud from the initial condition)."""
+    return {"workload": "ensemble: seeded clouds x 20 bubbles, 64^3 (the same clouds as the GPU arm)",
+            "grid": N_GRID, "bubbles": 20, "stencil_precision": "fp64", "reductions": "f64",
+            "timed": f"each step: {cores} clouds (one per host thread), one RK3 step from the initial "
+                     "condition, plain FP64 C oracle on the host cores",
+            "parallelism": "host threads, one cloud each"}
+
+
+def fp32_peak_tflops(device_index, peaks, clk):
+    """SMs x 128 lanes x 2 x max SM clock, with where each factor came from."""
+    import torch
+    sms = torch.cuda.get_device_properties(device_index).multi_processor_count
+    mhz, src = SM_MAX_MHZ_FALLBACK, "default 2070 MHz"
+    if peaks and peaks.get("sm_max_mhz"):
+        mhz, src = float(peaks["sm_max_mhz"]), "measured peaks file"
+    elif clk and clk.get("sm_max_mhz"):
+        mhz, src = float(clk["sm_max_mhz"]), "nvidia-smi clocks.max.sm"
+    tf = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    return tf, f"derived: {sms} SMs (device query) x {FP32_LANES_PER_SM} FP32 lanes x 2 x {mhz:.0f} MHz ({src})"
 
 
 def load_json(path):
@@ -367,11 +403,18 @@ def run_ours(args):
     es = 4 if args.precision == "fp32" else 8
     # words per cell: stage 1 Q in, Q' and dQ out; stage 2 Q, dQ in, Q', dQ out; stage 3 Q, dQ in, Q' out
     bytes_per_cell_stage = (21 + 28 + 21) / 3.0 * es
+    # DRAM bytes per cell of each of the three stage launches (one ncu capture
+    # each), averaged like the CUDA-event time: traffic of the average launch
     traffic_rec = load_json(TRAFFIC_FILE) or {}
     traffic = None
     if traffic_rec.get("kernel_hash") == kernel_hash() and traffic_rec.get("precision") == args.precision:
-        traffic = traffic_rec.get("dram_bytes_per_cell_stage") * cells_per_launch
-    alu_peak = FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS
+        per_stage = traffic_rec.get("dram_bytes_per_cell_stage_by_stage")
+        if per_stage and len(per_stage) == 3:
+            traffic = float(np.mean(per_stage)) * cells_per_launch
+    if args.precision == "fp32":
+        alu_peak, alu_peak_src = fp32_peak_tflops(local, peaks, clk)
+    else:
+        alu_peak, alu_peak_src = FP64_PEAK_TFLOPS, "nominal FP64 of the part"
     achieved_tflops = f_stage * cells_per_launch / (avg_stage_ms / 1e3) / 1e12 if f_stage else None
     achieved_gbs = bytes_per_cell_stage * cells_per_launch / (avg_stage_ms / 1e3) / 1e9
     alu_ceiling = alu_peak * 1e12 / f_stage if f_stage else float("inf")   # cell-stages/s
@@ -379,8 +422,9 @@ def run_ours(args):
     if alu_ceiling <= hbm_ceiling and achieved_tflops is not None:
         roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": achieved_tflops / alu_peak, "traffic": traffic,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if args.precision == "fp32"
-                    else "nominal FP64 of the part",
+                    "traffic_per_stage_B_per_cell": traffic_rec.get("dram_bytes_per_cell_stage_by_stage")
+                    if traffic is not None else None,
+                    "peak_source": alu_peak_src,
                     "kernel": "stage_kernel (fused WENO5 + HLLC + 2N update)",
                     "per_launch": {"cells": cells_per_launch, "flops_per_cell": f_stage,
                                    "avg_ms": avg_stage_ms, "launches_timed": stage_n},
@@ -425,9 +469,32 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """Small fixed case for profiler captures (see the module docstring)."""
+    import torch
+
+    from paper_1705_04374_gb300 import api
+    torch.cuda.set_device(0)
+    w, sp = workload(args.precision)
+    s = api.Solver(sp, args.precision)
+    g = api.make_group(sp, N_GRID, list(range(args.samples)), W.BASE_SEED)
+    b = api.Batch(s, w.cloud, [g])
+    b.init()
+    b.set_variant(args.variant)
+    b.set_profiling(True)
+    b.run(args.steps)
+    torch.cuda.synchronize()
+    ms, n = b.stage_time()
+    print(f"profile case: {args.samples} x {N_GRID}^3 {args.precision}, variant {args.variant}, {args.steps} steps, "
+          f"stage kernel avg {ms / max(n, 1):.3f} ms over {n} launches")
+    b.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -598,6 +598,65 @@ __device__ __forceinline__ void hllc_frame(const float* wl, const float* wr, flo
     F[7] = uf;
 }
 
+// Packed single-precision arithmetic on two independent values at once
+// (sm_100 family: one instruction issues both lanes).  Subtraction is a
+// multiply-add with -1, which is exact in its product.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(1.0f / a.x, 1.0f / a.y); }
+
+// WENO5 states of a run of R faces (the arithmetic of face_run_fp32's
+// scalar loop) for two variables at once: lane x from Pa, lane y from Pb.
+template <int R>
+__device__ __forceinline__ void weno5_run2(const float* __restrict__ Pa, const float* __restrict__ Pb,
+                                           const int (&idx)[R + 5], float eps4s, float2 (&wl)[R],
+                                           float2 (&wr)[R]) {
+    const float2 eps4 = f2(eps4s), k = f2(13.0f / 3.0f);
+    float2 p[R + 5];
+#pragma unroll
+    for (int i = 0; i < R + 5; ++i) p[i] = make_float2(Pa[idx[i]], Pb[idx[i]]);
+    float2 d[R + 4], D[R + 3], sv[R + 3];
+#pragma unroll
+    for (int i = 0; i < R + 4; ++i) d[i] = sub2(p[i + 1], p[i]);
+#pragma unroll
+    for (int i = 0; i < R + 3; ++i) {
+        D[i] = sub2(d[i + 1], d[i]);
+        sv[i] = fma2(mul2(k, D[i]), D[i], eps4);
+    }
+#pragma unroll
+    for (int j = 2; j <= R + 2; ++j) {   // cell idx[j]
+        const float2 tl = fma2(f2(2.0f), d[j - 1], D[j - 2]);
+        const float2 tm = add2(d[j - 1], d[j]);
+        const float2 th = fma2(f2(-2.0f), d[j], D[j]);
+        float2 El = fma2(tl, tl, sv[j - 2]), Em = fma2(tm, tm, sv[j - 1]), Eh = fma2(th, th, sv[j]);
+        El = mul2(El, El);
+        Em = mul2(Em, Em);
+        Eh = mul2(Eh, Eh);
+        const float2 X = mul2(Em, Eh), Y6 = mul2(f2(6.0f), mul2(El, Eh)), Z = mul2(El, Em);
+        if (j <= R + 1) {   // left state of face j - 2 of the run
+            const float2 hd = mul2(f2(0.5f), d[j]);
+            const float2 a2 = mul2(f2(3.0f), Z);
+            const float2 q0 = fma2(D[j - 2], f2(1.0f / 3.0f), mul2(f2(0.5f), d[j - 1]));
+            const float2 q1 = fma2(D[j - 1], f2(-1.0f / 6.0f), hd);
+            const float2 q2 = fma2(D[j], f2(-1.0f / 6.0f), hd);
+            const float2 num = fma2(X, q0, fma2(Y6, q1, mul2(a2, q2)));
+            wl[j - 2] = fma2(num, rcp2(add2(add2(X, Y6), a2)), p[j]);
+        }
+        if (j >= 3) {       // right state of face j - 3 of the run
+            const float2 hd = mul2(f2(0.5f), d[j - 1]);
+            const float2 a2 = mul2(f2(3.0f), X);
+            const float2 q0 = fma2(D[j], f2(1.0f / 3.0f), mul2(f2(-0.5f), d[j]));
+            const float2 q1 = fma2(D[j - 1], f2(-1.0f / 6.0f), mul2(f2(-1.0f), hd));
+            const float2 q2 = fma2(D[j - 2], f2(-1.0f / 6.0f), mul2(f2(-1.0f), hd));
+            const float2 num = fma2(Z, q0, fma2(Y6, q1, mul2(a2, q2)));
+            wr[j - 3] = fma2(num, rcp2(add2(add2(Z, Y6), a2)), p[j]);
+        }
+    }
+}
+
 // One face in single precision: stencil of six staged cells (staged indices
 // i6); vo[v] is the staged offset of face-frame variable v (slot 2 the normal
 // velocity, 3 and 4 the tangential ones), so the states are reconstructed
@@ -644,9 +703,27 @@ __device__ __forceinline__ void face_run_fp32(const Eos<float>& e, const float* 
                                               float* __restrict__ dst, int step, int stride) {
     float wl[R][7], wr[R][7];
     const float eps4 = 4.0f * e.eps;
-    const float k = 13.0f / 3.0f;
+    // the face-frame velocities (2, 3) and (4, 5) in packed pairs (packing the
+    // partial densities (0, 1) as well needs more registers than the three
+    // resident blocks per SM leave, and the spills cost more than it saves)
+    constexpr int V0 = 2;
 #pragma unroll
-    for (int v = 0; v < 7; ++v) {
+    for (int v = V0; v < 6; v += 2) {
+        float2 l2[R], r2[R];
+        weno5_run2<R>(sW + vo[v], sW + vo[v + 1], idx, eps4, l2, r2);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            wl[r][v] = l2[r].x;
+            wl[r][v + 1] = l2[r].y;
+            wr[r][v] = r2[r].x;
+            wr[r][v + 1] = r2[r].y;
+        }
+    }
+    // alpha2 (variable 6) and the partial densities one at a time
+#pragma unroll
+    for (int si = 0; si < 1 + V0; ++si) {
+        const int v = si == 0 ? 6 : si - 1;
+        const float k = 13.0f / 3.0f;
         const float* P = sW + vo[v];
         float p[R + 5];
 #pragma unroll
@@ -949,9 +1026,20 @@ __device__ __forceinline__ void face_store(const Eos<T>& e, const T* __restrict_
     }
 }
 
+// The tile cells a thread owns for the accumulation and the update: in
+// single precision two x-neighbours (2t, 2t+1), so the update moves 8 bytes
+// per global access; in double precision t and t + NT.
+template <typename T>
+constexpr bool kPairCells = std::is_same<T, float>::value;
+template <typename T>
+__device__ __forceinline__ int own_cell(int k) {
+    if constexpr (kPairCells<T>) return 2 * (int)threadIdx.x + k;
+    return (int)threadIdx.x + k * NT;
+}
+
 // Right-hand sides of one tile's cells (faces direction by direction,
 // per-cell flux differences and the face-velocity divergence), from the
-// primitives staged in sW.  Cell k of this thread is threadIdx.x + k * NT.
+// primitives staged in sW.  Cell k of this thread is own_cell<T>(k).
 template <typename T>
 struct TileRhs {
     T rhs[CELLS_PER_THREAD][7];
@@ -1029,9 +1117,43 @@ __device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>&
             face_store<T, ORD>(e, sW, i6, dir, sF + c, NCELL);
         }
         __syncthreads();
+        if constexpr (kPairCells<T>) {
+            // cells c, c + 1 (x-neighbours): both lanes of each difference at once
+            const int c = own_cell<T>(0);
+            const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+            const int cd = dir == 0 ? x : (dir == 1 ? y : z);
+            const int step = dir == 0 ? 1 : (dir == 1 ? 8 : 64);
+            const int line = dir == 0 ? c >> 3 : (dir == 1 ? x + 8 * z : c & 63);
+            const float* __restrict__ Fb = sFb + dir * 8 * TS * TS;
+            const float2 mih = f2(-(float)invh);
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const float2 Fn = *reinterpret_cast<const float2*>(sF + v * NCELL + c);
+                float2 Fr;
+                if (dir == 0) {
+                    Fr.x = sF[v * NCELL + c + 1];
+                    Fr.y = x + 1 < TS - 1 ? sF[v * NCELL + c + 2] : Fb[v * TS * TS + line];
+                } else {
+                    Fr = cd < TS - 1 ? *reinterpret_cast<const float2*>(sF + v * NCELL + c + step)
+                                     : *reinterpret_cast<const float2*>(Fb + v * TS * TS + line);
+                }
+                const float2 dF = sub2(Fr, Fn);
+                if (v < 7) {
+                    const float2 r = fma2(dF, mih, make_float2(rhs[0][v], rhs[1][v]));
+                    rhs[0][v] = r.x;
+                    rhs[1][v] = r.y;
+                } else {
+                    const float2 r = fma2(dF, f2((float)invh), make_float2(divu[0], divu[1]));
+                    divu[0] = r.x;
+                    divu[1] = r.y;
+                }
+            }
+            __syncthreads();
+            continue;
+        }
 #pragma unroll
         for (int k = 0; k < CELLS_PER_THREAD; ++k) {
-            const int c = threadIdx.x + k * NT;
+            const int c = own_cell<T>(k);
             if (c < NCELL) {
                 const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
                 const int cd = dir == 0 ? x : (dir == 1 ? y : z);
@@ -1056,7 +1178,7 @@ __device__ __forceinline__ void tile_cell_pa(const T* __restrict__ sW, T (&pc)[C
                                              T (&ac)[CELLS_PER_THREAD]) {
 #pragma unroll
     for (int k = 0; k < CELLS_PER_THREAD; ++k) {
-        const int c = threadIdx.x + k * NT;
+        const int c = own_cell<T>(k);
         if (c < NCELL) {
             const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
             const int si = (z * TS + y) * RW + XOFF + x;   // row_off(y, z) + x for tile cells
@@ -1087,9 +1209,49 @@ __device__ __forceinline__ void tile_update(const Params<T>& P, const TileCtx<T>
     const T A = (T)P.rkA[STAGE], B = (T)P.rkB[STAGE];
     RedT<T> red;
     red_init(red);
+    if constexpr (kPairCells<T>) {
+        // cells c, c + 1: alpha2 source per cell, then 8-byte loads and stores
+        const int c = own_cell<T>(0);
+        const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const T p = pc[k];
+            const T a2raw = ac[k];
+            const T a2 = clamp01(a2raw);
+            const T a1 = T(1) - a2;
+            const T z1 = e.g1 * (p + e.pc1);  // rho_1 c_1^2
+            const T z2 = e.g2 * (p + e.pc2);  // rho_2 c_2^2
+            const T K = a1 * a2 * (z1 - z2) / (a1 * z2 + a2 * z1);
+            rhs[k][6] += (a2raw + K) * divu[k];
+        }
+        const size_t gi = ((size_t)(bw.z0 + z) * N + (bw.y0 + y)) * N + (bw.x0 + x);
+        float2 qn[7];
+#pragma unroll
+        for (int v = 0; v < 7; ++v) {
+            const float2 q = *reinterpret_cast<const float2*>(Qin + v * n3 + gi);
+            float2 d = mul2(f2(dt), make_float2(rhs[0][v], rhs[1][v]));
+            if (STAGE > 0) d = fma2(f2(A), *reinterpret_cast<const float2*>(dQ + v * n3 + gi), d);
+            if (STAGE < 2) *reinterpret_cast<float2*>(dQ + v * n3 + gi) = d;
+            qn[v] = fma2(f2(B), d, q);
+            *reinterpret_cast<float2*>(Qout + v * n3 + gi) = qn[v];
+        }
+        if (STAGE == 2) {
+            T q0[7], q1[7];
+#pragma unroll
+            for (int v = 0; v < 7; ++v) {
+                q0[v] = qn[v].x;
+                q1[v] = qn[v].y;
+            }
+            red_cell(e, q0, (long long)gi, red);
+            red_cell(e, q1, (long long)gi + 1, red);
+            const long long tile = tile_index - G.block0 - (long long)bw.s_local * G.tps;
+            block_reduce_write(red_widen(red), G.part + (size_t)bw.s_local * G.tps + tile);
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < CELLS_PER_THREAD; ++k) {
-        const int c = threadIdx.x + k * NT;
+        const int c = own_cell<T>(k);
         if (c < NCELL) {
             const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
             const T p = pc[k];
@@ -1137,7 +1299,7 @@ __device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& 
 
 // One RK stage, one block per tile (ORD: WENO order, 5 or 3).
 template <typename T, int STAGE, int ORD>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
     stage_kernel(const __grid_constant__ Params<T> P, int parity) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sW = reinterpret_cast<T*>(smem_raw);  // [7][NCROSS] primitives, compact layout
@@ -1184,7 +1346,7 @@ __device__ __forceinline__ long long next_active(const Params<T>& P, long long t
 // update, so the update's global loads and the next tile's copies are in
 // flight together.  Same arithmetic as stage_kernel.
 template <typename T, int STAGE, int ORD>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
     stage_kernel_persistent(const __grid_constant__ Params<T> P, int parity) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sW = reinterpret_cast<T*>(smem_raw);
@@ -1449,7 +1611,7 @@ unsigned persistent_grid(const Params<T>& P) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long want = (long long)sms * (sizeof(T) == 4 ? 3 : 1);
+    const long long want = (long long)sms * (sizeof(T) == 4 ? BLOCKS_FP32 : 1);
     return (unsigned)(P.total_blocks < want ? P.total_blocks : want);
 }
 

@@ -22,6 +22,9 @@ constexpr int NT = 256;                  // threads per block (measured better t
 constexpr int CELLS_PER_THREAD = (NCELL + NT - 1) / NT;  // 2
 constexpr int NEAR_RUN = 2;             // FP32: consecutive near faces per thread task (1: one face per task)
 constexpr int CHUNK_STEPS = 8;           // steps per captured graph (even)
+// resident FP32 stage-kernel blocks per SM: 80 registers per thread (two blocks
+// at up to 128 registers measured 10 % slower: latency hiding wins over spills)
+constexpr int BLOCKS_FP32 = 3;
 
 
 template <typename T>
