@@ -32,6 +32,7 @@
 #include <new>
 #include <vector>
 
+#include "host_shared.cuh"
 #include "internal.h"
 #include "ofmlmc.h"
 #include "types.cuh"
@@ -111,31 +112,12 @@ struct ofm_batch {
 
 namespace {
 
-// Sensor membership: cells whose centre lies within max(r, h) of the sensor
-// centre (integer-derived coordinates, FP64), listed in increasing linear index.
-void sensor_cells(const ofm_solver* s, int N, GroupHost& g) {
-    const double h = 1.0 / N;
-    g.sens_cells.clear();
-    g.sens_off[0] = 0;
-    for (int k = 0; k < s->cfg.n_sensors; ++k) {
-        const double cx = s->cfg.sensors[k][0] / s->L, cy = s->cfg.sensors[k][1] / s->L;
-        const double cz = s->cfg.sensors[k][2] / s->L, r = s->cfg.sensors[k][3] / s->L;
-        const double R = r > h ? r : h;
-        for (int z = 0; z < N; ++z)
-            for (int y = 0; y < N; ++y)
-                for (int x = 0; x < N; ++x) {
-                    const double dx = (x + 0.5) * h - cx, dy = (y + 0.5) * h - cy, dz = (z + 0.5) * h - cz;
-                    if (dx * dx + dy * dy + dz * dz <= R * R) g.sens_cells.push_back((z * N + y) * N + x);
-                }
-        g.sens_off[k + 1] = (int)g.sens_cells.size();
-    }
-}
+void sensor_cells(const ofm_solver* s, int N, GroupHost& g) { sensor_cell_list(s, N, g.sens_cells, g.sens_off); }
 
 template <typename T>
 void fill_params(ofm_batch* b, Params<T>& P) {
     std::memset(&P, 0, sizeof(P));
     const ofm_solver_config& c = b->solver->cfg;
-    const double pref = b->solver->p_ref;
     P.n_groups = b->n_groups;
     long long blk = 0;
     int slot = 0;
@@ -174,36 +156,7 @@ void fill_params(ofm_batch* b, Params<T>& P) {
     P.s.n_active = (int*)(b->ws + b->off_active);
     P.s.g_active = (int*)(b->ws + b->off_active + 16);
     P.s.bubbles = (const double*)(b->ws + b->off_bub);
-    const double g1 = c.gamma[0], g2 = c.gamma[1];
-    const double pc1 = c.pc[0] / pref, pc2 = c.pc[1] / pref;
-    P.eos.g1 = (T)g1;
-    P.eos.g2 = (T)g2;
-    P.eos.pc1 = (T)pc1;
-    P.eos.pc2 = (T)pc2;
-    P.eos.gi1 = (T)(1.0 / (g1 - 1.0));
-    P.eos.gi2 = (T)(1.0 / (g2 - 1.0));
-    P.eos.pi1 = (T)(g1 * pc1 / (g1 - 1.0));
-    P.eos.pi2 = (T)(g2 * pc2 / (g2 - 1.0));
-    P.eos.eps = (T)c.weno_eps;
-    for (int s = 0; s < 3; ++s) {
-        P.rkA[s] = RK_A[s];
-        P.rkB[s] = RK_B[s];
-    }
-    P.bc = c.bc;
-    P.bc_penalty = c.bc_penalty;
-    P.weno_order = c.weno_order == 3 ? 3 : 5;
-    P.nb = b->nb;
-    P.n_sens = c.n_sensors;
-    P.n_out = c.n_out_times;
-    P.max_steps = c.max_steps;
-    P.t_end = c.t_end / b->solver->t_ref;
-    P.cfl = c.cfl;
-    P.p_gas = c.p_gas / pref;
-    P.p_liq = c.p_liq / pref;
-    P.p_cloud = c.p_cloud / pref;
-    P.ramp_r0 = c.ramp_radius / c.domain_L;
-    P.rho1 = c.rho0[0] / 1000.0;
-    P.rho2 = c.rho0[1] / 1000.0;
+    params_constants(b->solver, b->nb, P);
 }
 
 // Stage-kernel table with only the groups in `mask`: same pointers and sample
@@ -632,36 +585,9 @@ extern "C" int ofm_batch_qoi(ofm_batch* b) {
         for (int i = 0; i < gh.M; ++i, ++slot) {
             const DevQoi& d = q[slot];
             if (d.status) any_bad = 1;
-            if (gh.qoi_out) {
-                ofm_qoi& o = gh.qoi_out[i];
-                std::memset(&o, 0, sizeof(o));
-                o.p_peak = d.p_peak * s->p_ref;
-                o.peak_index = d.peak_index;
-                const long long k = d.peak_index;
-                const double h = 1.0 / N;
-                o.p_peak_xyz[0] = ((k % N) + 0.5) * h * s->L;
-                o.p_peak_xyz[1] = (((k / N) % N) + 0.5) * h * s->L;
-                o.p_peak_xyz[2] = ((k / ((long long)N * N)) + 0.5) * h * s->L;
-                const double cx = 0.5 * s->L;
-                o.p_peak_dist = std::sqrt((o.p_peak_xyz[0] - cx) * (o.p_peak_xyz[0] - cx) +
-                                          (o.p_peak_xyz[1] - cx) * (o.p_peak_xyz[1] - cx) +
-                                          (o.p_peak_xyz[2] - cx) * (o.p_peak_xyz[2] - cx));
-                o.p_peak_t = d.p_peak_t * s->t_ref;
-                for (int k2 = 0; k2 < c.n_sensors; ++k2) o.sensor_peak[k2] = d.sensor_peak[k2] * s->p_ref;
-                o.c_max = d.c_max * s->u_ref;
-                for (int k2 = 0; k2 < c.n_sensors; ++k2) {
-                    o.sensor_alpha0[k2] = d.sensor_alpha0[k2];
-                    o.sensor_alpha_min[k2] = d.sensor_alpha_min[k2];
-                    o.sensor_alpha_min_t[k2] = d.sensor_alpha_min_t[k2] * s->t_ref;
-                }
-                for (int v = 0; v < 6; ++v) {
-                    o.totals0[v] = d.totals0[v];
-                    o.totals_end[v] = d.totals_end[v];
-                }
-                o.t_final = (done[slot] ? d.t_final : tt[slot]) * s->t_ref;
-                o.n_steps = done[slot] ? d.n_steps : nsteps[slot];
-                o.status = d.status;
-            }
+            if (gh.qoi_out)
+                qoi_to_si(s, N, d, done[slot] ? d.t_final : tt[slot], done[slot] ? d.n_steps : nsteps[slot],
+                          gh.qoi_out[i]);
             if (gh.hist_out && hist_n) {
                 const size_t per = (size_t)c.n_sensors * c.n_out_times;
                 for (size_t a = 0; a < per; ++a) gh.hist_out[(size_t)i * per + a] = hist[(size_t)slot * per + a] * s->p_ref;

@@ -14,7 +14,10 @@
 // Set-up: the first call on a device, with that device current, looks up the
 // array's device address with cudaGetSymbolAddress (host code cannot use the
 // array's name as a device address) and caches it for the device.  Make that
-// first call before any stream capture.
+// first call before any stream capture.  The cached address assumes the
+// device's primary context lives as long as the process: after
+// cudaDeviceReset the module is loaded again and the array may move, so a
+// process that resets a device must not call this entry point afterwards.
 //
 // Every call shares the one array: calls that overlap on the GPU (on
 // different streams or host threads) race on it.  Each call re-initialises
@@ -27,6 +30,7 @@
 #include <mutex>
 #include <vector>
 
+#include "host_shared.cuh"
 #include "internal.h"
 #include "ofmlmc.h"
 #include "types.cuh"
@@ -104,7 +108,6 @@ void static_params(const ofm_solver* s, int N, int M, int nb, unsigned char* ws,
                    const int* sens_off, Params<T>& P) {
     std::memset(&P, 0, sizeof(P));
     const ofm_solver_config& c = s->cfg;
-    const double pref = s->p_ref;
     P.n_groups = 1;
     GroupDev& G = P.g[0];
     G.N = N;
@@ -134,36 +137,7 @@ void static_params(const ofm_solver* s, int N, int M, int nb, unsigned char* ws,
     P.s.n_active = (int*)(ws + L.active);
     P.s.g_active = (int*)(ws + L.gact);
     P.s.bubbles = (const double*)(ws + L.bub);
-    const double g1 = c.gamma[0], g2 = c.gamma[1];
-    const double pc1 = c.pc[0] / pref, pc2 = c.pc[1] / pref;
-    P.eos.g1 = (T)g1;
-    P.eos.g2 = (T)g2;
-    P.eos.pc1 = (T)pc1;
-    P.eos.pc2 = (T)pc2;
-    P.eos.gi1 = (T)(1.0 / (g1 - 1.0));
-    P.eos.gi2 = (T)(1.0 / (g2 - 1.0));
-    P.eos.pi1 = (T)(g1 * pc1 / (g1 - 1.0));
-    P.eos.pi2 = (T)(g2 * pc2 / (g2 - 1.0));
-    P.eos.eps = (T)c.weno_eps;
-    for (int k = 0; k < 3; ++k) {
-        P.rkA[k] = RK_A[k];
-        P.rkB[k] = RK_B[k];
-    }
-    P.bc = c.bc;
-    P.bc_penalty = c.bc_penalty;
-    P.weno_order = c.weno_order == 3 ? 3 : 5;
-    P.nb = nb;
-    P.n_sens = c.n_sensors;
-    P.n_out = c.n_out_times;
-    P.max_steps = c.max_steps;
-    P.t_end = c.t_end / s->t_ref;
-    P.cfl = c.cfl;
-    P.p_gas = c.p_gas / pref;
-    P.p_liq = c.p_liq / pref;
-    P.p_cloud = c.p_cloud / pref;
-    P.ramp_r0 = c.ramp_radius / c.domain_L;
-    P.rho1 = c.rho0[0] / 1000.0;
-    P.rho2 = c.rho0[1] / 1000.0;
+    params_constants(s, nb, P);
 }
 
 #define STATIC_TRY(call)                                                                   \
@@ -210,23 +184,10 @@ extern "C" int ofm_solve_level_static(const ofm_solver* s, const ofm_cloud_param
     const ofm_solver_config& c = s->cfg;
     const int nb = cloud->n_bubbles;
 
-    // sensor membership: cell centres within max(r, h) of the sensor centre
-    const double h = 1.0 / N;
+    // sensor membership: the same cells as the batch API's
     std::vector<int> cells;
     int sens_off[OFM_MAX_SENSORS + 1];
-    sens_off[0] = 0;
-    for (int k = 0; k < c.n_sensors; ++k) {
-        const double cx = c.sensors[k][0] / s->L, cy = c.sensors[k][1] / s->L;
-        const double cz = c.sensors[k][2] / s->L, r = c.sensors[k][3] / s->L;
-        const double R = r > h ? r : h;
-        for (int z = 0; z < N; ++z)
-            for (int y = 0; y < N; ++y)
-                for (int x = 0; x < N; ++x) {
-                    const double dx = (x + 0.5) * h - cx, dy = (y + 0.5) * h - cy, dz = (z + 0.5) * h - cz;
-                    if (dx * dx + dy * dy + dz * dz <= R * R) cells.push_back((z * N + y) * N + x);
-                }
-        sens_off[k + 1] = (int)cells.size();
-    }
+    sensor_cell_list(s, N, cells, sens_off);
 
     const StaticLayout L = static_layout(s, N, n, nb, cells.size());
     if (L.total > OFM_STATIC_SCRATCH_BYTES)
@@ -270,33 +231,7 @@ extern "C" int ofm_solve_level_static(const ofm_solver* s, const ofm_cloud_param
     int any_bad = 0;
     for (int i = 0; i < n; ++i) {
         const DevQoi& d = q[i];
-        ofm_qoi& o = out[i];
-        std::memset(&o, 0, sizeof(o));
-        o.p_peak = d.p_peak * s->p_ref;
-        o.peak_index = d.peak_index;
-        const long long k = d.peak_index;
-        o.p_peak_xyz[0] = ((k % N) + 0.5) * h * s->L;
-        o.p_peak_xyz[1] = (((k / N) % N) + 0.5) * h * s->L;
-        o.p_peak_xyz[2] = ((k / ((long long)N * N)) + 0.5) * h * s->L;
-        const double cx = 0.5 * s->L;
-        o.p_peak_dist = std::sqrt((o.p_peak_xyz[0] - cx) * (o.p_peak_xyz[0] - cx) +
-                                  (o.p_peak_xyz[1] - cx) * (o.p_peak_xyz[1] - cx) +
-                                  (o.p_peak_xyz[2] - cx) * (o.p_peak_xyz[2] - cx));
-        o.p_peak_t = d.p_peak_t * s->t_ref;
-        for (int k2 = 0; k2 < c.n_sensors; ++k2) o.sensor_peak[k2] = d.sensor_peak[k2] * s->p_ref;
-        o.c_max = d.c_max * s->u_ref;
-        for (int k2 = 0; k2 < c.n_sensors; ++k2) {
-            o.sensor_alpha0[k2] = d.sensor_alpha0[k2];
-            o.sensor_alpha_min[k2] = d.sensor_alpha_min[k2];
-            o.sensor_alpha_min_t[k2] = d.sensor_alpha_min_t[k2] * s->t_ref;
-        }
-        for (int v = 0; v < 6; ++v) {
-            o.totals0[v] = d.totals0[v];
-            o.totals_end[v] = d.totals_end[v];
-        }
-        o.t_final = d.t_final * s->t_ref;
-        o.n_steps = d.n_steps;
-        o.status = d.status;
+        qoi_to_si(s, N, d, d.t_final, d.n_steps, out[i]);
         if (d.status) any_bad = 1;
         if (sensor_hist && per)
             for (size_t a = 0; a < per; ++a) sensor_hist[(size_t)i * per + a] = hist[(size_t)i * per + a] * s->p_ref;

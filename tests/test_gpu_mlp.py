@@ -6,6 +6,17 @@ FP64, the GPU differs only by FP32 accumulation (~1e-6) and by rare one-ulp
 flips where an FP32 activation sits on a BF16 rounding boundary: relative L2
 <= 2e-3 for outputs and gradients.  Against the plain FP64 oracle (no BF16),
 each of the four GEMM layers adds ~2u of relative noise: <= 3e-2.
+
+Element by element (each element against |its reference| plus 1e-2 of the
+largest reference element): without flips the error is FP32 accumulation,
+~1e-7 (measured 1.7e-7 to 7.5e-6 on the narrow networks).  A flip moves one
+operand by one BF16 ulp (<= 2^-8 of it); in a weight gradient that changes
+the column it feeds by ~2^-8/sqrt(rows) of its size, ~3e-4 on 130 rows, and
+more on elements near zero, which the floor judges on the layer's scale:
+measured 4.2e-3 (outputs) and 4.3e-2 (first-layer weight gradient) on the
+200 -> 256 x 3 network.  Bounds: 2e-2 for outputs, 0.15 for gradients, and
+relative L2 per row and per column of every weight gradient <= 1e-2 (a wrong
+row or column gives ~1 there).
 """
 import math
 
@@ -22,6 +33,10 @@ pytestmark = pytest.mark.gpu
 
 from paper_1705_04374_gb300 import surrogate as S  # noqa: E402
 
+ELEM_FWD = 2e-2
+ELEM_GRAD = 0.15
+ROWCOL_GRAD = 1e-2
+
 
 @pytest.fixture(scope="module", autouse=True)
 def _cuda():
@@ -37,6 +52,14 @@ def init_params(rng, sizes):
 
 def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, float) - np.asarray(b, float)) / max(np.linalg.norm(b), 1e-300))
+
+
+def rel_elem(a, b, floor=1e-2):
+    """Largest element-wise error, each relative to its reference element
+    plus a floor of `floor` times the largest reference magnitude (so that
+    elements near zero are judged on the vector's scale)."""
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return float(np.max(np.abs(a - b) / (np.abs(b) + floor * max(np.max(np.abs(b)), 1e-300))))
 
 
 def setup_net(d_in, hidden, n_hidden, d_out, rows, seed=0, max_rows=None):
@@ -62,6 +85,9 @@ def test_forward_matches_oracle(shape):
     y_fp64, _ = omlp.forward(P, Xd)
     assert rel_l2(Y, y_lowp) < 2e-3
     assert rel_l2(Y, y_fp64) < 3e-2
+    e = rel_elem(Y, y_lowp)
+    print(f"\nforward {shape}: element-wise error vs the BF16-operand oracle {e:.2e}")
+    assert e < ELEM_FWD
     net.close()
 
 
@@ -91,8 +117,16 @@ def test_gradients_match_oracle(shape):
         assert rel_l2(g, gref) < tol, (lowp, rel_l2(g, gref))
         # and layer by layer
         ggpu = omlp.unflatten(g.astype(np.float64), sizes)
-        for (gw, gb), (rw, rb) in zip(ggpu, G):
+        for li, ((gw, gb), (rw, rb)) in enumerate(zip(ggpu, G)):
             assert rel_l2(gw, rw) < tol and rel_l2(gb, rb) < tol
+            if lowp:   # element by element, and row by row / column by column, against the BF16-operand oracle
+                ew, eb = rel_elem(gw, rw), rel_elem(gb, rb)
+                er = max(rel_l2(gw[i], rw[i]) for i in range(rw.shape[0]))
+                ec = max(rel_l2(gw[:, j], rw[:, j]) for j in range(rw.shape[1]))
+                print(f"\ngradients {shape} layer {li}: element-wise error W {ew:.2e} b {eb:.2e}, "
+                      f"worst row {er:.2e}, worst column {ec:.2e}")
+                assert ew < ELEM_GRAD and eb < ELEM_GRAD
+                assert er < ROWCOL_GRAD and ec < ROWCOL_GRAD
         assert abs(loss - omlp.mse_loss(y, Td)) < tol * omlp.mse_loss(y, Td)
     net.close()
 

@@ -3,14 +3,18 @@
 Tolerances: FP64 path, relative L1 per variable <= 1e-12 after one step and
 relative QoI error <= 1e-9 at t_end, on the same seeded clouds.
 
-FP32 stencil path: relative L1 <= 1e-3 after one step.  Derivation: a face
-flux carries HLLC star terms of size |s| ~ c ~ 29 (non-dimensional) times
-O(1) states, so FP32 rounding (6e-8) leaves ~2e-6 absolute noise per face,
-while one step from rest gives momenta of only ~dt |grad p| (the L1 mean of
-|grad p| over the box is ~1e-3 of p), i.e. up to ~1e-3 relative in the
-momenta; masses, energy and alpha2 stay near 1e-7.  QoI errors at t_end are
-measured and bounded loosely (the FP32 pressure loses about two digits to
-the cancellation E - rho|u|^2/2 - Pi with Pi/p ~ 40 in the liquid).
+FP32 stencil path, one step, relative L1 per variable (TOL_STEP_FP32).
+The state is stored in FP32, so each cell carries a rounding error of about
+6e-8 of its own value; a step moves the masses, the energy and alpha2 by a
+small fraction of themselves, so their relative L1 stays within a few ulps:
+measured <= 1.9e-7 (alpha2 rho2, 64^3), 4.4e-8 (E), 3e-7 (alpha2) over the
+one-step cases here; bounds 1e-6, 1e-6, 5e-7 and 3e-6.  The momenta start
+from zero: one step gives them ~dt |grad p|, while every face flux carries
+absolute FP32 noise of ~6e-8 times its star-state terms (|s| ~ c ~ 29
+non-dimensional, O(1) states), so their relative L1 is ~1e-3 at the
+smallest grids and falls as the momenta grow: measured <= 7.1e-4; bound 2e-3.
+QoI errors at t_end are bounded at about ten times the measured errors
+(test_fp32_qoi_errors_are_small_and_stated).
 """
 import os
 from concurrent.futures import ThreadPoolExecutor
@@ -31,7 +35,11 @@ from paper_1705_04374_gb300 import native as nv  # noqa: E402
 THREADS = max(1, min(32, os.cpu_count() or 1))
 TOL_STEP_FP64 = 1e-12
 TOL_QOI_FP64 = 1e-9
-TOL_STEP_FP32 = 1e-3
+# per variable: a1r1, a2r2, rho u, rho v, rho w, E, alpha2
+TOL_STEP_FP32 = np.array([1e-6, 1e-6, 2e-3, 2e-3, 2e-3, 5e-7, 3e-6])
+# whole runs of FP32 with different multiply-add contraction (the two stage-kernel
+# variants): round-off of the one-step size, accumulated over the run
+TOL_RUN_FP32 = 1e-3
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -123,6 +131,46 @@ def test_one_step_fp64_periodic_smooth_field():
     b.close()
 
 
+def sharp_cube_state(sp, N, width=3, p_gas=0.01):
+    """A sharp cube of width^3 gas cells (alpha2 = 1 - 1e-6, p = 0.01 p_liq) in
+    liquid at p_liq, at rest: WENO5 overshoots at the cube's faces, so face
+    states fail the admissibility test (alpha2 outside [0, 1], a negative
+    partial density or pressure) by wide margins and fall back to their cells."""
+    g = osolver.grid_from_params(sp, N)
+    a2 = np.full((N, N, N), 1e-6)
+    lo = N // 2 - width // 2
+    a2[lo:lo + width, lo:lo + width, lo:lo + width] = 1.0 - 1e-6
+    Wp = np.zeros((7, N, N, N))
+    Wp[0] = 1.0 - a2
+    Wp[1] = a2 * (sp.rho0[1] / sp.rho0[0])
+    Wp[5] = np.where(a2 > 0.5, p_gas, 1.0)
+    Wp[6] = a2
+    return g, osolver.prim_to_cons(g, Wp.reshape(7, -1)).reshape(7, N, N, N)
+
+
+@pytest.mark.parametrize("precision,variant", [("fp64", 0), ("fp64", 1), ("fp32", 0), ("fp32", 1)])
+def test_one_step_positivity_fallback(precision, variant):
+    """The face-state fallback (reading of Sec. 2.2's silence on positivity)
+    in both stage-kernel variants: the oracle counts > 0 fallbacks in the
+    step, and the GPU state matches it."""
+    N = 16
+    sp = W.tiny(N, 4).solver
+    g, Q0 = sharp_cube_state(sp, N)
+    s, groups, b = gpu_batch(sp, precision, [(N, [0])], W.cloud_uniform(1))
+    b.set_variant(variant)
+    b.init()
+    b.set_state(0, 0, Q0)
+    b.run(1)
+    dt = sp.cfl * g.h / osolver.max_speed(g, Q0)
+    osolver.fallback_reset()
+    ref = osolver.rk3_step(g, Q0, dt)
+    assert osolver.fallback_count() > 0
+    tol = TOL_STEP_FP64 if precision == "fp64" else TOL_STEP_FP32
+    r = rel_l1(b.state(0, 0), ref)
+    assert np.all(r <= tol), r
+    b.close()
+
+
 @pytest.mark.parametrize("precision,tol,kappa,variant", [("fp64", TOL_STEP_FP64, 1.0, 0),
                                                           ("fp64", TOL_STEP_FP64, 0.5, 1),
                                                           ("fp32", TOL_STEP_FP32, 1.0, 0),
@@ -147,7 +195,7 @@ def test_one_step_characteristic_boundary(precision, tol, kappa, variant):
         got = b.state(0, i)
         assert np.all(rel_l1(got, ref) <= tol), (sid, rel_l1(got, ref))
         trans = oracle_one_step(replace(sp, bc=nv.OFM_BC_TRANSMISSIVE), N, bub)
-        assert np.max(rel_l1(got, trans)) > 100 * tol   # the boundary did act
+        assert np.any(rel_l1(got, trans) > 100 * tol)   # the boundary did act
     b.close()
 
 
@@ -168,7 +216,7 @@ def test_one_step_weno3(precision, tol, variant, N):
         got = b.state(0, i)
         assert np.all(rel_l1(got, ref) <= tol), (sid, rel_l1(got, ref))
         ref5 = oracle_one_step(W.with_solver(w, weno_order=5).solver, N, bub)
-        assert np.max(rel_l1(got, ref5)) > 100 * tol   # the third-order path did run
+        assert np.any(rel_l1(got, ref5) > 100 * tol)   # the third-order path did run
     b.close()
 
 
@@ -305,12 +353,17 @@ def test_fp32_qoi_errors_are_small_and_stated(capsys):
     with capsys.disabled():
         print("\nFP32 vs FP64 oracle, relative QoI errors (32^3, 4 bubbles):",
               {k: f"{max(v):.2e}" for k, v in errs.items()})
-    assert max(errs["p_peak"]) < 1e-3
-    assert max(errs["sensor_peak"]) < 1e-2
-    assert max(errs["hist"]) < 1e-2
-    assert max(errs["c_max"]) < 1e-3
-    assert max(errs["alpha_min"]) < 1e-3
-    assert max(errs["alpha_hist"]) < 1e-3
+    # about ten times the errors measured on this case (p_peak 1.1e-5, sensor
+    # peaks 4.3e-6, pressure histories 3.2e-5, c_max 5.2e-7, gas-fraction minima
+    # 1.4e-8, gas-fraction histories 1.4e-4 of their maximum): the FP32 pressure
+    # loses about two digits to E - rho|u|^2/2 - Pi (Pi/p ~ 40 in the liquid),
+    # ~2e-6 per step, accumulated over ~60 steps
+    assert max(errs["p_peak"]) < 1e-4
+    assert max(errs["sensor_peak"]) < 5e-5
+    assert max(errs["hist"]) < 3e-4
+    assert max(errs["c_max"]) < 5e-6
+    assert max(errs["alpha_min"]) < 2e-7
+    assert max(errs["alpha_hist"]) < 1.5e-3
     b.close()
 
 
@@ -447,6 +500,27 @@ def test_full_size_ensemble_one_step_sampled(precision, tol):
     b.close()
 
 
+def test_full_size_clouds_fp64_qois_at_t_end_sampled():
+    """Three clouds of the 64^3 ensemble workload (20 bubbles, 8 sensors) in
+    FP64 to t_end (~120 steps): every QoI within 1e-9 of the oracle's."""
+    w = W.cfg2("fp64")
+    sp = w.solver
+    picks = [0, 257, 511]
+    s, groups, b = gpu_batch(sp, "fp64", [(64, picks)], w.cloud)
+    b.init()
+    while b.run(64) > 0:
+        pass
+    b.qoi()
+    ns = len(sp.sensors)
+    got = groups[0].qoi_dicts(ns)
+    ref = oracle_qois(sp, 64, w.cloud, picks)
+    for i in range(len(picks)):
+        compare_qoi(got[i], groups[0].hist[i], ref[i][0], ref[i][1], TOL_QOI_FP64, ns,
+                    ag=groups[0].alpha_hist[i])
+        assert got[i]["peak_index"] == ref[i][0]["peak_index"]
+    b.close()
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_stage_kernel_variants_are_bitwise_identical(precision):
     """One block per tile, persistent blocks and the autotuned choice give the
@@ -475,8 +549,8 @@ def test_stage_kernel_variants_are_bitwise_identical(precision):
             if precision == "fp64":
                 assert np.array_equal(a, c)
             else:   # FP32: the two kernels may fuse multiply-adds differently; the
-                #        round-off grows over the run like the FP32 one-step bound
-                assert np.all(rel_l1(a, c.astype(np.float64)) <= TOL_STEP_FP32)
+                #        round-off grows over the run
+                assert np.all(rel_l1(a, c.astype(np.float64)) <= TOL_RUN_FP32)
         for ga, gc in zip(q, res[0][1]):
             for a, c in zip(ga, gc):
                 assert a["n_steps"] == c["n_steps"]
@@ -484,4 +558,4 @@ def test_stage_kernel_variants_are_bitwise_identical(precision):
                     assert a["p_peak"] == c["p_peak"]
                     assert np.array_equal(a["totals_end"], c["totals_end"])
                 else:
-                    assert abs(a["p_peak"] - c["p_peak"]) <= 1e-3 * c["p_peak"]   # the FP32 QoI bound
+                    assert abs(a["p_peak"] - c["p_peak"]) <= TOL_RUN_FP32 * c["p_peak"]
