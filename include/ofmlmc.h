@@ -256,11 +256,14 @@ int ofm_solve_level(ofm_solver* solver, const ofm_cloud_params* cloud, int N, in
  * clouds from `cloud`) and outputs (`out`, `sensor_hist`, as in
  * ofm_solve_level) are host arrays owned by the caller.
  *   - Sizes whose scratch would exceed the array are rejected with
- *     OFM_ENOMEM and a message giving the bytes needed (for example one FP32
- *     sample on 64^3 fits; 512 do not).
+ *     OFM_ENOMEM and a message giving the bytes needed.  Each sample takes
+ *     three state buffers of 7 N^3 values: up to 12 FP32 or 6 FP64 samples on
+ *     32^3 fit, one FP32 sample on 64^3, no FP64 sample on 64^3.
  *   - The first call on a device, with that device current, looks up the
  *     array's device address (cudaGetSymbolAddress) and caches it; make that
- *     first call before any stream capture.
+ *     first call before any stream capture.  The cache assumes the device's
+ *     primary context is never reset: after cudaDeviceReset the array may
+ *     move, so do not call this entry point again in that process.
  *   - Every call uses the same array and re-initialises what it reads; calls
  *     that overlap on the GPU (other streams or host threads) race on it.
  *   - Synchronises `stream` before returning.
@@ -397,6 +400,26 @@ typedef struct {
     int fit_variances;         /* 1: step 3's variance fit (ofm_estimate_fitted) in every
                                   iteration; with L >= 3 the finest level keeps the single
                                   warm-up pair of Eq. (warmup) (L < 2 is refused) */
+    /* Learned surrogate of q_L as an extra control variate of the top level term
+     * (not in the paper; see ofm_estimate_surrogate).  Once level L has
+     * surrogate_min_pairs usable pairs, every iteration trains two MLPs
+     * (surrogate_hidden x 3 GELU layers, BF16 operands, FP32 accumulation,
+     * Adam at surrogate_lr, up to surrogate_steps steps with the parameters of
+     * the lowest error on a fifth of the fold held out) on the two halves of
+     * the level-L pairs (input: the surrogate_nearest bubbles nearest the domain
+     * centre, ofm_cloud_features, and the pair's q_{L-1}; target: q_L), predicts
+     * each pair with the network of the other half (cross-fitting) and the
+     * level-(L-1) pairs' fine members with both, and estimates with
+     * ofm_estimate_surrogate; step 7 then takes the modified variances.  Its
+     * device time counts in gpu_seconds.  Needs L >= 1 and no variance fit. */
+    int surrogate;             /* 1: on */
+    int surrogate_min_pairs;   /* 0: 64 */
+    int surrogate_nearest;     /* bubbles per cloud in the input (0: all) */
+    int surrogate_steps;       /* 0: 600 */
+    int surrogate_hidden;      /* 0: 256 */
+    double surrogate_lr;       /* 0: 1e-3 */
+    double* surrogate_h_out;   /* optional host array (one per returned pair, in pairs_out
+                                  order): the prediction used for that pair, NaN where none */
 } ofm_run_config;
 
 typedef struct {
@@ -408,6 +431,11 @@ typedef struct {
     int64_t failed;              /* pairs excluded */
     int capped;                  /* 1 if max_cell_steps stopped the loop */
     ofm_estimate_out est;        /* final estimator, Eqs. (ocv-mlmc), (ocv-mlmc-err) */
+    int surrogate_used;          /* 1 if the final estimator has the surrogate control variate */
+    double beta;                 /* its coefficient (0 without) */
+    double surrogate_seconds;    /* device time of its training and inference (in gpu_seconds) */
+    double eps2_plain;           /* eps^2 of the plain estimator on the final pairs */
+    double sigma_tilde2_plain[OFM_MAX_LEVELS];  /* and its level variances */
 } ofm_run_result;
 
 int ofm_run(ofm_solver* solver, const ofm_cloud_params* cloud, const ofm_run_config* config, double* pairs_out,
@@ -433,8 +461,62 @@ int ofm_probe_fma_tflops(int precision, double* tflops, void* stream);
  * any fixed beta, so a poor surrogate costs variance, never bias.
  * Host FP64; arrays are host pointers; M >= 2, N >= 1.
  * ------------------------------------------------------------------------- */
+/* ---------------------------------------------------------------------------
+ * OF-MLMC with the surrogate as an extra control variate of the top level
+ * term, inside the estimator (not in the paper; it extends Eq. (ocv-mlmc) of
+ * Section 2.4.2 by one coefficient).  The surrogate h predicts q_L from a
+ * cloud and its q_{L-1}; the control variate is its prediction of the top
+ * level term, g = h - alpha_{L-1} q_{L-1}.  Its mean is estimated on the fine
+ * members of the level-(L-1) pairs, whose q_{L-1} is computed anyway:
+ *   level L-1 terms: alpha_{L-1} q_{L-1} - alpha_{L-2} q_{L-2} + beta g(h_extra)
+ *   level L terms:   q_L - alpha_{L-1} q_{L-1} - beta g(h_top)
+ * The estimate is unbiased for any fixed alpha and beta (h must not have been
+ * trained on the pairs it is evaluated on: cross-fitting), every level stays
+ * a mean over its own pairs, so eps2 = sum sigma_tilde2/M and the sample
+ * numbers of step 7 (ofm_optimal_samples) apply to the modified variances.
+ *   L >= 1; M, q, W as in ofm_estimate (host arrays);
+ *   h_top: M[L] predictions on the level-L pairs' inputs (cloud, coarse member);
+ *   h_extra: M[L-1] predictions on the level-(L-1) pairs' inputs (cloud, fine member);
+ *   beta_in: NaN for the coefficient that minimises eps2 at the current M,
+ *            (Cov_L(D_L, g)/M_L - Cov_{L-1}(D_{L-1}, g)/M_{L-1})
+ *            / (V_{L-1}[g]/M_{L-1} + V_L[g]/M_L), 0 when g does not vary;
+ *            else that fixed beta;
+ *   out: alpha, sigma2, cov as in ofm_estimate; sigma_tilde2, mean, eps2 of the
+ *        corrected estimator; beta_out: the coefficient used;
+ *   sigma_tilde2_plain (may be NULL): L+1 variances of the plain estimator.
+ * Errors: OFM_EINVAL (bad sizes, fewer than 2 pairs on a level).
+ * ------------------------------------------------------------------------- */
+int ofm_estimate_surrogate(int L, const int64_t* M, const double* const* q, const double* W,
+                           const double* h_top, const double* h_extra, double beta_in,
+                           ofm_estimate_out* out, double* beta_out, double* sigma_tilde2_plain);
+
 int ofm_surrogate_cv(const double* D, const double* s_paired, int64_t M, const double* s_extra, int64_t N,
                      double* beta, double* corrected_mean, double* variance);
+
+/* ---------------------------------------------------------------------------
+ * Level-wise kernel density estimate of a QoI (Section 3.2, which estimates
+ * the PDFs of its QoIs with level-dependent kernel density estimators whose
+ * bandwidth comes from the "solve-the-equation" method of Sheather and Jones,
+ * 1991).  Host FP64.
+ *   ofm_sj_bandwidth: the solve-the-equation bandwidth of a Gaussian-kernel
+ *     KDE of x[n] (n >= 2): h = [R(K)/(n psi_4(g(h)))]^(1/5), psi_r estimated
+ *     by sum_{i != j} phi^(r)((x_i - x_j)/g)/(n (n-1) g^(r+1)), the pilot g(h)
+ *     from normal-reference pilots (scale min(sd, IQR/1.349); a pilot estimate
+ *     of the wrong sign, psi_4 <= 0 or psi_6 >= 0, takes its normal-reference
+ *     value), the root by bisection to 1e-10 relative; 0 for a sample without
+ *     spread.  O(n^2) per evaluation.
+ *   ofm_level_kde: density[k] at x[k] of
+ *     f(x) = sum_l (1/M_l) sum_i [alpha_l K_b(x - q_l^i) - alpha_{l-1} K_b(x - q_{l-1}^i)],
+ *     K_b the Gaussian kernel, b = b_l the larger of the solve-the-equation
+ *     bandwidths of level l's fine and coarse members (bandwidth[l], may be
+ *     NULL); pairs q and M as in ofm_estimate, alpha e.g. ofm_estimate's.
+ *     It integrates to alpha_L = 1, its first moment is Eq. (ocv-mlmc)'s mean.
+ *   Errors: OFM_EINVAL (fewer than 2 pairs on a level), OFM_ENUMERIC (a level
+ *   without spread).
+ * ------------------------------------------------------------------------- */
+int ofm_sj_bandwidth(const double* x, int64_t n, double* h);
+int ofm_level_kde(int L, const int64_t* M, const double* const* q, const double* alpha, const double* x,
+                  int64_t n_x, double* density, double* bandwidth);
 
 /* ---------------------------------------------------------------------------
  * MLP (the surrogate network): d_in -> hidden (x n_hidden, exact-erf GELU) ->

@@ -11,7 +11,9 @@ Plain numpy in FP64, following Section 2.4 of the paper:
   - warm-up sample numbers, Eq. (warmup);
   - the MC-equivalent cost, Eq. (speedup);
   - the same estimator from per-level summaries (counts, means, squared
-    deviations, fine/coarse co-deviation) that combine across processes.
+    deviations, fine/coarse co-deviation) that combine across processes;
+  - (not in the paper) a learned surrogate as an extra control variate of the
+    top level term with its own coefficient (estimate_surrogate).
 
 Input convention: ``pairs[l]`` is an (M_l, 2) array; column 0 holds q_l and
 column 1 holds q_{l-1} evaluated on the same random input (column 1 unused
@@ -417,3 +419,60 @@ def surrogate_cv(D_top: np.ndarray, s_paired: np.ndarray, s_extra: np.ndarray):
     var = (_var(D_top) - c * c / (vs * (1.0 + M / N))) / M if vs > 0 else _var(D_top) / M
     return dict(beta=beta, correction=float(corr), var=float(var),
                 mean=float(D_top.sum() / M + corr))
+
+
+def estimate_surrogate(pairs, W, h_top, h_extra, alpha=None, beta=None):
+    """OF-MLMC with a surrogate of q_L as an extra control variate (not in the paper).
+
+    h_top[i]: the surrogate's prediction of q_L on the input of level-L pair
+    i (its cloud and its coarse member q_{L-1}), from a network that was not
+    trained on pair i; h_extra[j]: the surrogate on the input of the fine
+    member of level-(L-1) pair j (its cloud and that q_{L-1}), with the
+    networks weighted so that h_extra and h_top have the same expectation
+    (both inputs are a random cloud and its q_{L-1}).  The control variate is
+    the surrogate's prediction of the top level term,
+        g = h - alpha_{L-1} q_{L-1},
+    and with the coefficients alpha of Eq. (alpha-matvec) (unless given) the
+    two top level terms become
+
+        level L-1:  alpha_{L-1} q_{L-1} - alpha_{L-2} q_{L-2} + beta g  (over the level-(L-1) pairs)
+        level L:    q_L - alpha_{L-1} q_{L-1} - beta g                  (over the level-L pairs)
+
+    Their expectations move by +beta E[g] and -beta E[g], so the estimator of
+    Eq. (ocv-mlmc) stays unbiased for any fixed alpha and beta; each level is
+    still a mean over its own independent pairs, so Eq. (ocv-mlmc-err) and
+    the sample numbers of step 7 apply to the modified sigma~^2_l.  Unless
+    given, beta minimises eps^2 = sum_l sigma~^2_l / M_l at the current M_l:
+
+        beta = (Cov_L(D_L, g)/M_L - Cov_{L-1}(D_{L-1}, g)/M_{L-1})
+               / (V_{L-1}[g]/M_{L-1} + V_L[g]/M_L)
+
+    (D_l the plain level terms; beta = 0 when g does not vary).  Needs L >= 1.
+    """
+    L = len(pairs) - 1
+    if L < 1:
+        raise ValueError("the surrogate control variate needs L >= 1")
+    base = estimate(pairs, W)
+    alpha = base["alpha"] if alpha is None else np.asarray(alpha, dtype=np.float64)
+    h_top = np.asarray(h_top, dtype=np.float64)
+    h_extra = np.asarray(h_extra, dtype=np.float64)
+    M = [p.shape[0] for p in pairs]
+    if h_top.size != M[L] or h_extra.size != M[L - 1]:
+        raise ValueError("h_top needs one value per level-L pair, h_extra one per level-(L-1) pair")
+    D = [alpha[0] * pairs[0][:, 0]]
+    for l in range(1, L + 1):
+        D.append(alpha[l] * pairs[l][:, 0] - alpha[l - 1] * pairs[l][:, 1])
+    g_top = h_top - alpha[L - 1] * pairs[L][:, 1]
+    g_extra = h_extra - alpha[L - 1] * pairs[L - 1][:, 0]
+    if beta is None:
+        den = _var(g_extra) / M[L - 1] + _var(g_top) / M[L]
+        num = _cov(D[L], g_top) / M[L] - _cov(D[L - 1], g_extra) / M[L - 1]
+        beta = num / den if den > 0.0 else 0.0
+    Dm = list(D)
+    Dm[L - 1] = D[L - 1] + beta * g_extra
+    Dm[L] = D[L] - beta * g_top
+    st2 = np.array([_var(d) for d in Dm])
+    mean = float(sum(d.sum() / d.size for d in Dm))
+    st2_plain = sigma_tilde2(pairs, alpha)
+    return dict(alpha=alpha, beta=float(beta), sigma2=base["sigma2"], cov=base["cov"], sigma_tilde2=st2,
+                sigma_tilde2_plain=st2_plain, mean=mean, eps2=eps2(st2, M), eps2_plain=eps2(st2_plain, M), M=M)

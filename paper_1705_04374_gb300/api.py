@@ -261,6 +261,53 @@ def estimate(pairs: Sequence[np.ndarray], W: Sequence[float], fit: bool = False)
     return res
 
 
+def estimate_surrogate(pairs: Sequence[np.ndarray], W: Sequence[float], h_top, h_extra, beta=None) -> dict:
+    """ofm_estimate_surrogate: OF-MLMC with the surrogate's prediction of the top
+    level term as an extra control variate (beta None: the optimal one)."""
+    L = len(pairs) - 1
+    arrs = [np.ascontiguousarray(np.asarray(p, dtype=np.float64).reshape(-1, 2)) for p in pairs]
+    M = (C.c_int64 * (L + 1))(*[a.shape[0] for a in arrs])
+    ptrs = (C.POINTER(C.c_double) * (L + 1))(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs])
+    Wc = (C.c_double * (L + 1))(*W)
+    ht = np.ascontiguousarray(h_top, dtype=np.float64)
+    he = np.ascontiguousarray(h_extra, dtype=np.float64)
+    out = nv.ofm_estimate_out()
+    b = C.c_double()
+    plain = (C.c_double * (L + 1))()
+    nv.check(nv.lib().ofm_estimate_surrogate(L, M, ptrs, Wc, ht.ctypes.data_as(C.POINTER(C.c_double)),
+                                             he.ctypes.data_as(C.POINTER(C.c_double)),
+                                             float("nan") if beta is None else float(beta), C.byref(out),
+                                             C.byref(b), plain), "ofm_estimate_surrogate")
+    n = L + 1
+    return dict(alpha=np.array(out.alpha[:n]), sigma2=np.array(out.sigma2[:n]), cov=np.array(out.cov[:n]),
+                sigma_tilde2=np.array(out.sigma_tilde2[:n]), sigma_tilde2_plain=np.array(plain[:n]),
+                mean=out.mean, eps2=out.eps2, beta=b.value)
+
+
+def sj_bandwidth(x) -> float:
+    """ofm_sj_bandwidth: the solve-the-equation bandwidth of a Gaussian-kernel KDE."""
+    xs = np.ascontiguousarray(x, dtype=np.float64)
+    h = C.c_double()
+    nv.check(nv.lib().ofm_sj_bandwidth(xs.ctypes.data_as(C.POINTER(C.c_double)), xs.size, C.byref(h)),
+             "ofm_sj_bandwidth")
+    return h.value
+
+
+def level_kde(pairs: Sequence[np.ndarray], alpha, x):
+    """ofm_level_kde: the level-wise density of Sec. 3.2 on the points x; returns (density, bandwidths)."""
+    L = len(pairs) - 1
+    arrs = [np.ascontiguousarray(np.asarray(p, dtype=np.float64).reshape(-1, 2)) for p in pairs]
+    M = (C.c_int64 * (L + 1))(*[a.shape[0] for a in arrs])
+    ptrs = (C.POINTER(C.c_double) * (L + 1))(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs])
+    al = (C.c_double * (L + 1))(*alpha)
+    xs = np.ascontiguousarray(x, dtype=np.float64)
+    f = np.zeros_like(xs)
+    bw = (C.c_double * (L + 1))()
+    nv.check(nv.lib().ofm_level_kde(L, M, ptrs, al, xs.ctypes.data_as(C.POINTER(C.c_double)), xs.size,
+                                    f.ctypes.data_as(C.POINTER(C.c_double)), bw), "ofm_level_kde")
+    return f, np.array(bw[:L + 1])
+
+
 def fit_level_variances(V: Sequence[float], M: Sequence[int]):
     """ofm_fit_level_variances: (a, b, V_fit) of ln V_l = a + b l (V[0] ignored)."""
     L = len(V) - 1
@@ -341,9 +388,13 @@ def warmup_samples(W) -> np.ndarray:
 def run_ofmlmc(solver: Solver, cloud, levels, target: float, mode: str = "tol", qoi: int = 0,
                seed: int = 20170509, max_iterations: int = 10, min_samples: int = 2,
                max_batch_bytes: int = 0, capacity: int = 1 << 16, max_cell_steps: float = 0.0,
-               fit_variances: bool = False):
+               fit_variances: bool = False, surrogate: bool = False, surrogate_min_pairs: int = 0,
+               surrogate_nearest: int = 0, surrogate_steps: int = 0, surrogate_hidden: int = 0,
+               surrogate_lr: float = 0.0):
     """ofm_run: the adaptive OF-MLMC loop over GPU solves.  Returns (result dict, pairs per level, ids per level).
-    fit_variances: step 3's variance fit, and one warm-up pair on the finest of L >= 3 levels."""
+    fit_variances: step 3's variance fit, and one warm-up pair on the finest of L >= 3 levels.
+    surrogate: the learned surrogate of q_L as an extra control variate of the top level term
+    (the result then holds its predictions per pair under "h", NaN where none)."""
     cfg = nv.ofm_run_config()
     cfg.L = len(levels) - 1
     for i, n in enumerate(levels):
@@ -357,6 +408,14 @@ def run_ofmlmc(solver: Solver, cloud, levels, target: float, mode: str = "tol", 
     cfg.max_batch_bytes = max_batch_bytes
     cfg.max_cell_steps = max_cell_steps
     cfg.fit_variances = 1 if fit_variances else 0
+    cfg.surrogate = 1 if surrogate else 0
+    cfg.surrogate_min_pairs = surrogate_min_pairs
+    cfg.surrogate_nearest = surrogate_nearest
+    cfg.surrogate_steps = surrogate_steps
+    cfg.surrogate_hidden = surrogate_hidden
+    cfg.surrogate_lr = surrogate_lr
+    h = np.full(capacity, np.nan)
+    cfg.surrogate_h_out = h.ctypes.data_as(C.POINTER(C.c_double))
     cp = cloud_params(cloud)
     pairs = np.zeros((capacity, 2))
     ids = np.zeros(capacity, dtype=np.uint64)
@@ -366,15 +425,18 @@ def run_ofmlmc(solver: Solver, cloud, levels, target: float, mode: str = "tol", 
                               _torch_stream_ptr()), "ofm_run")
     L = cfg.L
     M = [res.M[l] for l in range(L + 1)]
-    per_pairs, per_ids, at = [], [], 0
+    per_pairs, per_ids, per_h, at = [], [], [], 0
     for l in range(L + 1):
         per_pairs.append(pairs[at:at + M[l]].copy())
         per_ids.append(ids[at:at + M[l]].copy())
+        per_h.append(h[at:at + M[l]].copy())
         at += M[l]
     n = L + 1
     est = dict(alpha=np.array(res.est.alpha[:n]), sigma2=np.array(res.est.sigma2[:n]),
                cov=np.array(res.est.cov[:n]), sigma_tilde2=np.array(res.est.sigma_tilde2[:n]),
                mean=res.est.mean, eps2=res.est.eps2)
     out = dict(iterations=res.iterations, M=M, W=[res.W[l] for l in range(n)], gpu_seconds=res.gpu_seconds,
-               cell_steps=res.cell_steps, failed=res.failed, capped=res.capped, est=est)
+               cell_steps=res.cell_steps, failed=res.failed, capped=res.capped, est=est,
+               surrogate_used=bool(res.surrogate_used), beta=res.beta, surrogate_seconds=res.surrogate_seconds,
+               eps2_plain=res.eps2_plain, sigma_tilde2_plain=np.array(res.sigma_tilde2_plain[:n]), h=per_h)
     return out, per_pairs, per_ids

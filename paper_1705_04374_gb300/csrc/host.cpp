@@ -453,6 +453,65 @@ extern "C" int ofm_optimal_samples(int L, const double* st2, const double* W, co
     }
 }
 
+// OF-MLMC with the surrogate of q_L as an extra control variate of the top
+// level term (not in the paper): g = h - alpha_{L-1} q_{L-1}, added with
+// coefficient beta to the level-(L-1) terms (h on their fine inputs) and
+// subtracted from the level-L terms (h on their coarse inputs).  Unbiased for
+// fixed alpha and beta; beta minimises sum_l sigma~^2_l / M_l.
+extern "C" int ofm_estimate_surrogate(int L, const int64_t* M, const double* const* q, const double* W,
+                                      const double* h_top, const double* h_extra, double beta_in,
+                                      ofm_estimate_out* out, double* beta_out, double* sigma_tilde2_plain) {
+    if (L < 1 || L >= OFM_MAX_LEVELS || !M || !q || !W || !h_top || !h_extra || !out || !beta_out)
+        return fail(OFM_EINVAL, "ofm_estimate_surrogate: bad arguments (needs L >= 1)");
+    int rc = estimate_core(L, M, q, W, out, false, nullptr);
+    if (rc != OFM_OK) return rc;
+    if (sigma_tilde2_plain)
+        for (int l = 0; l <= L; ++l) sigma_tilde2_plain[l] = out->sigma_tilde2[l];
+    const double* al = out->alpha;
+    auto term = [&](int l, int64_t i) {
+        return l == 0 ? al[0] * q[0][2 * i] : al[l] * q[l][2 * i] - al[l - 1] * q[l][2 * i + 1];
+    };
+    const int64_t ML = M[L], Mm = M[L - 1];
+    std::vector<double> DL(ML), gL(ML), Dm(Mm), gm(Mm);
+    for (int64_t i = 0; i < ML; ++i) {
+        DL[i] = term(L, i);
+        gL[i] = h_top[i] - al[L - 1] * q[L][2 * i + 1];
+    }
+    for (int64_t j = 0; j < Mm; ++j) {
+        Dm[j] = term(L - 1, j);
+        gm[j] = h_extra[j] - al[L - 1] * q[L - 1][2 * j];
+    }
+    double beta = beta_in;
+    if (std::isnan(beta_in)) {
+        const double den = var_of(gm) / (double)Mm + var_of(gL) / (double)ML;
+        const double num = cov_of(DL, gL) / (double)ML - cov_of(Dm, gm) / (double)Mm;
+        beta = den > 0.0 ? num / den : 0.0;
+    }
+    for (int64_t i = 0; i < ML; ++i) DL[i] -= beta * gL[i];
+    for (int64_t j = 0; j < Mm; ++j) Dm[j] += beta * gm[j];
+    out->sigma_tilde2[L] = var_of(DL);
+    out->sigma_tilde2[L - 1] = var_of(Dm);
+    double mean = 0.0, e2 = 0.0;
+    for (int l = 0; l <= L; ++l) {
+        double m;
+        if (l == L)
+            m = mean_of(DL);
+        else if (l == L - 1)
+            m = mean_of(Dm);
+        else {
+            std::vector<double> d(M[l]);
+            for (int64_t i = 0; i < M[l]; ++i) d[i] = term(l, i);
+            m = mean_of(d);
+        }
+        mean += m;
+        e2 += out->sigma_tilde2[l] / (double)M[l];
+    }
+    out->mean = mean;
+    out->eps2 = e2;
+    *beta_out = beta;
+    return OFM_OK;
+}
+
 extern "C" int ofm_surrogate_cv(const double* D, const double* s_paired, int64_t M, const double* s_extra, int64_t N,
                                 double* beta, double* corrected_mean, double* variance) {
     if (!D || !s_paired || !s_extra || M < 2 || N < 1 || !beta || !corrected_mean || !variance)
@@ -465,5 +524,119 @@ extern "C" int ofm_surrogate_cv(const double* D, const double* s_paired, int64_t
     *beta = b;
     *corrected_mean = mean_of(d) + b * (mean_of(se) - mean_of(sp));
     *variance = vs > 0.0 ? (var_of(d) - c * c / (vs * f)) / (double)M : var_of(d) / (double)M;
+    return OFM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Level-wise kernel density estimate (Section 3.2): the OF-MLMC estimator of
+// E[K_b(x - q)] with a Gaussian kernel, each level's pairs with one
+// bandwidth, the larger of its two members' solve-the-equation bandwidths
+// (Sheather and Jones 1991).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr double kSqrt2Pi = 2.5066282746310002;
+
+// r-th derivative (r = 4 or 6) of the standard normal density: phi(u) He_r(u).
+double phi_deriv(double u, int r) {
+    const double phi = std::exp(-0.5 * u * u) / kSqrt2Pi, u2 = u * u;
+    return r == 4 ? phi * (u2 * u2 - 6.0 * u2 + 3.0) : phi * (u2 * u2 * u2 - 15.0 * u2 * u2 + 45.0 * u2 - 15.0);
+}
+
+// psi_r = int f^(r) f estimated with bandwidth g, the pairs i = j left out.
+double psi_hat(const std::vector<double>& x, int r, double g) {
+    const size_t n = x.size();
+    double tot = 0.0;
+    for (size_t i = 0; i < n; ++i)
+        for (size_t j = i + 1; j < n; ++j) tot += phi_deriv((x[i] - x[j]) / g, r);
+    return 2.0 * tot / ((double)n * (double)(n - 1) * std::pow(g, (double)(r + 1)));
+}
+
+// Percentile with linear interpolation between order statistics.
+double percentile(std::vector<double> v, double p) {
+    std::sort(v.begin(), v.end());
+    const double pos = p / 100.0 * (double)(v.size() - 1);
+    const size_t lo = (size_t)std::floor(pos), hi = std::min(lo + 1, v.size() - 1);
+    return v[lo] + (pos - (double)lo) * (v[hi] - v[lo]);
+}
+
+double sj_bandwidth(const std::vector<double>& x) {
+    const double n = (double)x.size();
+    const double sd = std::sqrt(var_of(x));
+    const double iqr = (percentile(x, 75.0) - percentile(x, 25.0)) / 1.349;
+    const double s = iqr > 0.0 ? std::min(sd, iqr) : sd;
+    if (!(s > 0.0)) return 0.0;
+    const double rk = 1.0 / (2.0 * std::sqrt(M_PI)), k4 = 3.0 / kSqrt2Pi, k6 = -15.0 / kSqrt2Pi;
+    // normal-reference pilots for psi_4 and psi_6
+    const double psi6n = -15.0 / (16.0 * std::sqrt(M_PI) * std::pow(s, 7.0));
+    const double psi8n = 105.0 / (32.0 * std::sqrt(M_PI) * std::pow(s, 9.0));
+    const double a = std::pow(-2.0 * k4 / (psi6n * n), 1.0 / 7.0);
+    const double b = std::pow(-2.0 * k6 / (psi8n * n), 1.0 / 9.0);
+    // psi_4 > 0 > psi_6 for any smooth density; a pilot estimate of the wrong sign
+    // (possible for a small sample) takes its normal-reference value
+    double p4a = psi_hat(x, 4, a), p6b = psi_hat(x, 6, b);
+    if (!(p4a > 0.0)) p4a = 3.0 / (8.0 * std::sqrt(M_PI) * std::pow(s, 5.0));
+    if (!(p6b < 0.0)) p6b = psi6n;
+    const double c_g = std::pow(2.0 * k4 / rk * (p4a / -p6b), 1.0 / 7.0);
+    auto f = [&](double h) -> double {
+        const double p4 = psi_hat(x, 4, c_g * std::pow(h, 5.0 / 7.0));
+        if (!(p4 > 0.0)) return HUGE_VAL;   // the pilot resolves no curvature: h is too small
+        return std::pow(rk / (n * p4), 0.2) - h;
+    };
+    const double h0 = std::pow(4.0 / (3.0 * n), 0.2) * s;
+    double lo = h0, hi = h0;
+    for (int k = 0; k < 200 && f(hi) > 0.0; ++k) hi *= 2.0;
+    for (int k = 0; k < 200 && f(lo) < 0.0; ++k) lo *= 0.5;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (f(mid) > 0.0)
+            lo = mid;
+        else
+            hi = mid;
+        if (hi - lo <= 1e-10 * hi) break;
+    }
+    return 0.5 * (lo + hi);
+}
+
+}  // namespace
+
+extern "C" int ofm_sj_bandwidth(const double* x, int64_t n, double* h) {
+    if (!x || !h || n < 2) return fail(OFM_EINVAL, "ofm_sj_bandwidth: needs n >= 2 samples");
+    *h = sj_bandwidth(std::vector<double>(x, x + n));
+    return OFM_OK;
+}
+
+extern "C" int ofm_level_kde(int L, const int64_t* M, const double* const* q, const double* alpha, const double* x,
+                             int64_t n_x, double* density, double* bandwidth) {
+    if (L < 0 || L >= OFM_MAX_LEVELS || !M || !q || !alpha || !x || n_x < 0 || !density)
+        return fail(OFM_EINVAL, "ofm_level_kde: bad arguments");
+    for (int l = 0; l <= L; ++l)
+        if (M[l] < 2 || !q[l]) return fail(OFM_EINVAL, "ofm_level_kde: level %d needs >= 2 pairs", l);
+    for (int64_t k = 0; k < n_x; ++k) density[k] = 0.0;
+    for (int l = 0; l <= L; ++l) {
+        std::vector<double> fine(M[l]), coarse(M[l]);
+        for (int64_t i = 0; i < M[l]; ++i) {
+            fine[i] = q[l][2 * i];
+            coarse[i] = q[l][2 * i + 1];
+        }
+        double b = sj_bandwidth(fine);
+        if (l > 0) b = std::max(b, sj_bandwidth(coarse));
+        if (bandwidth) bandwidth[l] = b;
+        if (!(b > 0.0)) return fail(OFM_ENUMERIC, "ofm_level_kde: level %d has no spread", l);
+        const double wf = alpha[l] / ((double)M[l] * b * kSqrt2Pi);
+        const double wc = l > 0 ? alpha[l - 1] / ((double)M[l] * b * kSqrt2Pi) : 0.0;
+        for (int64_t k = 0; k < n_x; ++k) {
+            double sf = 0.0, sc = 0.0;
+            for (int64_t i = 0; i < M[l]; ++i) {
+                const double uf = (x[k] - fine[i]) / b;
+                sf += std::exp(-0.5 * uf * uf);
+                if (l > 0) {
+                    const double uc = (x[k] - coarse[i]) / b;
+                    sc += std::exp(-0.5 * uc * uc);
+                }
+            }
+            density[k] += wf * sf - wc * sc;
+        }
+    }
     return OFM_OK;
 }

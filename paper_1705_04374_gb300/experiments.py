@@ -267,9 +267,11 @@ def cmd_surrogate(quick):
     cv = S.surrogate_cv(D0, alpha[0] * s_pair, alpha[0] * s_extra)
     plain_var0 = np.var(D0, ddof=1) / len(D0)
     sur_seconds = t_train + t_inf0 + t_inf
-    # equal GPU-seconds: the plain estimator spends sur_seconds on more level-0 samples instead
+    # equal GPU-seconds: the surrogate estimator paid for all counts[0] level-0 solves
+    # (n_tr of them only train the network) plus training and inference; the plain
+    # estimator averages every one of those solves and spends sur_seconds on more
     extra_plain = sur_seconds / Wsec[0]
-    plain_var0_eq = np.var(D0, ddof=1) / (len(D0) + extra_plain)
+    plain_var0_eq = np.var(alpha[0] * q0, ddof=1) / (len(q0) + extra_plain)
     out["level0_geometry"] = dict(train_rows=n_tr, cv_rows=len(D0), nearest_bubbles=k0,
                                   corr=float(np.corrcoef(s_pair, q0[n_tr:])[0, 1]), beta=cv["beta"],
                                   var_plain=plain_var0, var_with_surrogate=cv["var"],
@@ -353,11 +355,14 @@ def cmd_rmse(quick):
             return float(np.sum(np.sqrt(st * Wsec32)) ** 2 / tau32 ** 2)
         st_sur = st2.copy()
         st_sur[0] *= ratio
+        # the surrogate's cost: training, inference and the n_tr level-0 solves that only train it
         out["fp32_surrogate"] = dict(level0_variance_ratio=ratio, corr=float(np.corrcoef(s_pair, q0[n_tr:])[0, 1]),
                                      nearest_bubbles=k0,
                                      train_seconds=t_train, infer_seconds=t1 + t2,
+                                     training_solve_seconds=n_tr * float(Wsec32[0]),
                                      model_gpu_seconds_plain=cost(st2),
-                                     model_gpu_seconds_with_surrogate=cost(st_sur) + t_train + t1 + t2)
+                                     model_gpu_seconds_with_surrogate=cost(st_sur) + t_train + t1 + t2
+                                     + n_tr * float(Wsec32[0]))
         net.close()
     out["gpu_seconds_ratio_fp64_over_fp32"] = r64["gpu_seconds"] / max(r32["gpu_seconds"], 1e-30)
     return out
@@ -568,18 +573,53 @@ def cmd_fitwarm(quick):
     return out
 
 
+# ------------------------------------------------------------------------------ surrogate inside the loop
+
+def cmd_surloop(quick, nearest=(1, 2, 4), levels=None, tau=None, min_pairs=64, steps=600):
+    """Plain OF-MLMC against OF-MLMC with the learned surrogate of the top level
+    term inside ofm_run, to the same tolerance and with the same seed (FP32,
+    20-bubble clouds, centre-sensor peak pressure).  For each number of
+    nearest bubbles in the surrogate's input: GPU-seconds to reach tau (the
+    surrogate's training and inference included), the final eps, beta, and
+    eps^2 x GPU-seconds (at equal GPU-seconds eps^2 scales as 1/cost, so
+    this product compares the two at equal GPU-seconds)."""
+    cloud = W.cloud_uniform(20)
+    sp = W.tiny(16, 20).solver
+    levels = levels or ([16, 32] if quick else [16, 32, 64])
+    tau = tau or (6.0e5 if quick else 2.5e5)
+    s32 = api.Solver(sp, "fp32")
+    common = dict(target=tau, qoi=QOI, max_iterations=8, min_samples=16, max_cell_steps=4e11)
+
+    def summary(r):
+        e2 = r["est"]["eps2"]
+        return dict(gpu_seconds=r["gpu_seconds"], M=r["M"], eps=math.sqrt(e2), mean=r["est"]["mean"],
+                    iterations=r["iterations"], capped=r["capped"], eps2_times_gpu_seconds=e2 * r["gpu_seconds"],
+                    surrogate_used=r["surrogate_used"], beta=r["beta"], surrogate_seconds=r["surrogate_seconds"],
+                    eps_plain_same_pairs=math.sqrt(r["eps2_plain"]),
+                    sigma_tilde2=r["est"]["sigma_tilde2"].tolist(),
+                    sigma_tilde2_plain=r["sigma_tilde2_plain"].tolist())
+    plain, _, _ = api.run_ofmlmc(s32, cloud, levels, **common)
+    out = dict(experiment="surloop", levels=levels, tau=tau, bubbles=20, qoi="centre sensor peak pressure [Pa]",
+               min_pairs=min_pairs, steps=steps, plain=summary(plain), surrogate={})
+    for k in nearest:
+        r, _, _ = api.run_ofmlmc(s32, cloud, levels, surrogate=True, surrogate_min_pairs=min_pairs,
+                                 surrogate_nearest=k, surrogate_steps=steps, **common)
+        out["surrogate"][str(k)] = summary(r)
+    return out
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["uneven3", "surrogate", "rmse", "cfg5", "epsval", "paper500", "orders",
-                                     "fitwarm", "boundaries"])
+                                     "fitwarm", "boundaries", "surloop"])
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--min-samples", type=int, default=16, help="epsval: pairs every level starts with")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     fn = {"uneven3": cmd_uneven3, "surrogate": cmd_surrogate, "rmse": cmd_rmse, "cfg5": cmd_cfg5,
           "epsval": cmd_epsval, "paper500": cmd_paper500, "orders": cmd_orders, "fitwarm": cmd_fitwarm,
-          "boundaries": cmd_boundaries}[a.what]
+          "boundaries": cmd_boundaries, "surloop": cmd_surloop}[a.what]
     print(json.dumps(fn(a.quick, a.min_samples) if a.what == "epsval" else fn(a.quick)), flush=True)
 
 

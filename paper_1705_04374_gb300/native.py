@@ -74,13 +74,18 @@ class ofm_estimate_out(C.Structure):
 class ofm_run_config(C.Structure):
     _fields_ = [("L", C.c_int), ("N", C.c_int * OFM_MAX_LEVELS), ("mode", C.c_int), ("target", C.c_double),
                 ("qoi", C.c_int), ("seed", C.c_uint64), ("max_iterations", C.c_int), ("min_samples", C.c_int),
-                ("max_batch_bytes", C.c_size_t), ("max_cell_steps", C.c_double), ("fit_variances", C.c_int)]
+                ("max_batch_bytes", C.c_size_t), ("max_cell_steps", C.c_double), ("fit_variances", C.c_int),
+                ("surrogate", C.c_int), ("surrogate_min_pairs", C.c_int), ("surrogate_nearest", C.c_int),
+                ("surrogate_steps", C.c_int), ("surrogate_hidden", C.c_int), ("surrogate_lr", C.c_double),
+                ("surrogate_h_out", C.POINTER(C.c_double))]
 
 
 class ofm_run_result(C.Structure):
     _fields_ = [("iterations", C.c_int), ("M", C.c_int64 * OFM_MAX_LEVELS), ("W", C.c_double * OFM_MAX_LEVELS),
                 ("gpu_seconds", C.c_double), ("cell_steps", C.c_double), ("failed", C.c_int64),
-                ("capped", C.c_int), ("est", ofm_estimate_out)]
+                ("capped", C.c_int), ("est", ofm_estimate_out), ("surrogate_used", C.c_int), ("beta", C.c_double),
+                ("surrogate_seconds", C.c_double), ("eps2_plain", C.c_double),
+                ("sigma_tilde2_plain", C.c_double * OFM_MAX_LEVELS)]
 
 
 _vp = C.c_void_p
@@ -118,6 +123,12 @@ SIGNATURES = {
                                          C.c_uint64, _P(ofm_qoi), _P(C.c_double), _vp]),
     "ofm_run": (C.c_int, [_vp, _P(ofm_cloud_params), _P(ofm_run_config), _P(C.c_double), _P(C.c_uint64),
                           C.c_int64, _P(ofm_run_result), _vp]),
+    "ofm_estimate_surrogate": (C.c_int, [C.c_int, _P(C.c_int64), _P(_P(C.c_double)), _P(C.c_double),
+                                         _P(C.c_double), _P(C.c_double), C.c_double, _P(ofm_estimate_out),
+                                         _P(C.c_double), _P(C.c_double)]),
+    "ofm_sj_bandwidth": (C.c_int, [_P(C.c_double), C.c_int64, _P(C.c_double)]),
+    "ofm_level_kde": (C.c_int, [C.c_int, _P(C.c_int64), _P(_P(C.c_double)), _P(C.c_double), _P(C.c_double),
+                                C.c_int64, _P(C.c_double), _P(C.c_double)]),
     "ofm_surrogate_cv": (C.c_int, [_P(C.c_double), _P(C.c_double), C.c_int64, _P(C.c_double), C.c_int64,
                                    _P(C.c_double), _P(C.c_double), _P(C.c_double)]),
     "ofm_mlp_workspace_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P(C.c_size_t)]),

@@ -81,8 +81,18 @@ def test_run_with_variance_fit_starts_the_finest_level_from_one_pair():
     assert res["iterations"] == 1 and res["failed"] == 0
     assert res["M"] == want
     ref = E.estimate_fitted(pairs, res["W"])
-    for k in ("alpha", "sigma2", "cov", "sigma_tilde2"):
+    for k in ("alpha", "sigma2", "cov"):
         assert np.allclose(res["est"][k], ref[k], rtol=1e-12, atol=1e-12), k
+    # sigma~^2_l = V[alpha_l q_l - alpha_{l-1} q_{l-1}] inherits the alphas' rounding
+    # differences (the two solvers order their operations differently; the check
+    # above bounds them only absolutely for small alphas): by Cauchy-Schwarz,
+    # |d sigma~^2_l| <= 2 (|d alpha_l| sigma_l + |d alpha_{l-1}| sigma_{l-1}) sigma~_l to first
+    # order, plus the rounding of the variance sums
+    al, s2, st2 = ref["alpha"], ref["sigma2"], ref["sigma_tilde2"]
+    da = np.abs(np.asarray(res["est"]["alpha"]) - al)
+    bound = np.array([2.0 * (da[l] * np.sqrt(s2[l]) + (da[l - 1] * np.sqrt(s2[l - 1]) if l else 0.0)) * np.sqrt(st2[l])
+                      for l in range(4)]) + 1e-11 * st2
+    assert np.all(np.abs(res["est"]["sigma_tilde2"] - st2) <= bound), (res["est"]["sigma_tilde2"], st2, bound)
     # with a handful of pairs per level alpha can reach tens, so the mean is a
     # cancelling sum: bound its rounding by the size of its terms
     al = ref["alpha"]
@@ -115,3 +125,31 @@ def test_memory_admission_splits_batches_without_changing_results():
         assert np.array_equal(ia[l], ib[l])
         assert np.array_equal(pa[l], pb[l])
     assert a["est"]["mean"] == b["est"]["mean"]
+
+
+def test_run_with_surrogate_matches_oracle_estimator():
+    """The surrogate control variate inside ofm_run: two levels, the network
+    trained once the finest level has 16 pairs; the final estimator equals the
+    oracle's estimate_surrogate on the returned pairs and predictions, the
+    plain estimator on the same pairs is reported beside it, and the
+    surrogate's device time counts in the GPU-seconds."""
+    w = W.tiny(16, 4)
+    s = api.Solver(w.solver, "fp32")
+    res, pairs, ids = api.run_ofmlmc(s, w.cloud, [8, 16], target=1e9, mode="budget", qoi=1,
+                                     max_iterations=2, min_samples=24, max_cell_steps=5e8,
+                                     surrogate=True, surrogate_min_pairs=16, surrogate_nearest=2,
+                                     surrogate_steps=100, surrogate_hidden=64)
+    assert res["surrogate_used"] and res["failed"] == 0
+    h = res["h"]
+    ht, he = h[1], h[0]
+    assert np.all(np.isfinite(ht)) and np.all(np.isfinite(he))
+    ref = E.estimate_surrogate(pairs, res["W"], ht, he)
+    assert res["beta"] == pytest.approx(ref["beta"], rel=1e-10, abs=1e-12)
+    for k in ("alpha", "sigma_tilde2"):
+        assert np.allclose(res["est"][k], ref[k], rtol=1e-10, atol=0), k
+    assert res["est"]["mean"] == pytest.approx(ref["mean"], rel=1e-12)
+    assert res["est"]["eps2"] == pytest.approx(ref["eps2"], rel=1e-10)
+    assert res["eps2_plain"] == pytest.approx(E.estimate(pairs, res["W"])["eps2"], rel=1e-10)
+    assert 0.0 < res["surrogate_seconds"] < res["gpu_seconds"]
+    with pytest.raises(api.nv.OfmError):
+        api.run_ofmlmc(s, w.cloud, [8], target=1.0, max_iterations=1, surrogate=True)

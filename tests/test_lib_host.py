@@ -344,3 +344,61 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         nv.lib()
     with pytest.raises(ImportError):
         api.Solver(W.SolverParams())
+
+
+@pytest.mark.parametrize("precision,N,fits", [("fp32", 32, 12), ("fp64", 32, 6), ("fp32", 64, 1), ("fp64", 64, 0)])
+def test_static_entry_point_capacity(precision, N, fits):
+    """The allocation-free entry point's size check runs on the host before any
+    device call: `fits` samples on N^3 pass it, one more is rejected with
+    OFM_ENOMEM (three state buffers of 7 N^3 values per sample in a 32 MiB
+    array).  Without a GPU the accepted size fails later, at the device."""
+    import ctypes as C
+    sp = W.SolverParams(sensors=W.centre_sensor())
+    s = api.Solver(sp, precision)
+    cp = api.cloud_params(W.cloud_uniform(4))
+    for n, rejected in ((fits, False), (fits + 1, True)):
+        if n == 0:
+            continue
+        ids = (C.c_uint64 * n)(*range(n))
+        out = (nv.ofm_qoi * n)()
+        rc = nv.lib().ofm_solve_level_static(s.h, C.byref(cp), N, n, ids, W.BASE_SEED, out, None, None)
+        assert (rc == nv.OFM_ENOMEM) == rejected, (n, rc, nv.lib().ofm_last_error())
+
+
+def test_surrogate_estimator_matches_oracle():
+    """ofm_estimate_surrogate against the oracle on a toy hierarchy with a
+    nonlinear surrogate: optimal and fixed beta."""
+    rng = np.random.default_rng(9)
+    M = [150, 50, 16]
+    pairs = W.toy_levels(M, 2, 0.5, 0.6, seed=9)
+    ht = 0.7 * pairs[2][:, 1] + 0.2 * np.tanh(pairs[2][:, 1]) + 0.01 * rng.normal(size=M[2])
+    he = 0.7 * pairs[1][:, 0] + 0.2 * np.tanh(pairs[1][:, 0]) + 0.01 * rng.normal(size=M[1])
+    Wl = [1.0, 6.0, 40.0]
+    for beta in (None, 0.4, 0.0):
+        got = api.estimate_surrogate(pairs, Wl, ht, he, beta=beta)
+        ref = E.estimate_surrogate(pairs, Wl, ht, he, beta=beta)
+        assert got["beta"] == pytest.approx(ref["beta"], rel=1e-12, abs=1e-15)
+        for k in ("alpha", "sigma_tilde2", "sigma_tilde2_plain"):
+            assert np.allclose(got[k], ref[k], rtol=1e-12, atol=0), k
+        assert got["mean"] == pytest.approx(ref["mean"], rel=1e-13)
+        assert got["eps2"] == pytest.approx(ref["eps2"], rel=1e-12)
+    with pytest.raises(nv.OfmError):
+        api.estimate_surrogate(pairs[:1], Wl[:1], ht, he)
+
+
+def test_level_kde_matches_oracle():
+    """ofm_sj_bandwidth and ofm_level_kde against the oracle (Sec. 3.2's
+    level-wise density): the bandwidths to the bisection's 1e-10 (sums in
+    another order may move a bisection step), the density accordingly."""
+    from oracle import kde as K
+    pairs = W.toy_levels([300, 120, 40], 2, 0.5, 0.6, seed=12)
+    for x in (pairs[0][:, 0], np.random.default_rng(1).gamma(2.0, size=200)):
+        assert api.sj_bandwidth(x) == pytest.approx(K.sj_bandwidth(x), rel=1e-9)
+    alpha = [0.9, 1.2, 1.0]
+    xs = np.linspace(-6, 8, 57)
+    f, bw = api.level_kde(pairs, alpha, xs)
+    fr, bwr = K.level_kde(pairs, alpha, xs)
+    assert np.allclose(bw, bwr, rtol=1e-9)
+    assert np.allclose(f, fr, rtol=1e-7, atol=1e-9 * np.max(np.abs(fr)))
+    with pytest.raises(nv.OfmError):
+        api.sj_bandwidth([1.0])

@@ -352,3 +352,89 @@ def test_adaptive_loop_with_fit_starts_the_finest_level_from_one_pair():
     assert est["history"][0][:L] == list(np.maximum(E.warmup_M(W), 2))[:L]
     assert math.sqrt(est["eps2"]) <= 0.02
     assert abs(est["mean"] - mean[L]) < 5 * 0.02
+
+
+# ---------------------------------------------------------------- surrogate control variate (not in the paper)
+
+def _toy_with_inputs(M, L, a, b, seed, mu=1.0, c=0.5):
+    """The toy hierarchy of workloads.toy_levels, also returning each pair's
+    shared input Z (the "cloud") so that a surrogate can be evaluated."""
+    rng = np.random.default_rng(seed)
+    pairs, Zs = [], []
+    for l in range(L + 1):
+        m = M[l]
+        Z = rng.standard_normal(m)
+        Yf, Yc = rng.standard_normal(m), rng.standard_normal(m)
+        qf = mu + c * 2.0 ** (-l) + Z + 2.0 ** (-l) * (a * Z + b * Yf)
+        qc = (mu + c * 2.0 ** (-(l - 1)) + Z + 2.0 ** (-(l - 1)) * (a * Z + b * Yc)) if l > 0 else np.zeros(m)
+        pairs.append(np.stack([qf, qc], axis=1))
+        Zs.append(Z)
+    return pairs, Zs
+
+
+def _h(Z, q_coarse):
+    """A fixed, nonlinear, imperfect surrogate of q_L from (input, q_{L-1})."""
+    return 0.8 * q_coarse + 0.3 * np.tanh(Z) + 0.05 * Z ** 2
+
+
+def test_surrogate_estimator_with_zero_beta_is_plain_ofmlmc():
+    pairs, Zs = _toy_with_inputs([200, 60, 20], 2, 0.5, 0.6, seed=1)
+    W = [1.0, 5.0, 25.0]
+    ref = E.estimate(pairs, W)
+    got = E.estimate_surrogate(pairs, W, _h(Zs[2], pairs[2][:, 1]), _h(Zs[1], pairs[1][:, 0]), beta=0.0)
+    assert got["mean"] == pytest.approx(ref["mean"], rel=1e-14, abs=1e-14)
+    assert np.allclose(got["sigma_tilde2"], ref["sigma_tilde2"], rtol=1e-13)
+    assert got["eps2"] == pytest.approx(ref["eps2"], rel=1e-13)
+    # a surrogate that only repeats alpha_{L-1} q_{L-1} leaves nothing to correct: beta = 0
+    flat = E.estimate_surrogate(pairs, W, ref["alpha"][1] * pairs[2][:, 1], ref["alpha"][1] * pairs[1][:, 0])
+    assert flat["beta"] == 0.0 and flat["mean"] == pytest.approx(ref["mean"], rel=1e-14)
+
+
+def test_surrogate_beta_minimises_the_error_estimate():
+    pairs, Zs = _toy_with_inputs([300, 80, 25], 2, 0.5, 0.6, seed=2)
+    W = [1.0, 5.0, 25.0]
+    ht, he = _h(Zs[2], pairs[2][:, 1]), _h(Zs[1], pairs[1][:, 0])
+    best = E.estimate_surrogate(pairs, W, ht, he)
+    grid = np.linspace(best["beta"] - 1.0, best["beta"] + 1.0, 2001)
+    e2 = [E.estimate_surrogate(pairs, W, ht, he, beta=b)["eps2"] for b in grid]
+    assert best["eps2"] <= min(e2) * (1 + 1e-12)
+    assert abs(grid[int(np.argmin(e2))] - best["beta"]) <= 1e-3
+    assert best["eps2"] < best["eps2_plain"]
+
+
+def test_surrogate_estimator_unbiased_and_error_formula_for_fixed_coefficients():
+    """Over independent repeats with fixed alpha and beta: the mean of the
+    estimates is E[q_L] = mu + c 2^-L (any surrogate, even a biased one), and
+    their variance is the mean of eps^2 = sum_l sigma~^2_l / M_l."""
+    L, M, W = 2, [120, 40, 12], [1.0, 5.0, 25.0]
+    alpha, beta = np.array([0.9, 0.95, 1.0]), 0.7
+    R = 4000
+    est, e2 = [], []
+    for r in range(R):
+        pairs, Zs = _toy_with_inputs(M, L, 0.5, 0.6, seed=1000 + r)
+        ht = _h(Zs[2], pairs[2][:, 1]) + 3.0            # biased on purpose
+        he = _h(Zs[1], pairs[1][:, 0]) + 3.0
+        out = E.estimate_surrogate(pairs, W, ht, he, alpha=alpha, beta=beta)
+        est.append(out["mean"])
+        e2.append(out["eps2"])
+    est = np.array(est)
+    truth = 1.0 + 0.5 * 2.0 ** (-L)
+    assert abs(est.mean() - truth) < 4.0 * est.std() / math.sqrt(R)
+    assert est.var(ddof=1) == pytest.approx(np.mean(e2), rel=0.08)
+
+
+def test_a_good_surrogate_lowers_the_top_level_variance():
+    """In the toy q_L = mu + c 2^-L + Z + 2^-L (a Z + b Y_f); the coarse member's
+    own Y is independent, so the best prediction of q_L from the input Z is
+    E[q_L | Z] = mu + c 2^-L + (1 + a 2^-L) Z.  As the surrogate it leaves the
+    top level term only q_L - E[q_L | Z] = 2^-L b Y_f: variance (2^-L b)^2
+    against ~0.13 for the plain term (a = 0.5, b = 0.6, L = 2, alpha ~ 1)."""
+    a, b, L = 0.5, 0.6, 2
+    pairs, Zs = _toy_with_inputs([4000, 800, 400], L, a, b, seed=5)
+    W = [1.0, 5.0, 25.0]
+    good = lambda Z: 1.0 + 0.5 * 2.0 ** (-L) + (1.0 + a * 2.0 ** (-L)) * Z
+    out = E.estimate_surrogate(pairs, W, good(Zs[2]), good(Zs[1]))
+    assert 0.8 < out["beta"] < 1.2
+    assert out["sigma_tilde2"][2] < 0.3 * out["sigma_tilde2_plain"][2]
+    assert out["sigma_tilde2"][2] == pytest.approx((2.0 ** (-L) * b) ** 2, rel=0.25)
+    assert out["eps2"] < out["eps2_plain"]
