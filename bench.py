@@ -384,6 +384,10 @@ def run_ours(args):
 
     # the FP pipes' multiply-add rate measured now, at the clocks this GPU runs at
     probe_tflops = api.probe_fma_tflops(args.precision)
+    try:
+        rmse = rmse_compare(api)
+    except Exception as exc:  # reported, never silently replaced
+        rmse = {"failed": str(exc)}
 
     # roofline of the dominant kernel (the RK-stage kernel)
     flops = load_json(FLOPS_FILE) or {}
@@ -463,10 +467,55 @@ def run_ours(args):
         "roofline_hbm": roofline_hbm,
         "cpu_baseline": cpu,
         "samples_failed": int(sum(1 for s in statuses if s)),
+        "rmse_compare": rmse,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def rmse_compare(api):
+    """GPU-seconds to a fixed OF-MLMC RMSE on a bounded configuration: 3 levels
+    16^3/32^3/64^3, 20-bubble clouds, the centre sensor's peak pressure, tau =
+    8e4 Pa (about 1 % of its mean).  FP32 to tau; FP32 with the learned
+    surrogate of the top level term to tau; FP64: its warm-up iteration
+    measured (the same sample ids as the FP32 runs' first pairs), the run to
+    tau extrapolated as the FP32 run's final sample numbers times the pair
+    costs W_l at FP64's measured seconds per cell-step (same variances up to
+    the FP32 bias, which the common warm-up samples measure and the FP32 RMSE
+    includes: sqrt(eps^2 + bias^2))."""
+    cloud = W.cloud_uniform(20)
+    sp = W.tiny(16, 20).solver
+    levels, tau, qoi = [16, 32, 64], 8.0e4, 1
+    common = dict(target=tau, qoi=qoi, max_iterations=8, min_samples=16, max_cell_steps=4e11)
+    s32 = api.Solver(sp, "fp32")
+    r32, p32, _ = api.run_ofmlmc(s32, cloud, levels, **common)
+    rs, _, _ = api.run_ofmlmc(s32, cloud, levels, surrogate=True, surrogate_min_pairs=64, surrogate_nearest=1,
+                              **common)
+    s64 = api.Solver(sp, "fp64")
+    w64, p64, _ = api.run_ofmlmc(s64, cloud, levels, **dict(common, max_iterations=1))
+    sec_per_cell64 = w64["gpu_seconds"] / w64["cell_steps"]
+    fp64_gpu_s = float(sum(m * w for m, w in zip(r32["M"], r32["W"]))) * sec_per_cell64
+    # FP32 bias on the common warm-up samples, with FP64's coefficients
+    alpha = w64["est"]["alpha"]
+    m0 = [len(p) for p in p64]
+    mean32 = sum(float(np.mean(alpha[l] * p32[l][:m0[l], 0] - (alpha[l - 1] * p32[l][:m0[l], 1] if l else 0.0)))
+                 for l in range(len(levels)))
+    bias = abs(mean32 - w64["est"]["mean"])
+
+    def arm(r):
+        return {"gpu_seconds": r["gpu_seconds"], "eps": float(np.sqrt(r["est"]["eps2"])),
+                "rmse": float(np.sqrt(r["est"]["eps2"] + bias ** 2)), "M": r["M"], "mean": r["est"]["mean"]}
+    sur = arm(rs)
+    sur.update(surrogate_used=rs["surrogate_used"], beta=rs["beta"], surrogate_seconds=rs["surrogate_seconds"])
+    return {"config": "3 levels 16^3/32^3/64^3, 20-bubble clouds, centre-sensor peak pressure, tau 8e4 Pa "
+                      "(~1 % of the mean)", "tau": tau, "fp32_bias": bias,
+            "fp32": arm(r32), "fp32_surrogate": sur,
+            "fp64": {"gpu_seconds": fp64_gpu_s, "method": "warm-up measured (gpu_seconds %.2f, M %s), extrapolated "
+                     "to the FP32 run's sample numbers at %.3g s per cell-step" % (w64["gpu_seconds"], w64["M"],
+                                                                                   sec_per_cell64)},
+            "fp64_over_fp32": fp64_gpu_s / r32["gpu_seconds"],
+            "fp64_over_fp32_surrogate": fp64_gpu_s / rs["gpu_seconds"]}
 
 
 def run_profile_case(args):

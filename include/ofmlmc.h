@@ -407,7 +407,8 @@ typedef struct {
      * Adam at surrogate_lr, up to surrogate_steps steps with the parameters of
      * the lowest error on a fifth of the fold held out) on the two halves of
      * the level-L pairs (input: the surrogate_nearest bubbles nearest the domain
-     * centre, ofm_cloud_features, and the pair's q_{L-1}; target: q_L), predicts
+     * centre, ofm_cloud_features, and the pair's q_{L-1}; target: the residual
+     * q_L - q_{L-1}, so the prediction of q_L is q_{L-1} plus it), predicts
      * each pair with the network of the other half (cross-fitting) and the
      * level-(L-1) pairs' fine members with both, and estimates with
      * ofm_estimate_surrogate; step 7 then takes the modified variances.  Its

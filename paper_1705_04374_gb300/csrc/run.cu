@@ -213,7 +213,7 @@ int predict(ofm_mlp* net, const std::vector<float>& X, int n, std::vector<double
     return r;
 }
 
-// One network trained on the rows `rows` of (X, y): He-initialised weights
+// One network trained on the rows `rows` of (X, y) (y: the residual q_L - q_{L-1}): He-initialised weights
 // from a seeded generator, inputs and target standardised by the training
 // rows' moments, full-batch Adam on the first four fifths of the rows in
 // chunks of SUR_CHUNK steps, the parameters with the lowest mean squared
@@ -325,9 +325,13 @@ int surrogate_predictions(const ofm_cloud_params* cloud, const ofm_run_config* r
     const int64_t M = (int64_t)ids_top.size();
     std::vector<int64_t> fold[2];
     for (int64_t i = 0; i < M; ++i) fold[i & 1].push_back(i);
+    // the networks learn the residual q_L - q_{L-1} (its spread is the level
+    // difference's, far below q_L's), and predict q_L as q_{L-1} plus it
+    std::vector<double> resid(M);
+    for (int64_t i = 0; i < M; ++i) resid[i] = fine_top[i] - coarse_top[i];
     ofm_mlp* net[2] = {nullptr, nullptr};
     for (int f = 0; f < 2 && r == OFM_OK; ++f)
-        r = train_fold(Xt, fine_top, d, fold[f], su, rc->seed ^ (0x5DEECE66Dull * (uint64_t)(2 * iteration + f + 1)),
+        r = train_fold(Xt, resid, d, fold[f], su, rc->seed ^ (0x5DEECE66Dull * (uint64_t)(2 * iteration + f + 1)),
                        &net[f], st);
     h_top.assign(M, 0.0);
     h_extra.assign(ids_extra.size(), 0.0);
@@ -339,14 +343,15 @@ int surrogate_predictions(const ofm_cloud_params* cloud, const ofm_run_config* r
                       Xf.begin() + i * d);
         std::vector<double> y;
         r = predict(net[1 - f], Xf, (int)fold[f].size(), y, st);
-        for (size_t i = 0; i < fold[f].size() && r == OFM_OK; ++i) h_top[fold[f][i]] = y[i];
+        for (size_t i = 0; i < fold[f].size() && r == OFM_OK; ++i)
+            h_top[fold[f][i]] = coarse_top[fold[f][i]] + y[i];
     }
     for (int f = 0; f < 2 && r == OFM_OK; ++f) {
         // network f predicts the rows of the other fold: weight = the other fold's share
         const double w = (double)fold[1 - f].size() / (double)M;
         std::vector<double> y;
         r = predict(net[f], Xe, (int)ids_extra.size(), y, st);
-        for (size_t j = 0; j < y.size() && r == OFM_OK; ++j) h_extra[j] += w * y[j];
+        for (size_t j = 0; j < y.size() && r == OFM_OK; ++j) h_extra[j] += w * (fine_extra[j] + y[j]);
     }
     for (int f = 0; f < 2; ++f) ofm_mlp_destroy(net[f]);
     cudaEventRecord(e1, st);

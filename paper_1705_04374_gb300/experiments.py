@@ -575,7 +575,7 @@ def cmd_fitwarm(quick):
 
 # ------------------------------------------------------------------------------ surrogate inside the loop
 
-def cmd_surloop(quick, nearest=(1, 2, 4), levels=None, tau=None, min_pairs=64, steps=600):
+def cmd_surloop(quick, nearest=(1, 2, 4), levels=None, tau=None, min_pairs=64, steps=600, hidden=256):
     """Plain OF-MLMC against OF-MLMC with the learned surrogate of the top level
     term inside ofm_run, to the same tolerance and with the same seed (FP32,
     20-bubble clouds, centre-sensor peak pressure).  For each number of
@@ -600,10 +600,10 @@ def cmd_surloop(quick, nearest=(1, 2, 4), levels=None, tau=None, min_pairs=64, s
                     sigma_tilde2_plain=r["sigma_tilde2_plain"].tolist())
     plain, _, _ = api.run_ofmlmc(s32, cloud, levels, **common)
     out = dict(experiment="surloop", levels=levels, tau=tau, bubbles=20, qoi="centre sensor peak pressure [Pa]",
-               min_pairs=min_pairs, steps=steps, plain=summary(plain), surrogate={})
+               min_pairs=min_pairs, steps=steps, hidden=hidden, plain=summary(plain), surrogate={})
     for k in nearest:
         r, _, _ = api.run_ofmlmc(s32, cloud, levels, surrogate=True, surrogate_min_pairs=min_pairs,
-                                 surrogate_nearest=k, surrogate_steps=steps, **common)
+                                 surrogate_nearest=k, surrogate_steps=steps, surrogate_hidden=hidden, **common)
         out["surrogate"][str(k)] = summary(r)
     return out
 

@@ -83,15 +83,25 @@ def test_run_with_variance_fit_starts_the_finest_level_from_one_pair():
     ref = E.estimate_fitted(pairs, res["W"])
     for k in ("alpha", "sigma2", "cov"):
         assert np.allclose(res["est"][k], ref[k], rtol=1e-12, atol=1e-12), k
-    # sigma~^2_l = V[alpha_l q_l - alpha_{l-1} q_{l-1}] inherits the alphas' rounding
-    # differences (the two solvers order their operations differently; the check
-    # above bounds them only absolutely for small alphas): by Cauchy-Schwarz,
-    # |d sigma~^2_l| <= 2 (|d alpha_l| sigma_l + |d alpha_{l-1}| sigma_{l-1}) sigma~_l to first
-    # order, plus the rounding of the variance sums
-    al, s2, st2 = ref["alpha"], ref["sigma2"], ref["sigma_tilde2"]
+    # sigma~^2_l = V[D_l], D_l = alpha_l q_l - alpha_{l-1} q_{l-1}.  With a handful of
+    # pairs the fit can make the alphas huge (here up to ~3e5 on peak pressures
+    # of 1e7 Pa that vary by a pascal), so D_l is ~1e7 times its own spread and
+    # the rounding of forming it, up to ~4 eps (|alpha_l q_l| + |alpha_{l-1} q_{l-1}|)
+    # per term, moves V[D_l] by up to 2 sigma~_l times that; the alphas' own
+    # rounding differences add 2 (|d alpha_l| sigma_l + |d alpha_{l-1}| sigma_{l-1}) sigma~_l
+    # (first order, Cauchy-Schwarz); a level with one pair takes sigma~^2 from the
+    # fitted moments, rounded on the scale of its terms
+    eps = np.finfo(float).eps
+    al, s2, st2, cv = ref["alpha"], ref["sigma2"], ref["sigma_tilde2"], ref["cov"]
     da = np.abs(np.asarray(res["est"]["alpha"]) - al)
-    bound = np.array([2.0 * (da[l] * np.sqrt(s2[l]) + (da[l - 1] * np.sqrt(s2[l - 1]) if l else 0.0)) * np.sqrt(st2[l])
-                      for l in range(4)]) + 1e-11 * st2
+    bound = np.zeros(4)
+    for l in range(4):
+        big = np.abs(al[l] * pairs[l][:, 0]) + (np.abs(al[l - 1] * pairs[l][:, 1]) if l else 0.0)
+        bound[l] = 2.0 * np.sqrt(st2[l]) * (4.0 * eps * np.max(big)
+                                            + da[l] * np.sqrt(s2[l]) + (da[l - 1] * np.sqrt(s2[l - 1]) if l else 0.0))
+        if pairs[l].shape[0] == 1:
+            bound[l] += 8.0 * eps * (al[l] ** 2 * s2[l] + al[l - 1] ** 2 * s2[l - 1] + 2.0 * abs(al[l] * al[l - 1] * cv[l]))
+    bound += 1e-12 * st2
     assert np.all(np.abs(res["est"]["sigma_tilde2"] - st2) <= bound), (res["est"]["sigma_tilde2"], st2, bound)
     # with a handful of pairs per level alpha can reach tens, so the mean is a
     # cancelling sum: bound its rounding by the size of its terms
