@@ -414,17 +414,17 @@ def cmd_paper500(quick):
     log-normal radii in [0.8, 1.2] mm), bubbles and the cloud's liquid at 0.5 MPa, 1/r ramp
     to 10 MPa from 1 mm beyond the cloud surface; QoI the centre pressure sensor p_c (Eq.
     sensor).  (a) An OF-MLMC run on 4 levels 32^3..256^3 for a fixed budget of cell-steps
-    (Eq. M-budget, FP32 stencil, 16 starting pairs per level, to the paper's 70 us).  The
-    paper's levels are 512^3..4096^3; here 16^3..128^3 (h = 0.78 mm on the finest, about a
-    bubble radius), so that 16 finest pairs fit the budget.  (b) Plain Monte Carlo
+    (Eq. M-budget, FP32 stencil, characteristic far-field boundaries, 16 starting pairs per
+    level, to the paper's 70 us).  The paper's levels are 512^3..4096^3; the finest here has
+    h = 0.39 mm (--quick: 8^3..64^3).  (b) Plain Monte Carlo
     statistics of the other QoIs of Sec. 3.2 on 64^3: peak pressure and its distance from
     the centre, maximum sound speed, and the cloud's gas-volume collapse time (time of the
     minimum gas fraction of a 20 mm ball about the centre, the paper's sensor #5)."""
     cloud = W.cloud_paper500()
     c = 0.5 * W.DOMAIN_L
     sp = W.solver_paper500(sensors=(W.centre_sensor()[0], (c, c, c, 0.02)), t_end=70e-6)
-    levels = [8, 16, 32, 64] if quick else [16, 32, 64, 128]
-    budget = 5.0e9 if quick else 6.0e10
+    levels = [8, 16, 32, 64] if quick else [32, 64, 128, 256]
+    budget = 5.0e9 if quick else 1.0e12
     s32 = api.Solver(sp, "fp32")
     res, pairs, ids = api.run_ofmlmc(s32, cloud, levels, target=budget, mode="budget", qoi=1, max_iterations=4,
                                      max_cell_steps=2.0 * budget, min_samples=16, capacity=1 << 18)
@@ -608,18 +608,127 @@ def cmd_surloop(quick, nearest=(1, 2, 4), levels=None, tau=None, min_pairs=64, s
     return out
 
 
+# ------------------------------------------------------------------------------ cfg5 to a tolerance
+
+def cmd_cfg5tol(quick, tau_rel=0.01, mean_guess=8.97e6):
+    """500-bubble clouds, 4 levels 32^3..256^3 (--quick: 16^3..128^3), peak
+    pressure, to tau = 1 % of its mean (mean from the earlier budget run of
+    this configuration, 8.97e6 Pa), FP32 stencil with the learned surrogate of
+    the top level term enabled (it enters once the finest level has 64 pairs),
+    memory-admitted batches.  The plain FP32 estimator on the same final pairs
+    is reported beside it.  FP64: its throughput measured per level on the
+    same clouds (2 samples, 6 steps each) and the run's cell-steps divided by
+    it; the FP32 bias from 3 common clouds solved to t_end in both precisions
+    on the two coarsest levels."""
+    import torch
+    cloud = W.cloud_uniform(500)
+    sp = W.SolverParams(sensors=W.centre_sensor())
+    levels = [16, 32, 64, 128] if quick else [32, 64, 128, 256]
+    tau = tau_rel * mean_guess
+    s32 = api.Solver(sp, "fp32")
+    res, pairs, ids = api.run_ofmlmc(s32, cloud, levels, target=tau, mode="tol", qoi=0, max_iterations=6,
+                                     min_samples=16, max_cell_steps=8e12, capacity=1 << 18, surrogate=True,
+                                     surrogate_min_pairs=64, surrogate_nearest=1)
+    out = dict(experiment="cfg5tol", levels=levels, bubbles=500, qoi="peak pressure [Pa]", tau=tau,
+               M=res["M"], W_cell_steps=res["W"], iterations=res["iterations"], capped=res["capped"],
+               failed=res["failed"], gpu_seconds=res["gpu_seconds"], cell_steps=res["cell_steps"],
+               eps=math.sqrt(res["est"]["eps2"]), eps_plain_same_pairs=math.sqrt(res["eps2_plain"]),
+               mean=res["est"]["mean"], alpha=res["est"]["alpha"].tolist(),
+               sigma_tilde2=res["est"]["sigma_tilde2"].tolist(), surrogate_used=res["surrogate_used"],
+               beta=res["beta"], surrogate_seconds=res["surrogate_seconds"])
+    # FP64 throughput per level on the same clouds
+    s64 = api.Solver(sp, "fp64")
+    rate64 = []
+    for N in levels:
+        g = api.make_group(sp, N, level_ids(8, 0, 2), W.BASE_SEED)
+        b = api.Batch(s64, cloud, [g])
+        b.init()
+        b.run(2)
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        b.run(6)
+        e1.record()
+        torch.cuda.synchronize()
+        rate64.append(2.0 * N ** 3 * 6 / (e0.elapsed_time(e1) / 1e3))
+        b.close()
+    fp64_s = float(sum(m * w / r for m, w, r in zip(res["M"], res["W"], rate64)))
+    # FP32 bias on common clouds (two coarsest levels, t_end, both precisions)
+    bias = []
+    for N in levels[:2]:
+        sid = level_ids(9, 0, 3)
+        (q32,), _, _ = solve_groups(s32, cloud, [(N, sid)])
+        (q64,), _, _ = solve_groups(s64, cloud, [(N, sid)])
+        bias.append(float(np.mean([a["p_peak"] - b["p_peak"] for a, b in zip(q32, q64)])))
+    out.update(fp64_rate_cell_updates_per_s=rate64, fp64_gpu_seconds_extrapolated=fp64_s,
+               fp64_over_fp32=fp64_s / max(res["gpu_seconds"], 1e-30), fp32_bias_by_level=bias,
+               rmse_fp32=math.sqrt(res["est"]["eps2"] + max(abs(b) for b in bias) ** 2))
+    return out
+
+
+# ------------------------------------------------------------------------------ MLP timing
+
+def cmd_mlptime(quick):
+    """The surrogate MLP (3 hidden layers of 256, GELU, BF16 operands, FP32
+    accumulation) at the shapes of the surrogate configurations: inference on
+    65,536 rows with 4 x 50 + 1 and 4 x 500 + 1 inputs, and training steps on
+    512 rows; CUDA events, algorithmic flops 2 rows sum(fan_in fan_out)
+    (forward; training 3 times that)."""
+    import torch
+    out = {}
+    for d_in in (201, 2001):
+        sizes = [d_in, 256, 256, 256, 1]
+        gemm = sum(a * b for a, b in zip(sizes[:-1], sizes[1:]))
+        rows = 65536
+        net = S.MLP(d_in, 256, 3, 1, max_rows=rows)
+        rng = np.random.default_rng(0)
+        net.set_params(np.concatenate([np.concatenate([(rng.normal(size=(a, b)) * math.sqrt(2.0 / a)).ravel(),
+                                                       np.zeros(b)]) for a, b in zip(sizes[:-1], sizes[1:])])
+                       .astype(np.float32))
+        X = torch.randn(rows, d_in, device="cuda")
+        net.forward(X)
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(10):
+            net.forward(X)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        res = dict(forward_rows=rows, forward_ms=ms, forward_tflops=2.0 * rows * gemm / (ms * 1e-3) / 1e12)
+        net.close()
+        n_tr = 512
+        net = S.MLP(d_in, 256, 3, 1, max_rows=n_tr)
+        net.set_params(np.zeros(sum(a * b + b for a, b in zip(sizes[:-1], sizes[1:])), dtype=np.float32) + 0.01)
+        Xt = torch.randn(n_tr, d_in, device="cuda")
+        Tt = torch.randn(n_tr, 1, device="cuda")
+        net.train(Xt, Tt, steps=5)
+        torch.cuda.synchronize()
+        e0.record()
+        net.train(Xt, Tt, steps=100)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_t = e0.elapsed_time(e1) / 100
+        res.update(train_rows=n_tr, train_step_ms=ms_t,
+                   train_tflops=3 * 2.0 * n_tr * gemm / (ms_t * 1e-3) / 1e12)
+        net.close()
+        out[f"d_in_{d_in}"] = res
+    return out
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["uneven3", "surrogate", "rmse", "cfg5", "epsval", "paper500", "orders",
-                                     "fitwarm", "boundaries", "surloop"])
+                                     "fitwarm", "boundaries", "surloop", "cfg5tol", "mlptime"])
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--min-samples", type=int, default=16, help="epsval: pairs every level starts with")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     fn = {"uneven3": cmd_uneven3, "surrogate": cmd_surrogate, "rmse": cmd_rmse, "cfg5": cmd_cfg5,
           "epsval": cmd_epsval, "paper500": cmd_paper500, "orders": cmd_orders, "fitwarm": cmd_fitwarm,
-          "boundaries": cmd_boundaries, "surloop": cmd_surloop}[a.what]
+          "boundaries": cmd_boundaries, "surloop": cmd_surloop, "cfg5tol": cmd_cfg5tol,
+          "mlptime": cmd_mlptime}[a.what]
     print(json.dumps(fn(a.quick, a.min_samples) if a.what == "epsval" else fn(a.quick)), flush=True)
 
 
