@@ -608,7 +608,7 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
 __device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(1.0f / a.x, 1.0f / a.y); }
 
-// WENO5 states of a run of R faces (the arithmetic of face_run_fp32's
+// WENO5 states of a run of R faces (the arithmetic of run_states_fp32's
 // scalar loop) for two variables at once: lane x from Pa, lane y from Pb.
 template <int R>
 __device__ __forceinline__ void weno5_run2(const float* __restrict__ Pa, const float* __restrict__ Pb,
@@ -689,19 +689,18 @@ __device__ __forceinline__ void face_fp32(const Eos<float>& e, const float* __re
     hllc_frame(wl, wr, GL, PiL, GR, PiR, F);
 }
 
-// Single precision: R consecutive faces of one line.  idx[i] (i = 0..R+4)
-// is the staged index of the line's cell j - 3 + i, where face j (between
-// cells j - 1 and j) is the run's first face.  Each variable's R + 5 staged
-// values are loaded once, and each of the cells j - 1 .. j + R - 1 forms its
-// three smoothness indicators once for the left state of the face to its
-// right and the right state of the face to its left (the operations of
-// weno5_pair, in its order).  vo as in face_fp32.  Face r's 8 values go to
-// dst[r * step + v * stride] in the staged variable order.
+// Single precision: the WENO5 states of R consecutive faces of one line.
+// idx[i] (i = 0..R+4) is the staged index of the line's cell j - 3 + i,
+// where face j (between cells j - 1 and j) is the run's first face.  Each
+// variable's R + 5 staged values are loaded once, and each of the cells
+// j - 1 .. j + R - 1 forms its three smoothness indicators once for the left
+// state of the face to its right and the right state of the face to its left
+// (the operations of weno5_pair, in its order).  vo as in face_fp32: the
+// states come out in the face frame.
 template <int R>
-__device__ __forceinline__ void face_run_fp32(const Eos<float>& e, const float* __restrict__ sW,
-                                              const int (&idx)[R + 5], const int (&vo)[7], int dir,
-                                              float* __restrict__ dst, int step, int stride) {
-    float wl[R][7], wr[R][7];
+__device__ __forceinline__ void run_states_fp32(const Eos<float>& e, const float* __restrict__ sW,
+                                                const int (&idx)[R + 5], const int (&vo)[7], float (&wl)[R][7],
+                                                float (&wr)[R][7]) {
     const float eps4 = 4.0f * e.eps;
     // the face-frame velocities (2, 3) and (4, 5) in packed pairs (packing the
     // partial densities (0, 1) as well needs more registers than the three
@@ -764,33 +763,26 @@ __device__ __forceinline__ void face_run_fp32(const Eos<float>& e, const float* 
             }
         }
     }
-    const int r1 = dir == 0 ? 3 : (dir == 1 ? 4 : 2);
-    const int r2 = dir == 0 ? 4 : (dir == 1 ? 2 : 3);
+}
+
+// Fluxes of face r of a run from its states (positivity fallback to the cell
+// values, then HLLC): F in the face frame (see hllc_frame).
+template <int R>
+__device__ __forceinline__ void run_flux_fp32(const Eos<float>& e, const float* __restrict__ sW,
+                                              const int (&idx)[R + 5], const int (&vo)[7], int r, float (&wl)[7],
+                                              float (&wr)[7], float (&F)[8]) {
+    float GL, PiL, GR, PiR;
+    if (!admissible_f(e, wl, GL, PiL)) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        float GL, PiL, GR, PiR;
-        if (!admissible_f(e, wl[r], GL, PiL)) {
-#pragma unroll
-            for (int v = 0; v < 7; ++v) wl[r][v] = sW[vo[v] + idx[r + 2]];
-            closure(e, wl[r][6], GL, PiL);
-        }
-        if (!admissible_f(e, wr[r], GR, PiR)) {
-#pragma unroll
-            for (int v = 0; v < 7; ++v) wr[r][v] = sW[vo[v] + idx[r + 3]];
-            closure(e, wr[r][6], GR, PiR);
-        }
-        float F[8];
-        hllc_frame(wl[r], wr[r], GL, PiL, GR, PiR, F);
-        float* o = dst + r * step;
-        o[0] = F[0];
-        o[stride] = F[1];
-        o[(2 + dir) * stride] = F[2];
-        o[r1 * stride] = F[3];
-        o[r2 * stride] = F[4];
-        o[5 * stride] = F[5];
-        o[6 * stride] = F[6];
-        o[7 * stride] = F[7];
+        for (int v = 0; v < 7; ++v) wl[v] = sW[vo[v] + idx[r + 2]];
+        closure(e, wl[6], GL, PiL);
     }
+    if (!admissible_f(e, wr, GR, PiR)) {
+#pragma unroll
+        for (int v = 0; v < 7; ++v) wr[v] = sW[vo[v] + idx[r + 3]];
+        closure(e, wr[6], GR, PiR);
+    }
+    hllc_frame(wl, wr, GL, PiL, GR, PiR, F);
 }
 
 // One face in double precision, in the FP64 reference's operation order.
@@ -1046,11 +1038,133 @@ struct TileRhs {
     T divu[CELLS_PER_THREAD];
 };
 
+// The far face of every line of the tile (x = 8, y = 8 or z = 8; 64 per
+// direction, all three directions), its 8 values (staged variable order) to
+// sFb[dir][v][line].
 template <typename T, int ORD>
-__device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>& c, const T* __restrict__ sW,
-                                           T* __restrict__ sF, const int* __restrict__ sRow, TileRhs<T>& R) {
-    const T invh = T(1) / (T)c.bw.G->h;  // 1/h, formed as the FP64 reference forms it
-    const Eos<T> e = P.eos;
+__device__ __forceinline__ void far_faces(const Eos<T>& e, const T* __restrict__ sW, const int* __restrict__ sRow,
+                                          T* __restrict__ sFb) {
+    for (int f = threadIdx.x; f < 3 * TS * TS; f += NT) {
+        const int dir = f >> 6, line = f & 63, a = line & 7, b = line >> 3;
+        int i6[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            i6[k] = dir == 0 ? sRow[(b + HALO) * BX + a + HALO] + TS - 3 + k
+                             : (dir == 1 ? sRow[(b + HALO) * BX + TS - 3 + k + HALO] + a
+                                         : sRow[(TS - 3 + k + HALO) * BX + b + HALO] + a);
+        face_store<T, ORD>(e, sW, i6, dir, sFb + dir * 8 * TS * TS + line, TS * TS);
+    }
+}
+
+// Slot of tile cell c = x + 8 y + 64 z in the accumulation array: bits 3-4
+// (the low bits of y) are XORed with (z >> 1) ^ (y >> 2), a permutation
+// within each group of 32 cells, so that the y-run stores (lanes x, runs
+// y = 0, 2, 4, 6), the z-run updates (lanes x, runs z = 0, 2, 4, 6) and the
+// owners' paired reads (x pairs, rows y) each touch 32 distinct banks.
+__device__ __forceinline__ int rslot(int c) { return c ^ ((((c >> 7) & 3) ^ ((c >> 5) & 1)) << 3); }
+
+// Single-precision WENO5 faces and right-hand sides of one tile, with no
+// staging of near-face fluxes: every thread takes one run of two consecutive
+// near faces j, j + 1 of one line per direction, so it holds both faces of
+// cell j; the run's neighbour along the line (the next thread in x, eight
+// threads on in y and z, so always in the same warp) hands over its first face
+// by a warp shuffle, the line's last run takes the far face computed up front.
+// Directions y and z add their flux differences to a shared per-cell array
+// (y stores, z accumulates, a barrier between them); direction x comes last,
+// where a thread's run is its own cell pair (2t, 2t + 1), so it adds its
+// differences in registers to the array's y + z sum.  Three barriers per tile
+// instead of seven.
+__device__ __forceinline__ void tile_faces_direct(const Eos<float>& e, float invh, const float* __restrict__ sW,
+                                                  float* __restrict__ sF, const int* __restrict__ sRow,
+                                                  TileRhs<float>& R) {
+    float* __restrict__ sR = sF;                   // [8][RSTRIDE]: y + z contributions per cell
+    float* __restrict__ sFb = sF + 8 * RSTRIDE;    // [3][8][64]: far faces
+    far_faces<float, 5>(e, sW, sRow, sFb);
+    __syncthreads();
+    const int t = threadIdx.x;
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+        const int dir = k == 2 ? 0 : k + 1;   // y, z, then x
+        int a, b, j;   // the line's two other coordinates and the run's first face
+        if (dir == 0) {
+            j = 2 * (t & 3);
+            a = (t >> 2) & 7;
+            b = t >> 5;
+        } else {
+            a = t & 7;
+            j = 2 * ((t >> 3) & 3);
+            b = t >> 5;
+        }
+        int idx[7];
+#pragma unroll
+        for (int i = 0; i < 7; ++i)
+            idx[i] = dir == 0 ? sRow[(b + HALO) * BX + a + HALO] + j - 3 + i
+                              : (dir == 1 ? sRow[(b + HALO) * BX + j - 3 + i + HALO] + a
+                                          : sRow[(j - 3 + i + HALO) * BX + b + HALO] + a);
+        const int r1 = dir == 0 ? 3 : (dir == 1 ? 4 : 2);   // staged variable of the first tangential velocity
+        const int r2 = dir == 0 ? 4 : (dir == 1 ? 2 : 3);   // and of the second
+        const int vo[7] = {0, NCROSS, (2 + dir) * NCROSS, r1 * NCROSS, r2 * NCROSS, 5 * NCROSS, 6 * NCROSS};
+        float F0[8], F1[8];
+        {
+            float wl[2][7], wr[2][7];
+            run_states_fp32<2>(e, sW, idx, vo, wl, wr);
+            run_flux_fp32<2>(e, sW, idx, vo, 0, wl[0], wr[0], F0);
+            run_flux_fp32<2>(e, sW, idx, vo, 1, wl[1], wr[1], F1);
+        }
+        // face j + 2: the next run's first face, or the line's far face
+        const int line = a + 8 * b;
+        const bool last = j == TS - 2;
+        const int so[8] = {0, 1, 2 + dir, r1, r2, 5, 6, 7};   // staged variable of face-frame value v
+        float dA[8], dB[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            float fn = __shfl_down_sync(0xffffffffu, F0[v], dir == 0 ? 1 : 8);
+            if (last) fn = sFb[(dir * 8 + so[v]) * (TS * TS) + line];
+            dA[v] = F1[v] - F0[v];
+            dB[v] = fn - F1[v];
+        }
+        if (dir == 0) {
+            // cells 2t, 2t + 1 (j + 8a + 64b): the thread's own pair, face frame = staged order
+            const int cA = rslot(2 * t);
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const float2 acc = *reinterpret_cast<const float2*>(sR + v * RSTRIDE + cA);
+                const float2 r = fma2(make_float2(dA[v], dB[v]), f2(v < 7 ? -invh : invh), acc);
+                if (v < 7) {
+                    R.rhs[0][v] = r.x;
+                    R.rhs[1][v] = r.y;
+                } else {
+                    R.divu[0] = r.x;
+                    R.divu[1] = r.y;
+                }
+            }
+        } else {
+            const int cA = dir == 1 ? a + 8 * j + 64 * b : a + 8 * b + 64 * j;
+            const int step = dir == 1 ? 8 : 64;
+            const int sA = rslot(cA), sB = rslot(cA + step);
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const float s = v < 7 ? -invh : invh;
+                float* dst = sR + so[v] * RSTRIDE;
+                if (dir == 1) {
+                    dst[sA] = dA[v] * s;
+                    dst[sB] = dB[v] * s;
+                } else {
+                    dst[sA] = fmaf(dA[v], s, dst[sA]);
+                    dst[sB] = fmaf(dB[v], s, dst[sB]);
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Faces staged per direction (double precision in the FP64 reference's
+// accumulation order, and single-precision WENO3): the near faces of one
+// direction into sF, a barrier, the per-cell differences, a barrier.
+template <typename T, int ORD>
+__device__ __forceinline__ void tile_faces_staged(const Eos<T>& e, T invh, const T* __restrict__ sW,
+                                                  T* __restrict__ sF, const int* __restrict__ sRow, TileRhs<T>& R) {
     T (&divu)[CELLS_PER_THREAD] = R.divu;
     T (&rhs)[CELLS_PER_THREAD][7] = R.rhs;
 #pragma unroll
@@ -1065,48 +1179,10 @@ __device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>&
     // of every cell (512, two per thread) into sF, so that every barrier
     // interval holds the same number of faces per thread.
     T* __restrict__ sFb = sF + 8 * NCELL;   // [3][8][64]
-    for (int f = threadIdx.x; f < 3 * TS * TS; f += NT) {
-        const int dir = f >> 6, line = f & 63, a = line & 7, b = line >> 3;
-        int i6[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-            i6[k] = dir == 0 ? sRow[(b + HALO) * BX + a + HALO] + TS - 3 + k
-                             : (dir == 1 ? sRow[(b + HALO) * BX + TS - 3 + k + HALO] + a
-                                         : sRow[(TS - 3 + k + HALO) * BX + b + HALO] + a);
-        face_store<T, ORD>(e, sW, i6, dir, sFb + dir * 8 * TS * TS + line, TS * TS);
-    }
+    far_faces<T, ORD>(e, sW, sRow, sFb);
 #pragma unroll 1
     for (int dir = 0; dir < 3; ++dir) {
-        bool by_runs = false;
-        if constexpr (std::is_same<T, float>::value && NEAR_RUN > 1 && ORD == 5) {
-            // runs of NEAR_RUN consecutive near faces along each line, one per thread
-            constexpr int NR = TS / NEAR_RUN;   // runs per line
-            for (int t = threadIdx.x; t < TS * TS * NR; t += NT) {
-                int a, b, j;   // the line's two other coordinates and the run's first face
-                if (dir == 0) {
-                    j = NEAR_RUN * (t % NR);
-                    a = (t / NR) & 7;
-                    b = (t / NR) >> 3;
-                } else {
-                    a = t & 7;
-                    j = NEAR_RUN * ((t >> 3) % NR);
-                    b = (t >> 3) / NR;
-                }
-                int idx[NEAR_RUN + 5];
-#pragma unroll
-                for (int i = 0; i < NEAR_RUN + 5; ++i)
-                    idx[i] = dir == 0 ? sRow[(b + HALO) * BX + a + HALO] + j - 3 + i
-                                      : (dir == 1 ? sRow[(b + HALO) * BX + j - 3 + i + HALO] + a
-                                                  : sRow[(j - 3 + i + HALO) * BX + b + HALO] + a);
-                const int r1 = dir == 0 ? 3 : (dir == 1 ? 4 : 2);
-                const int r2 = dir == 0 ? 4 : (dir == 1 ? 2 : 3);
-                const int vo[7] = {0, NCROSS, (2 + dir) * NCROSS, r1 * NCROSS, r2 * NCROSS, 5 * NCROSS, 6 * NCROSS};
-                const int c0 = dir == 0 ? j + 8 * a + 64 * b : (dir == 1 ? a + 8 * j + 64 * b : a + 8 * b + 64 * j);
-                face_run_fp32<NEAR_RUN>(e, sW, idx, vo, dir, sF + c0, dir == 0 ? 1 : (dir == 1 ? 8 : 64), NCELL);
-            }
-            by_runs = true;
-        }
-        for (int c = by_runs ? NCELL : threadIdx.x; c < NCELL; c += NT) {
+        for (int c = threadIdx.x; c < NCELL; c += NT) {
             const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
             int i6[6];
 #pragma unroll
@@ -1148,28 +1224,37 @@ __device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>&
                     divu[1] = r.y;
                 }
             }
-            __syncthreads();
-            continue;
-        }
+        } else {
 #pragma unroll
-        for (int k = 0; k < CELLS_PER_THREAD; ++k) {
-            const int c = own_cell<T>(k);
-            if (c < NCELL) {
-                const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-                const int cd = dir == 0 ? x : (dir == 1 ? y : z);
-                const int step = dir == 0 ? 1 : (dir == 1 ? 8 : 64);
-                const int line = dir == 0 ? c >> 3 : (dir == 1 ? x + 8 * z : c & 63);
-                // flux at the cell's far face: the next cell's near face, or the line's far face
-                const T* __restrict__ Fr = cd < TS - 1 ? sF + c + step : sFb + dir * 8 * TS * TS + line;
-                const int sr = cd < TS - 1 ? NCELL : TS * TS;
+            for (int k = 0; k < CELLS_PER_THREAD; ++k) {
+                const int c = own_cell<T>(k);
+                if (c < NCELL) {
+                    const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+                    const int cd = dir == 0 ? x : (dir == 1 ? y : z);
+                    const int step = dir == 0 ? 1 : (dir == 1 ? 8 : 64);
+                    const int line = dir == 0 ? c >> 3 : (dir == 1 ? x + 8 * z : c & 63);
+                    // flux at the cell's far face: the next cell's near face, or the line's far face
+                    const T* __restrict__ Fr = cd < TS - 1 ? sF + c + step : sFb + dir * 8 * TS * TS + line;
+                    const int sr = cd < TS - 1 ? NCELL : TS * TS;
 #pragma unroll
-                for (int v = 0; v < 7; ++v)
-                    rhs[k][v] -= (Fr[v * sr] - sF[v * NCELL + c]) * invh;
-                divu[k] += (Fr[7 * sr] - sF[7 * NCELL + c]) * invh;
+                    for (int v = 0; v < 7; ++v)
+                        rhs[k][v] -= (Fr[v * sr] - sF[v * NCELL + c]) * invh;
+                    divu[k] += (Fr[7 * sr] - sF[7 * NCELL + c]) * invh;
+                }
             }
         }
         __syncthreads();
     }
+}
+
+template <typename T, int ORD>
+__device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>& c, const T* __restrict__ sW,
+                                           T* __restrict__ sF, const int* __restrict__ sRow, TileRhs<T>& R) {
+    const T invh = T(1) / (T)c.bw.G->h;  // 1/h, formed as the FP64 reference forms it
+    if constexpr (std::is_same<T, float>::value && ORD == 5)
+        tile_faces_direct(P.eos, invh, sW, sF, sRow, R);
+    else
+        tile_faces_staged<T, ORD>(P.eos, invh, sW, sF, sRow, R);
 }
 
 // Pressure and raw alpha2 of this thread's cells (the alpha2 source term).
@@ -1247,40 +1332,40 @@ __device__ __forceinline__ void tile_update(const Params<T>& P, const TileCtx<T>
             const long long tile = tile_index - G.block0 - (long long)bw.s_local * G.tps;
             block_reduce_write(red_widen(red), G.part + (size_t)bw.s_local * G.tps + tile);
         }
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int k = 0; k < CELLS_PER_THREAD; ++k) {
-        const int c = own_cell<T>(k);
-        if (c < NCELL) {
-            const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-            const T p = pc[k];
-            const T a2raw = ac[k];
-            const T a2 = clamp01(a2raw);
-            const T a1 = T(1) - a2;
-            const T z1 = e.g1 * (p + e.pc1);  // rho_1 c_1^2
-            const T z2 = e.g2 * (p + e.pc2);  // rho_2 c_2^2
-            const T K = a1 * a2 * (z1 - z2) / (a1 * z2 + a2 * z1);
-            rhs[k][6] += (a2raw + K) * divu[k];
-            const size_t gi = ((size_t)(bw.z0 + z) * N + (bw.y0 + y)) * N + (bw.x0 + x);
-            T qn[7];
+        for (int k = 0; k < CELLS_PER_THREAD; ++k) {
+            const int c = own_cell<T>(k);
+            if (c < NCELL) {
+                const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+                const T p = pc[k];
+                const T a2raw = ac[k];
+                const T a2 = clamp01(a2raw);
+                const T a1 = T(1) - a2;
+                const T z1 = e.g1 * (p + e.pc1);  // rho_1 c_1^2
+                const T z2 = e.g2 * (p + e.pc2);  // rho_2 c_2^2
+                const T K = a1 * a2 * (z1 - z2) / (a1 * z2 + a2 * z1);
+                rhs[k][6] += (a2raw + K) * divu[k];
+                const size_t gi = ((size_t)(bw.z0 + z) * N + (bw.y0 + y)) * N + (bw.x0 + x);
+                T qn[7];
 #pragma unroll
-            for (int v = 0; v < 7; ++v) {
-                const T q = Qin[v * n3 + gi];
-                T d = dt * rhs[k][v];
-                if (STAGE > 0) d = A * dQ[v * n3 + gi] + d;
-                // the last stage's register is dead: the next step's first stage (A = 0)
-                // overwrites it without reading it
-                if (STAGE < 2) dQ[v * n3 + gi] = d;
-                qn[v] = q + B * d;
-                Qout[v * n3 + gi] = qn[v];
+                for (int v = 0; v < 7; ++v) {
+                    const T q = Qin[v * n3 + gi];
+                    T d = dt * rhs[k][v];
+                    if (STAGE > 0) d = A * dQ[v * n3 + gi] + d;
+                    // the last stage's register is dead: the next step's first stage (A = 0)
+                    // overwrites it without reading it
+                    if (STAGE < 2) dQ[v * n3 + gi] = d;
+                    qn[v] = q + B * d;
+                    Qout[v * n3 + gi] = qn[v];
+                }
+                if (STAGE == 2) red_cell(e, qn, (long long)gi, red);
             }
-            if (STAGE == 2) red_cell(e, qn, (long long)gi, red);
         }
-    }
-    if (STAGE == 2) {
-        const long long tile = tile_index - G.block0 - (long long)bw.s_local * G.tps;
-        block_reduce_write(red_widen(red), G.part + (size_t)bw.s_local * G.tps + tile);
+        if (STAGE == 2) {
+            const long long tile = tile_index - G.block0 - (long long)bw.s_local * G.tps;
+            block_reduce_write(red_widen(red), G.part + (size_t)bw.s_local * G.tps + tile);
+        }
     }
 }
 
@@ -1307,10 +1392,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
     int* sRow = reinterpret_cast<int*>(sF + NFLUX);  // [BX][BX] row offsets
     TileCtx<T> c;
     tile_ctx(P, blockIdx.x, parity, c);
-    if (P.s.done[c.bw.slot]) return;
+    // the finished-sample flag is read while the copies are issued (they only
+    // read the sample's own state); a finished tile returns once none is left
+    // in flight
+    const int done = P.s.done[c.bw.slot];
     tile_issue<T, STAGE>(P, c, sW);
     fill_rows(sRow);
     cp_async_wait_all();
+    if (done) return;
     __syncthreads();
     tile_convert(P.eos, sW);
     if (P.bc == OFM_BC_CHARACTERISTIC) {

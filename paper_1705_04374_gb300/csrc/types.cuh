@@ -17,7 +17,12 @@ constexpr int BX = TS + 2 * HALO;        // staged box edge (14)
 constexpr int NCELL = TS * TS * TS;      // 512 cells per tile
 constexpr int NSLAB = HALO * TS * TS;    // 192 cells per halo slab
 constexpr int NCROSS = TS * TS * 16 + 4 * NSLAB;  // 1792 staged slots (1664 cells + row padding)
-constexpr int NFLUX = 8 * NCELL + 3 * 8 * TS * TS;  // shared flux values: near faces of one direction + far faces of all three
+// Single-precision WENO5 accumulates per-cell flux differences in an
+// [8][RSTRIDE] array (slots permuted against bank conflicts) instead of
+// staging the near faces' fluxes.
+constexpr int RSTRIDE = NCELL;
+constexpr int NFAR = 3 * 8 * TS * TS;    // far faces of all three directions, 8 values each
+constexpr int NFLUX = (8 * RSTRIDE > 8 * NCELL ? 8 * RSTRIDE : 8 * NCELL) + NFAR;  // shared flux values
 constexpr int NT = 256;                  // threads per block (measured better than 192 and 256x2)
 constexpr int CELLS_PER_THREAD = (NCELL + NT - 1) / NT;  // 2
 constexpr int NEAR_RUN = 2;             // FP32: consecutive near faces per thread task (1: one face per task)
@@ -109,8 +114,9 @@ constexpr double RK_A[3] = {0.0, -2.915492524638791, -0.000000093517376};
 constexpr double RK_B[3] = {0.924574, 0.287713063186749, 0.626538109512740};
 
 // Stage-kernel dynamic shared memory: primitives of the staged cells, face
-// fluxes (near faces of one direction, far faces of all three) and the
-// staging layout's row-offset table
+// fluxes (near faces of one direction or, in single-precision WENO5, the
+// per-cell y + z flux differences; far faces of all three directions) and
+// the staging layout's row-offset table
 // (FP32: 73.5 KB, three blocks per SM; FP64: 146 KB, one).
 constexpr size_t smem_bytes(size_t elem) { return elem * (7 * NCROSS + NFLUX) + sizeof(int) * BX * BX; }
 
