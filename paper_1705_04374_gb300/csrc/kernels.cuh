@@ -972,17 +972,56 @@ __device__ __forceinline__ void tile_char_bc(const Params<T>& P, const BlockWork
     }
 }
 
-// Raw Q of every staged cell -> primitives, in place.
+// cons2prim of two cells at once in packed single precision.
+__device__ __forceinline__ void cons2prim2(const Eos<float>& e, const float2 (&q)[7], float2 (&w)[7]) {
+    const float2 rho = add2(q[0], q[1]);
+    const float2 ir = rcp2(rho);
+    const float2 u = mul2(q[2], ir), v = mul2(q[3], ir), ww = mul2(q[4], ir);
+    const float2 a = make_float2(clamp01(q[6].x), clamp01(q[6].y));
+    const float2 a1 = sub2(f2(1.0f), a);
+    const float2 G = fma2(a, f2(e.gi2), mul2(a1, f2(e.gi1)));
+    const float2 Pi = fma2(a, f2(e.pi2), mul2(a1, f2(e.pi1)));
+    const float2 ke = mul2(mul2(f2(0.5f), rho), fma2(u, u, fma2(v, v, mul2(ww, ww))));
+    w[0] = q[0];
+    w[1] = q[1];
+    w[2] = u;
+    w[3] = v;
+    w[4] = ww;
+    w[5] = mul2(sub2(sub2(q[5], ke), Pi), rcp2(G));
+    w[6] = q[6];
+}
+
+// Raw Q of every staged cell -> primitives, in place.  Single precision: four
+// consecutive slots of a row per thread with 16-byte shared-memory accesses,
+// as two packed pairs (row padding slots are converted too and never read).
 template <typename T>
 __device__ __forceinline__ void tile_convert(const Eos<T>& e, T* sW) {
-    for (int i = threadIdx.x; i < NCROSS; i += NT) {
-        if (pad_slot(i)) continue;
-        T q[7], w[7];
+    if constexpr (std::is_same<T, float>::value) {
+        for (int i4 = threadIdx.x; i4 < NCROSS / 4; i4 += NT) {
+            float4 q4[7];
 #pragma unroll
-        for (int v = 0; v < 7; ++v) q[v] = sW[v * NCROSS + i];
-        cons2prim(e, q, w);
+            for (int v = 0; v < 7; ++v) q4[v] = *reinterpret_cast<const float4*>(sW + v * NCROSS + 4 * i4);
+            float2 q[7], wa[7], wb[7];
 #pragma unroll
-        for (int v = 0; v < 7; ++v) sW[v * NCROSS + i] = w[v];
+            for (int v = 0; v < 7; ++v) q[v] = make_float2(q4[v].x, q4[v].y);
+            cons2prim2(e, q, wa);
+#pragma unroll
+            for (int v = 0; v < 7; ++v) q[v] = make_float2(q4[v].z, q4[v].w);
+            cons2prim2(e, q, wb);
+#pragma unroll
+            for (int v = 0; v < 7; ++v)
+                *reinterpret_cast<float4*>(sW + v * NCROSS + 4 * i4) = make_float4(wa[v].x, wa[v].y, wb[v].x, wb[v].y);
+        }
+    } else {
+        for (int i = threadIdx.x; i < NCROSS; i += NT) {
+            if (pad_slot(i)) continue;
+            T q[7], w[7];
+#pragma unroll
+            for (int v = 0; v < 7; ++v) q[v] = sW[v * NCROSS + i];
+            cons2prim(e, q, w);
+#pragma unroll
+            for (int v = 0; v < 7; ++v) sW[v * NCROSS + i] = w[v];
+        }
     }
 }
 
