@@ -58,7 +58,9 @@ enum { OFM_MODE_TOL = 0, OFM_MODE_BUDGET = 1 };           /* sample-number optim
 enum {
     OFM_ST_NONFINITE = 1, /* NaN/Inf in the state or pressure */
     OFM_ST_NEGATIVE = 2,  /* mixture density or squared sound speed <= 0 */
-    OFM_ST_MAXSTEPS = 4   /* step limit reached before t_end */
+    OFM_ST_MAXSTEPS = 4,  /* step limit reached before t_end */
+    OFM_ST_TIMEOUT = 8    /* a device-side wait for a tile's halo copies ran out
+                             (the sample is abandoned, the device stays usable) */
 };
 
 #define OFM_MAX_SENSORS 8

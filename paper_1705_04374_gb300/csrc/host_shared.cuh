@@ -5,6 +5,9 @@
 // the table or the record reaches both entry points.
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -15,6 +18,42 @@
 
 namespace ofm {
 namespace gpu {
+
+// The tensor maps of a group's two state buffers for the stage kernels'
+// halo staging: 4-D views (x, y, z, 7 sample + variable) of QA and QB, one
+// per staging box shape ([16, 8, 8], [8, 3, 8], [8, 8, 3] cells; the box of
+// the tile's rows starts four cells before the tile in x).  Encoded on the
+// host through the driver's cuTensorMapEncodeTiled (no allocation).
+inline int group_tensor_maps(GroupDev& G, size_t elem) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode) return ofm::fail(OFM_ECUDA, "the driver does not provide cuTensorMapEncodeTiled");
+    const cuuint64_t N = (cuuint64_t)G.N;
+    const cuuint64_t dims[4] = {N, N, N, 7ull * (cuuint64_t)G.n_samples};
+    const cuuint64_t strides[3] = {N * elem, N * N * elem, N * N * N * elem};
+    const cuuint32_t boxes[3][4] = {{(cuuint32_t)(TS + 8), TS, TS, 1}, {TS, HALO, TS, 1}, {TS, TS, HALO, 1}};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    void* bufs[2] = {G.QA, G.QB};
+    for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < 3; ++k) {
+            const CUresult r = encode(&G.tm[b][k],
+                                      elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                                      bufs[b], dims, strides, boxes[k], estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS)
+                return ofm::fail(OFM_ECUDA, "cuTensorMapEncodeTiled failed (%d) for N = %d, %d samples", (int)r, G.N,
+                                 G.n_samples);
+        }
+    return OFM_OK;
+}
 
 // Everything in Params that depends on the solver configuration only
 // (non-dimensional EOS constants, RK coefficients, boundary, WENO order,

@@ -238,8 +238,10 @@ __device__ __forceinline__ void hllc(const Eos<T>& e, const T* wl, const T* wr, 
 // row starting on a 16-byte boundary so that rows are copied 16 bytes at a
 // time.  Rows whose (y, z) both lie in the tile have RW = 16 slots holding
 // x = -4..11 (the stencils read x = -3..10; slots 0 and 15 are padding); rows
-// of the y- and z-halo slabs hold x = 0..7.  row_off(y, z) + x is the staged
-// index.
+// of the y- and z-halo slabs hold x = 0..7.  Each of the five regions (the
+// tile's rows, the low and high y slab, the low and high z slab) is one dense
+// box in (x, y, z) order, as a tensor copy lands it.  row_off(y, z) + x is
+// the staged index.
 constexpr int RW = 16;                                 // slots of a full-width row
 constexpr int XOFF = 4;                                // slot of x = 0 in a full-width row
 constexpr int ROWS_INT = TS * TS * RW;                 // 1024 slots in full-width rows
@@ -249,9 +251,9 @@ static_assert(ROWS_Y + 2 * HALO * TS * TS == NCROSS, "staging layout size");
 __device__ __forceinline__ int row_off(int y, int z) {
     const bool yi = (unsigned)y < (unsigned)TS, zi = (unsigned)z < (unsigned)TS;
     if (yi && zi) return (z * TS + y) * RW + XOFF;
-    if (zi) {
-        const int hy = y < 0 ? y + HALO : y - TS + HALO;  // 0..5
-        return ROWS_INT + (hy * TS + z) * TS;
+    if (zi) {   // y slab [z][y'][x], y' = 0..2 (low side: y = -3..-1, high side: y = 8..10)
+        const int side = y < 0 ? 0 : 1, hy = y < 0 ? y + HALO : y - TS;
+        return ROWS_INT + side * NSLAB + (z * HALO + hy) * TS;
     }
     const int hz = z < 0 ? z + HALO : z - TS + HALO;      // 0..5
     return ROWS_Y + (hz * TS + y) * TS;
@@ -837,6 +839,50 @@ __device__ __forceinline__ void prefetch_l2(const void* gmem, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
 }
 
+// Tensor-memory-accelerator copies (cp.async.bulk.tensor) completing on a
+// shared-memory mbarrier, and the barrier operations they need.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    // make the initialised barrier visible to the asynchronous proxy
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of bar (each try_wait may itself suspend
+// the thread for a while): false if it did not complete within the limit.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Per-tile context of one RK stage.  parity 0: read Q_a, write Q_b; 1: the reverse.
 template <typename T>
 struct TileCtx {
@@ -865,6 +911,19 @@ __device__ __forceinline__ void tile_ctx(const Params<T>& P, long long b, int pa
 // that read dQ, an L2 prefetch of the tile's own dQ rows.
 constexpr int NSEG_INT = TS * TS * 4;                 // full-width rows: 4 segments each
 constexpr int NSEG = NSEG_INT + 4 * HALO * TS * 2;     // + y and z halo rows: 2 each (448)
+
+// L2 prefetch of the tile's own dQ rows (stages that read dQ).
+template <typename T>
+__device__ __forceinline__ void tile_prefetch_dq(const TileCtx<T>& c) {
+    const BlockWork<T>& bw = c.bw;
+    const int N = bw.G->N;
+    const size_t n3 = (size_t)N * N * N;
+    for (int r = threadIdx.x; r < 7 * TS * TS; r += NT) {
+        const int v = r / (TS * TS), yz = r % (TS * TS);
+        const size_t gi = ((size_t)(bw.z0 + yz / TS) * N + (bw.y0 + yz % TS)) * N + bw.x0;
+        prefetch_l2(c.dQ + v * n3 + gi, TS * sizeof(T));
+    }
+}
 
 template <typename T, int STAGE>
 __device__ __forceinline__ void tile_issue(const Params<T>& P, const TileCtx<T>& c, T* sBuf) {
@@ -914,12 +973,62 @@ __device__ __forceinline__ void tile_issue(const Params<T>& P, const TileCtx<T>&
             }
         }
     }
-    if (STAGE > 0) {
-        for (int r = threadIdx.x; r < 7 * TS * TS; r += NT) {
-            const int v = r / (TS * TS), yz = r % (TS * TS);
-            const size_t gi = ((size_t)(bw.z0 + yz / TS) * N + (bw.y0 + yz % TS)) * N + bw.x0;
-            prefetch_l2(c.dQ + v * n3 + gi, TS * sizeof(T));
-        }
+    if (STAGE > 0) tile_prefetch_dq(c);
+}
+
+// The tile's halo'd box by tensor copies: per variable the tile's rows with
+// their x halos (x0 - 4 .. x0 + 11), the two y slabs and the two z slabs,
+// all completing on bar (7 NCROSS elements).  Issued by the lanes 0..6 of
+// one warp, lane v for variable v (lane 0 also posts the expected bytes;
+// the barrier's phase cannot complete before that arrival).  Boxes that
+// reach outside the domain are zero-filled there; the ghost cells are then
+// set by tile_clamp_ghosts.  (x0 - 4 and x0 are multiples of four elements,
+// so every box starts on a 16-byte boundary.)
+template <typename T>
+__device__ __forceinline__ void tile_issue_tma(const TileCtx<T>& c, int parity, T* sW, unsigned long long* bar,
+                                               int v) {
+    const BlockWork<T>& bw = c.bw;
+    const CUtensorMap* m = bw.G->tm[parity];
+    const int x0 = bw.x0, y0 = bw.y0, z0 = bw.z0, w = 7 * bw.s_local + v;
+    if (v == 0) mbar_expect_tx(bar, (unsigned)(7 * NCROSS * sizeof(T)));
+    T* d = sW + v * NCROSS;
+    tma_load_4d(d, &m[TMA_BOX_INT], x0 - XOFF, y0, z0, w, bar);
+    tma_load_4d(d + ROWS_INT, &m[TMA_BOX_YHALO], x0, y0 - HALO, z0, w, bar);
+    tma_load_4d(d + ROWS_INT + NSLAB, &m[TMA_BOX_YHALO], x0, y0 + TS, z0, w, bar);
+    tma_load_4d(d + ROWS_Y, &m[TMA_BOX_ZHALO], x0, y0, z0 - HALO, w, bar);
+    tma_load_4d(d + ROWS_Y + NSLAB, &m[TMA_BOX_ZHALO], x0, y0, z0 + TS, w, bar);
+}
+
+// Faces of the tile on the domain boundary (bit 2 axis + side).
+template <typename T>
+__device__ __forceinline__ unsigned boundary_faces(const BlockWork<T>& bw) {
+    const int N = bw.G->N;
+    return (bw.x0 == 0 ? 1u : 0u) | (bw.x0 + TS == N ? 2u : 0u) | (bw.y0 == 0 ? 4u : 0u) |
+           (bw.y0 + TS == N ? 8u : 0u) | (bw.z0 == 0 ? 16u : 0u) | (bw.z0 + TS == N ? 32u : 0u);
+}
+
+// Ghost cells of a tile on the domain boundary after tensor staging (the
+// transmissive map: every ghost takes the value of the boundary cell on its
+// line), copied from the staged boundary cells; `on` from boundary_faces.
+template <typename T>
+__device__ __forceinline__ void tile_clamp_ghosts(unsigned on, T* sW) {
+    constexpr int PER = HALO * TS * TS;
+    const int n_on = __popc(on);
+    for (int u = threadIdx.x; u < n_on * PER; u += NT) {
+        const int q = u / PER, r = u - q * PER;
+        unsigned rest = on;   // face = the q-th set bit of on
+        for (int i = 0; i < q; ++i) rest &= rest - 1;
+        const int face = __ffs(rest) - 1;
+        const int axis = face >> 1, hi = face & 1;
+        const int layer = r / (TS * TS), a = (r / TS) % TS, b = r % TS;
+        const int off = hi ? TS + layer : -1 - layer, edge = hi ? TS - 1 : 0;
+        const int x = axis == 0 ? off : b;
+        const int y = axis == 1 ? off : (axis == 0 ? b : a);
+        const int z = axis == 2 ? off : a;
+        const int dst = row_off(y, z) + x;
+        const int src = row_off(axis == 1 ? edge : y, axis == 2 ? edge : z) + (axis == 0 ? edge : x);
+#pragma unroll
+        for (int v = 0; v < 7; ++v) sW[v * NCROSS + dst] = sW[v * NCROSS + src];
     }
 }
 
@@ -1425,15 +1534,18 @@ __device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& 
 template <typename T, int STAGE, int ORD>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
     stage_kernel(const __grid_constant__ Params<T> P, int parity) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sW = reinterpret_cast<T*>(smem_raw);  // [7][NCROSS] primitives, compact layout
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // [7][NCROSS] primitives (staged as raw Q)
+    T* sW = reinterpret_cast<T*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     T* sF = sW + 7 * NCROSS;                 // face fluxes + face velocities (NFLUX)
     int* sRow = reinterpret_cast<int*>(sF + NFLUX);  // [BX][BX] row offsets
     TileCtx<T> c;
     tile_ctx(P, blockIdx.x, parity, c);
     // the finished-sample flag is read while the copies are issued (they only
     // read the sample's own state); a finished tile returns once none is left
-    // in flight
+    // in flight.  (Staging by tensor copies measured 0.6-1 % slower here: one
+    // launch keeps three tiles per SM in flight either way, and the per-row
+    // copies need no barrier set-up; the persistent variant uses them.)
     const int done = P.s.done[c.bw.slot];
     tile_issue<T, STAGE>(P, c, sW);
     fill_rows(sRow);
@@ -1449,70 +1561,96 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
     tile_body<T, STAGE, ORD>(P, c, (long long)blockIdx.x, sW, sF, sRow);
 }
 
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// First tile at or after t (stepping by stride) whose sample is not finished.
-template <typename T>
-__device__ __forceinline__ long long next_active(const Params<T>& P, long long t, long long stride) {
-    while (t < P.total_blocks) {
-        int gi = 0;
-        while (gi + 1 < P.n_groups && t >= P.g[gi + 1].block0) ++gi;
-        const GroupDev& G = P.g[gi];
-        const int slot = G.slot0 + (int)((t - G.block0) / G.tps);
-        if (!P.s.done[slot]) return t;
-        t += stride;
-    }
-    return t;
-}
-
 // One RK stage, persistent blocks (three per SM in single precision, one
 // staging buffer each): each block walks tiles blockIdx.x, blockIdx.x +
-// gridDim.x, ... (finished samples skipped without a launch).  Once a tile's
-// faces are done and its pressure and alpha2 are in registers, the block
-// issues the next tile's halo copies and then performs the current tile's
-// update, so the update's global loads and the next tile's copies are in
-// flight together.  Same arithmetic as stage_kernel.
+// gridDim.x, ...  Once a tile's faces are done and its pressure and alpha2
+// are in registers, one thread issues the next tile's tensor copies into the
+// staging buffer and the block then performs the current tile's update, so
+// the update's global loads and stores overlap the next tile's copies.
+// Finished samples' tiles are staged but not computed.  Same arithmetic as
+// stage_kernel.  (Periodic boundaries: per-row cp.async staging, the next
+// tile's copies issued the same way.)
 template <typename T, int STAGE, int ORD>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
     stage_kernel_persistent(const __grid_constant__ Params<T> P, int parity) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sW = reinterpret_cast<T*>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long s_bar;
+    T* sW = reinterpret_cast<T*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     T* sF = sW + 7 * NCROSS;
     int* sRow = reinterpret_cast<int*>(sF + NFLUX);
+    const bool tma = P.bc != OFM_BC_PERIODIC;
     fill_rows(sRow);
+    if (tma && threadIdx.x == 0) mbar_init(&s_bar, 1);
+    __syncthreads();   // the barrier is initialised before any thread waits on it
     const long long stride = gridDim.x;
-    long long t = next_active(P, (long long)blockIdx.x, stride);
-    TileCtx<T> c;
+    long long t = blockIdx.x;
+    int done = 1;
     if (t < P.total_blocks) {
+        TileCtx<T> c;
         tile_ctx(P, t, parity, c);
-        tile_issue<T, STAGE>(P, c, sW);
+        done = P.s.done[c.bw.slot];
+        if (!tma)
+            tile_issue<T, STAGE>(P, c, sW);
+        else if (threadIdx.x < 7)
+            tile_issue_tma(c, parity, sW, &s_bar, (int)threadIdx.x);
     }
+    unsigned phase = 0;
     while (t < P.total_blocks) {
-        cp_async_wait_all();
-        __syncthreads();
-        tile_convert(P.eos, sW);
-        if (P.bc == OFM_BC_CHARACTERISTIC) {
-            __syncthreads();
-            tile_char_bc(P, c.bw, sW);
-        }
-        __syncthreads();
         TileRhs<T> R;
-        tile_faces<T, ORD>(P, c, sW, sF, sRow, R);
         T pc[CELLS_PER_THREAD], ac[CELLS_PER_THREAD];
-        tile_cell_pa(sW, pc, ac);
-        __syncthreads();   // every read of sW is done
-        const long long tn = next_active(P, t + stride, stride);
-        TileCtx<T> cn;
-        if (tn < P.total_blocks) {
-            tile_ctx(P, tn, parity, cn);
-            tile_issue<T, STAGE>(P, cn, sW);
+        {
+            TileCtx<T> c;
+            tile_ctx(P, t, parity, c);
+            if (tma) {
+                if (STAGE > 0 && !done) tile_prefetch_dq(c);
+                const bool ok = mbar_wait_bounded(&s_bar, phase);
+                if (__syncthreads_or(!ok)) {   // a wait ran out: abandon the sample, leave the device usable
+                    if (threadIdx.x == 0) atomicOr(&P.s.qoi[c.bw.slot].status, OFM_ST_TIMEOUT);
+                    return;
+                }
+                phase ^= 1u;
+                if (!done) tile_clamp_ghosts(boundary_faces(c.bw), sW);
+            } else {
+                cp_async_wait_all();
+            }
+            if (!done) {
+                __syncthreads();
+                tile_convert(P.eos, sW);
+                if (P.bc == OFM_BC_CHARACTERISTIC) {
+                    __syncthreads();
+                    tile_char_bc(P, c.bw, sW);
+                }
+                __syncthreads();
+                tile_faces<T, ORD>(P, c, sW, sF, sRow, R);
+                tile_cell_pa(sW, pc, ac);
+            }
         }
-        tile_update<T, STAGE>(P, c, t, R, pc, ac);
+        __syncthreads();   // every read of sW is done
+        // the tile's context is formed again below rather than kept in registers through the faces
+        asm volatile("" : "+l"(t));
+        const long long tn = t + stride;
+        int done_n = 1;
+        if (tn < P.total_blocks) {
+            TileCtx<T> cn;
+            tile_ctx(P, tn, parity, cn);
+            done_n = P.s.done[cn.bw.slot];
+            if (!tma) {
+                tile_issue<T, STAGE>(P, cn, sW);
+            } else if (threadIdx.x < 7) {
+                // the block's generic-proxy accesses of sW come before the copies' writes
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                tile_issue_tma(cn, parity, sW, &s_bar, (int)threadIdx.x);
+            }
+        }
+        if (!done) {
+            TileCtx<T> c;
+            tile_ctx(P, t, parity, c);
+            tile_update<T, STAGE>(P, c, t, R, pc, ac);
+        }
         t = tn;
-        c = cn;
+        done = done_n;
     }
-    cp_async_wait_all();
+    if (!tma) cp_async_wait_all();
 }
 
 // Pressure at one cell of a stored state (sensor evaluation).

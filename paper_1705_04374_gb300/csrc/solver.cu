@@ -394,11 +394,15 @@ extern "C" int ofm_batch_create(ofm_batch** out, ofm_solver* s, const ofm_cloud_
     b->active_mask = 0;
     if (b->precision == OFM_FP64) {
         fill_params(b, b->pd);
+        for (int g = 0; g < b->n_groups; ++g)
+            if ((rc = group_tensor_maps(b->pd.g[g], sizeof(double))) != OFM_OK) return bail(rc);
         b->pd_s = b->pd;
         b->total_blocks = b->pd.total_blocks;
         if ((rc = set_smem_attrs<double>()) != OFM_OK) return bail(rc);
     } else {
         fill_params(b, b->pf);
+        for (int g = 0; g < b->n_groups; ++g)
+            if ((rc = group_tensor_maps(b->pf.g[g], sizeof(float))) != OFM_OK) return bail(rc);
         b->pf_s = b->pf;
         b->total_blocks = b->pf.total_blocks;
         if ((rc = set_smem_attrs<float>()) != OFM_OK) return bail(rc);

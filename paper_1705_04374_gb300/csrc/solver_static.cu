@@ -152,7 +152,9 @@ int run_static(const ofm_solver* s, int N, int M, int nb, unsigned char* ws, con
                const int* sens_off, cudaStream_t st) {
     Params<T> P;
     static_params(s, N, M, nb, ws, L, sens_off, P);
-    int rc = set_smem_attrs<T>();
+    int rc = group_tensor_maps(P.g[0], sizeof(T));
+    if (rc != OFM_OK) return rc;
+    rc = set_smem_attrs<T>();
     if (rc != OFM_OK) return rc;
     long long launches = 0;
     rc = launch_init(P, st, true, &launches);

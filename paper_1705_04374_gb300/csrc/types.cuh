@@ -1,6 +1,7 @@
 // Types shared by the host API and the per-precision kernel translation units.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the staging tensor maps of the state buffers)
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -65,7 +66,14 @@ struct DevQoi {           // per-sample record, non-dimensional
     double sensor_alpha_min_t[OFM_MAX_SENSORS];  // and the first time of it
 };
 
+// Box shapes of the halo staging by the tensor memory accelerator (x extent
+// first): the tile's rows with their x halos, a y-halo slab, a z-halo slab.
+constexpr int TMA_BOX_INT = 0, TMA_BOX_YHALO = 1, TMA_BOX_ZHALO = 2;
+
 struct GroupDev {
+    // tm[b][k]: 4-D tiled view (x, y, z, 7 sample + variable) of state buffer
+    // b (0: QA, 1: QB) with box shape k
+    CUtensorMap tm[2][3];
     int N, tpd, tps, n_samples, slot0;
     long long block0;     // first block of this group in the flattened tile grid
     void* QA;
@@ -118,7 +126,9 @@ constexpr double RK_B[3] = {0.924574, 0.287713063186749, 0.626538109512740};
 // per-cell y + z flux differences; far faces of all three directions) and
 // the staging layout's row-offset table
 // (FP32: 73.5 KB, three blocks per SM; FP64: 146 KB, one).
-constexpr size_t smem_bytes(size_t elem) { return elem * (7 * NCROSS + NFLUX) + sizeof(int) * BX * BX; }
+// (+128 bytes: the kernels align the staging buffer to 128 bytes for the
+// tensor copies.)
+constexpr size_t smem_bytes(size_t elem) { return elem * (7 * NCROSS + NFLUX) + sizeof(int) * BX * BX + 128; }
 
 // Stage-kernel variants: one block per tile, or persistent blocks that issue
 // the next tile's copies before the current tile's update.

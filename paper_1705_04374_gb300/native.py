@@ -18,7 +18,7 @@ OFM_FP64, OFM_FP32 = 0, 1
 OFM_BC_TRANSMISSIVE, OFM_BC_PERIODIC, OFM_BC_CHARACTERISTIC = 0, 1, 2
 OFM_RADII_UNIFORM, OFM_RADII_LOGNORMAL = 0, 1
 OFM_MODE_TOL, OFM_MODE_BUDGET = 0, 1
-OFM_ST_NONFINITE, OFM_ST_NEGATIVE, OFM_ST_MAXSTEPS = 1, 2, 4
+OFM_ST_NONFINITE, OFM_ST_NEGATIVE, OFM_ST_MAXSTEPS, OFM_ST_TIMEOUT = 1, 2, 4, 8
 OFM_MAX_SENSORS, OFM_MAX_GROUPS, OFM_MAX_LEVELS = 8, 8, 16
 OFM_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 
