@@ -240,28 +240,91 @@ __device__ __forceinline__ void hllc(const Eos<T>& e, const T* wl, const T* wr, 
 // x = -4..11 (the stencils read x = -3..10; slots 0 and 15 are padding); rows
 // of the y- and z-halo slabs hold x = 0..7.  Each of the five regions (the
 // tile's rows, the low and high y slab, the low and high z slab) is one dense
-// box in (x, y, z) order, as a tensor copy lands it.  row_off(y, z) + x is
-// the staged index.
+// box in (x, y, z) order in the dense layout (stage_slot has both layouts).
 constexpr int RW = 16;                                 // slots of a full-width row
 constexpr int XOFF = 4;                                // slot of x = 0 in a full-width row
 constexpr int ROWS_INT = TS * TS * RW;                 // 1024 slots in full-width rows
 constexpr int ROWS_Y = ROWS_INT + 2 * HALO * TS * TS;  // start of z-halo rows (1408)
 static_assert(ROWS_Y + 2 * HALO * TS * TS == NCROSS, "staging layout size");
 
-__device__ __forceinline__ int row_off(int y, int z) {
+// Two layouts of the same regions.  LAYOUT_DENSE: every region one dense
+// box (the tensor copies of the persistent variant land it so).
+// LAYOUT_SWZ (the default kernel, staged by per-row cp.async): the 16-byte
+// chunks of each 32-slot group of the tile's rows are XOR-permuted by a
+// linear function of the group index (rows_xor), and each 16-byte chunk of
+// the halo slabs has its own place (c_slab), so that the stencil loads of the
+// face runs and far faces spread over the shared-memory banks (a search over
+// the kernel's access patterns: 327 instead of 864 wavefronts per tile and
+// variable; the x runs, whose lanes read cells of one parity, stay two-way).
+// Chunks stay whole and 16-byte aligned, so every copy is unchanged in size.
+constexpr int LAYOUT_DENSE = 0, LAYOUT_SWZ = 1;
+
+// XOR mask (in slots) of tile row `row` = z TS + y: bits 2-4 from the XOR of
+// (1, 6, 4, 1, 4) over the set bits of row >> 1.
+__device__ __forceinline__ int rows_xor(int row) {
+    const int g = row >> 1;
+    const int s = ((g & 1) ? 1 : 0) ^ ((g & 2) ? 6 : 0) ^ ((g & 4) ? 4 : 0) ^ ((g & 8) ? 1 : 0) ^ ((g & 16) ? 4 : 0);
+    return s << 2;
+}
+
+// Slot offsets of the halo slabs' chunks in LAYOUT_SWZ, [y slab, z slab][((side
+// 3 + layer) 8 + other coordinate) 2 + half], half = x >> 2.
+__constant__ short c_slab[2][96] = {
+    {
+        0, 12, 16, 28, 4, 8, 20, 24, 48, 60, 44, 32, 64, 40, 36, 72,
+        56, 52, 68, 104, 88, 76, 108, 96, 136, 100, 120, 84, 128, 140, 80, 92,
+        168, 132, 152, 116, 172, 160, 112, 124, 184, 148, 164, 200, 156, 144, 192, 204,
+        196, 232, 180, 216, 264, 228, 188, 176, 248, 212, 244, 208, 236, 280, 260, 296,
+        312, 276, 240, 224, 220, 272, 268, 256, 328, 292, 324, 288, 304, 252, 336, 284,
+        316, 308, 300, 320, 344, 348, 340, 332, 352, 380, 372, 356, 360, 364, 376, 368,
+    },
+    {
+        4, 8, 20, 24, 28, 16, 0, 56, 48, 60, 12, 32, 64, 40, 44, 92,
+        96, 88, 128, 76, 120, 52, 72, 36, 68, 104, 152, 84, 100, 184, 116, 136,
+        160, 108, 124, 80, 168, 132, 164, 200, 148, 216, 196, 232, 156, 112, 248, 180,
+        188, 212, 280, 244, 144, 264, 220, 176, 252, 208, 140, 192, 312, 276, 228, 296,
+        240, 172, 328, 260, 284, 272, 224, 204, 236, 256, 316, 304, 288, 268, 308, 344,
+        292, 340, 348, 324, 300, 332, 336, 320, 356, 368, 380, 360, 352, 376, 364, 372,
+    }};
+
+// Staged slot of cell (x, y, z) of the tile and its halo (no corners): x in
+// -4..11 for the tile's rows, 0..7 for the slab rows.
+template <int LAYOUT>
+__device__ __forceinline__ int stage_slot(int x, int y, int z) {
     const bool yi = (unsigned)y < (unsigned)TS, zi = (unsigned)z < (unsigned)TS;
-    if (yi && zi) return (z * TS + y) * RW + XOFF;
-    if (zi) {   // y slab [z][y'][x], y' = 0..2 (low side: y = -3..-1, high side: y = 8..10)
-        const int side = y < 0 ? 0 : 1, hy = y < 0 ? y + HALO : y - TS;
-        return ROWS_INT + side * NSLAB + (z * HALO + hy) * TS;
+    if (yi && zi) {
+        const int row = z * TS + y;
+        const int s = row * RW + XOFF + x;
+        return LAYOUT == LAYOUT_SWZ ? s ^ rows_xor(row) : s;
     }
-    const int hz = z < 0 ? z + HALO : z - TS + HALO;      // 0..5
-    return ROWS_Y + (hz * TS + y) * TS;
+    if (zi) {   // y slab, layer y' = 0..2 (low side: y = -3..-1, high side: y = 8..10)
+        const int side = y < 0 ? 0 : 1, hy = y < 0 ? y + HALO : y - TS;
+        if (LAYOUT == LAYOUT_SWZ) return ROWS_INT + c_slab[0][((side * HALO + hy) * TS + z) * 2 + (x >> 2)] + (x & 3);
+        return ROWS_INT + side * NSLAB + (z * HALO + hy) * TS + x;
+    }
+    const int side = z < 0 ? 0 : 1, hz = z < 0 ? z + HALO : z - TS;
+    if (LAYOUT == LAYOUT_SWZ) return ROWS_Y + c_slab[1][((side * HALO + hz) * TS + y) * 2 + (x >> 2)] + (x & 3);
+    return ROWS_Y + side * NSLAB + (hz * TS + y) * TS + x;
 }
 
 // Staged slot i in [0, NCROSS) that holds no stencil cell (row padding).
+template <int LAYOUT>
 __device__ __forceinline__ bool pad_slot(int i) {
-    return i < ROWS_INT && ((i & (RW - 1)) == 0 || (i & (RW - 1)) == RW - 1);
+    if (i >= ROWS_INT) return false;
+    const int u = LAYOUT == LAYOUT_SWZ ? i ^ rows_xor((i >> 5) << 1) : i;   // one mask per 32-slot group
+    return (u & (RW - 1)) == 0 || (u & (RW - 1)) == RW - 1;
+}
+
+// The per-row table: sRows[(z + HALO) BX + y + HALO] = (slot of x = 0, slot
+// of x = 4) of row (y, z).  slot_lo: cells x = 0..7 of any row; slot_x:
+// cells x = -4..11 of a tile row (its slots are the dense ones XOR one mask).
+__device__ __forceinline__ int slot_lo(const int2* __restrict__ sRows, int y, int z, int x) {
+    const int* t = reinterpret_cast<const int*>(sRows) + 2 * ((z + HALO) * BX + y + HALO);
+    return t[x >> 2] + (x & 3);
+}
+__device__ __forceinline__ int row_xmask(const int2* __restrict__ sRows, int y, int z, int& base) {
+    base = (z * TS + y) * RW + XOFF;
+    return sRows[(z + HALO) * BX + y + HALO].x ^ base;
 }
 
 __device__ __forceinline__ int bc_map(int g, int N, int bc) {
@@ -925,7 +988,7 @@ __device__ __forceinline__ void tile_prefetch_dq(const TileCtx<T>& c) {
     }
 }
 
-template <typename T, int STAGE>
+template <typename T, int STAGE, int LAYOUT>
 __device__ __forceinline__ void tile_issue(const Params<T>& P, const TileCtx<T>& c, T* sBuf) {
     const BlockWork<T>& bw = c.bw;
     const int N = bw.G->N;
@@ -955,7 +1018,7 @@ __device__ __forceinline__ void tile_issue(const Params<T>& P, const TileCtx<T>&
         const int gy = bc_map(bw.y0 + by, N, bc);
         const int gz = bc_map(bw.z0 + bz, N, bc);
         const size_t grow = ((size_t)gz * N + gy) * N;
-        const int si = row_off(by, bz) + bx0;
+        const int si = stage_slot<LAYOUT>(bx0, by, bz);   // a 16-byte chunk: its 4 cells consecutive
         const int gx0 = bw.x0 + bx0;
         if (gx0 >= 0 && gx0 + 4 <= N) {
 #pragma unroll
@@ -1010,6 +1073,7 @@ __device__ __forceinline__ unsigned boundary_faces(const BlockWork<T>& bw) {
 // Ghost cells of a tile on the domain boundary after tensor staging (the
 // transmissive map: every ghost takes the value of the boundary cell on its
 // line), copied from the staged boundary cells; `on` from boundary_faces.
+// (Tensor staging lands the dense layout.)
 template <typename T>
 __device__ __forceinline__ void tile_clamp_ghosts(unsigned on, T* sW) {
     constexpr int PER = HALO * TS * TS;
@@ -1025,18 +1089,19 @@ __device__ __forceinline__ void tile_clamp_ghosts(unsigned on, T* sW) {
         const int x = axis == 0 ? off : b;
         const int y = axis == 1 ? off : (axis == 0 ? b : a);
         const int z = axis == 2 ? off : a;
-        const int dst = row_off(y, z) + x;
-        const int src = row_off(axis == 1 ? edge : y, axis == 2 ? edge : z) + (axis == 0 ? edge : x);
+        const int dst = stage_slot<LAYOUT_DENSE>(x, y, z);
+        const int src = stage_slot<LAYOUT_DENSE>(axis == 0 ? edge : x, axis == 1 ? edge : y, axis == 2 ? edge : z);
 #pragma unroll
         for (int v = 0; v < 7; ++v) sW[v * NCROSS + dst] = sW[v * NCROSS + src];
     }
 }
 
-__device__ __forceinline__ void fill_rows(int* sRow) {
+template <int LAYOUT>
+__device__ __forceinline__ void fill_rows(int2* sRows) {
     for (int i = threadIdx.x; i < BX * BX; i += NT) {
         const int y = i % BX - HALO, z = i / BX - HALO;
         const bool yi = (unsigned)y < (unsigned)TS, zi = (unsigned)z < (unsigned)TS;
-        sRow[i] = (yi || zi) ? row_off(y, z) : -1;
+        sRows[i] = (yi || zi) ? make_int2(stage_slot<LAYOUT>(0, y, z), stage_slot<LAYOUT>(4, y, z)) : make_int2(-1, -1);
     }
 }
 
@@ -1062,7 +1127,7 @@ __device__ __forceinline__ void char_ghost(const Eos<T>& e, T pinf, T kappa, T* 
 // The characteristic ghosts of a tile: the three halo layers behind each
 // tile face that lies on a domain face (ghosts outside along one axis only,
 // the only ones a stencil reads; every layer takes the same state).
-template <typename T>
+template <typename T, int LAYOUT>
 __device__ __forceinline__ void tile_char_bc(const Params<T>& P, const BlockWork<T>& bw, T* sW) {
     const int N = bw.G->N;
     const T pinf = (T)P.p_liq, kappa = (T)P.bc_penalty;
@@ -1077,7 +1142,7 @@ __device__ __forceinline__ void tile_char_bc(const Params<T>& P, const BlockWork
         const int x = axis == 0 ? off : b;
         const int y = axis == 1 ? off : (axis == 0 ? b : a);
         const int z = axis == 2 ? off : a;
-        char_ghost(P.eos, pinf, kappa, sW, row_off(y, z) + x, axis, hi ? T(1) : T(-1));
+        char_ghost(P.eos, pinf, kappa, sW, stage_slot<LAYOUT>(x, y, z), axis, hi ? T(1) : T(-1));
     }
 }
 
@@ -1103,7 +1168,7 @@ __device__ __forceinline__ void cons2prim2(const Eos<float>& e, const float2 (&q
 // Raw Q of every staged cell -> primitives, in place.  Single precision: four
 // consecutive slots of a row per thread with 16-byte shared-memory accesses,
 // as two packed pairs (row padding slots are converted too and never read).
-template <typename T>
+template <typename T, int LAYOUT>
 __device__ __forceinline__ void tile_convert(const Eos<T>& e, T* sW) {
     if constexpr (std::is_same<T, float>::value) {
         for (int i4 = threadIdx.x; i4 < NCROSS / 4; i4 += NT) {
@@ -1123,7 +1188,7 @@ __device__ __forceinline__ void tile_convert(const Eos<T>& e, T* sW) {
         }
     } else {
         for (int i = threadIdx.x; i < NCROSS; i += NT) {
-            if (pad_slot(i)) continue;
+            if (pad_slot<LAYOUT>(i)) continue;
             T q[7], w[7];
 #pragma unroll
             for (int v = 0; v < 7; ++v) q[v] = sW[v * NCROSS + i];
@@ -1190,16 +1255,21 @@ struct TileRhs {
 // direction, all three directions), its 8 values (staged variable order) to
 // sFb[dir][v][line].
 template <typename T, int ORD>
-__device__ __forceinline__ void far_faces(const Eos<T>& e, const T* __restrict__ sW, const int* __restrict__ sRow,
+__device__ __forceinline__ void far_faces(const Eos<T>& e, const T* __restrict__ sW, const int2* __restrict__ sRows,
                                           T* __restrict__ sFb) {
     for (int f = threadIdx.x; f < 3 * TS * TS; f += NT) {
         const int dir = f >> 6, line = f & 63, a = line & 7, b = line >> 3;
         int i6[6];
+        if (dir == 0) {
+            int base;
+            const int m = row_xmask(sRows, a, b, base);
 #pragma unroll
-        for (int k = 0; k < 6; ++k)
-            i6[k] = dir == 0 ? sRow[(b + HALO) * BX + a + HALO] + TS - 3 + k
-                             : (dir == 1 ? sRow[(b + HALO) * BX + TS - 3 + k + HALO] + a
-                                         : sRow[(TS - 3 + k + HALO) * BX + b + HALO] + a);
+            for (int k = 0; k < 6; ++k) i6[k] = (base + TS - 3 + k) ^ m;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                i6[k] = dir == 1 ? slot_lo(sRows, TS - 3 + k, b, a) : slot_lo(sRows, b, TS - 3 + k, a);
+        }
         face_store<T, ORD>(e, sW, i6, dir, sFb + dir * 8 * TS * TS + line, TS * TS);
     }
 }
@@ -1223,11 +1293,11 @@ __device__ __forceinline__ int rslot(int c) { return c ^ ((((c >> 7) & 3) ^ ((c 
 // differences in registers to the array's y + z sum.  Three barriers per tile
 // instead of seven.
 __device__ __forceinline__ void tile_faces_direct(const Eos<float>& e, float invh, const float* __restrict__ sW,
-                                                  float* __restrict__ sF, const int* __restrict__ sRow,
+                                                  float* __restrict__ sF, const int2* __restrict__ sRows,
                                                   TileRhs<float>& R) {
     float* __restrict__ sR = sF;                   // [8][RSTRIDE]: y + z contributions per cell
     float* __restrict__ sFb = sF + 8 * RSTRIDE;    // [3][8][64]: far faces
-    far_faces<float, 5>(e, sW, sRow, sFb);
+    far_faces<float, 5>(e, sW, sRows, sFb);
     __syncthreads();
     const int t = threadIdx.x;
 #pragma unroll 1
@@ -1244,11 +1314,16 @@ __device__ __forceinline__ void tile_faces_direct(const Eos<float>& e, float inv
             b = t >> 5;
         }
         int idx[7];
+        if (dir == 0) {
+            int base;
+            const int m = row_xmask(sRows, a, b, base);
 #pragma unroll
-        for (int i = 0; i < 7; ++i)
-            idx[i] = dir == 0 ? sRow[(b + HALO) * BX + a + HALO] + j - 3 + i
-                              : (dir == 1 ? sRow[(b + HALO) * BX + j - 3 + i + HALO] + a
-                                          : sRow[(j - 3 + i + HALO) * BX + b + HALO] + a);
+            for (int i = 0; i < 7; ++i) idx[i] = (base + j - 3 + i) ^ m;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 7; ++i)
+                idx[i] = dir == 1 ? slot_lo(sRows, j - 3 + i, b, a) : slot_lo(sRows, b, j - 3 + i, a);
+        }
         const int r1 = dir == 0 ? 3 : (dir == 1 ? 4 : 2);   // staged variable of the first tangential velocity
         const int r2 = dir == 0 ? 4 : (dir == 1 ? 2 : 3);   // and of the second
         const int vo[7] = {0, NCROSS, (2 + dir) * NCROSS, r1 * NCROSS, r2 * NCROSS, 5 * NCROSS, 6 * NCROSS};
@@ -1312,7 +1387,7 @@ __device__ __forceinline__ void tile_faces_direct(const Eos<float>& e, float inv
 // direction into sF, a barrier, the per-cell differences, a barrier.
 template <typename T, int ORD>
 __device__ __forceinline__ void tile_faces_staged(const Eos<T>& e, T invh, const T* __restrict__ sW,
-                                                  T* __restrict__ sF, const int* __restrict__ sRow, TileRhs<T>& R) {
+                                                  T* __restrict__ sF, const int2* __restrict__ sRows, TileRhs<T>& R) {
     T (&divu)[CELLS_PER_THREAD] = R.divu;
     T (&rhs)[CELLS_PER_THREAD][7] = R.rhs;
 #pragma unroll
@@ -1327,17 +1402,22 @@ __device__ __forceinline__ void tile_faces_staged(const Eos<T>& e, T invh, const
     // of every cell (512, two per thread) into sF, so that every barrier
     // interval holds the same number of faces per thread.
     T* __restrict__ sFb = sF + 8 * NCELL;   // [3][8][64]
-    far_faces<T, ORD>(e, sW, sRow, sFb);
+    far_faces<T, ORD>(e, sW, sRows, sFb);
 #pragma unroll 1
     for (int dir = 0; dir < 3; ++dir) {
         for (int c = threadIdx.x; c < NCELL; c += NT) {
             const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
             int i6[6];
+            if (dir == 0) {
+                int base;
+                const int m = row_xmask(sRows, y, z, base);
 #pragma unroll
-            for (int k = 0; k < 6; ++k)
-                i6[k] = dir == 0 ? sRow[(z + HALO) * BX + y + HALO] + x - 3 + k
-                                 : (dir == 1 ? sRow[(z + HALO) * BX + y - 3 + k + HALO] + x
-                                             : sRow[(z - 3 + k + HALO) * BX + y + HALO] + x);
+                for (int k = 0; k < 6; ++k) i6[k] = (base + x - 3 + k) ^ m;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+                    i6[k] = dir == 1 ? slot_lo(sRows, y - 3 + k, z, x) : slot_lo(sRows, y, z - 3 + k, x);
+            }
             face_store<T, ORD>(e, sW, i6, dir, sF + c, NCELL);
         }
         __syncthreads();
@@ -1397,24 +1477,24 @@ __device__ __forceinline__ void tile_faces_staged(const Eos<T>& e, T invh, const
 
 template <typename T, int ORD>
 __device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>& c, const T* __restrict__ sW,
-                                           T* __restrict__ sF, const int* __restrict__ sRow, TileRhs<T>& R) {
+                                           T* __restrict__ sF, const int2* __restrict__ sRows, TileRhs<T>& R) {
     const T invh = T(1) / (T)c.bw.G->h;  // 1/h, formed as the FP64 reference forms it
     if constexpr (std::is_same<T, float>::value && ORD == 5)
-        tile_faces_direct(P.eos, invh, sW, sF, sRow, R);
+        tile_faces_direct(P.eos, invh, sW, sF, sRows, R);
     else
-        tile_faces_staged<T, ORD>(P.eos, invh, sW, sF, sRow, R);
+        tile_faces_staged<T, ORD>(P.eos, invh, sW, sF, sRows, R);
 }
 
 // Pressure and raw alpha2 of this thread's cells (the alpha2 source term).
 template <typename T>
-__device__ __forceinline__ void tile_cell_pa(const T* __restrict__ sW, T (&pc)[CELLS_PER_THREAD],
-                                             T (&ac)[CELLS_PER_THREAD]) {
+__device__ __forceinline__ void tile_cell_pa(const T* __restrict__ sW, const int2* __restrict__ sRows,
+                                             T (&pc)[CELLS_PER_THREAD], T (&ac)[CELLS_PER_THREAD]) {
 #pragma unroll
     for (int k = 0; k < CELLS_PER_THREAD; ++k) {
         const int c = own_cell<T>(k);
         if (c < NCELL) {
             const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-            const int si = (z * TS + y) * RW + XOFF + x;   // row_off(y, z) + x for tile cells
+            const int si = slot_lo(sRows, y, z, x);
             pc[k] = sW[5 * NCROSS + si];
             ac[k] = sW[6 * NCROSS + si];
         }
@@ -1522,11 +1602,11 @@ __device__ __forceinline__ void tile_update(const Params<T>& P, const TileCtx<T>
 template <typename T, int STAGE, int ORD>
 __device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& c, long long tile_index,
                                           const T* __restrict__ sW, T* __restrict__ sF,
-                                          const int* __restrict__ sRow) {
+                                          const int2* __restrict__ sRows) {
     TileRhs<T> R;
-    tile_faces<T, ORD>(P, c, sW, sF, sRow, R);
+    tile_faces<T, ORD>(P, c, sW, sF, sRows, R);
     T pc[CELLS_PER_THREAD], ac[CELLS_PER_THREAD];
-    tile_cell_pa(sW, pc, ac);
+    tile_cell_pa(sW, sRows, pc, ac);
     tile_update<T, STAGE>(P, c, tile_index, R, pc, ac);
 }
 
@@ -1538,7 +1618,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
     // [7][NCROSS] primitives (staged as raw Q)
     T* sW = reinterpret_cast<T*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     T* sF = sW + 7 * NCROSS;                 // face fluxes + face velocities (NFLUX)
-    int* sRow = reinterpret_cast<int*>(sF + NFLUX);  // [BX][BX] row offsets
+    int2* sRows = reinterpret_cast<int2*>(sF + NFLUX);  // [BX][BX] per-row slot table
     TileCtx<T> c;
     tile_ctx(P, blockIdx.x, parity, c);
     // the finished-sample flag is read while the copies are issued (they only
@@ -1547,18 +1627,18 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
     // launch keeps three tiles per SM in flight either way, and the per-row
     // copies need no barrier set-up; the persistent variant uses them.)
     const int done = P.s.done[c.bw.slot];
-    tile_issue<T, STAGE>(P, c, sW);
-    fill_rows(sRow);
+    tile_issue<T, STAGE, LAYOUT_SWZ>(P, c, sW);
+    fill_rows<LAYOUT_SWZ>(sRows);
     cp_async_wait_all();
     if (done) return;
     __syncthreads();
-    tile_convert(P.eos, sW);
+    tile_convert<T, LAYOUT_SWZ>(P.eos, sW);
     if (P.bc == OFM_BC_CHARACTERISTIC) {
         __syncthreads();
-        tile_char_bc(P, c.bw, sW);
+        tile_char_bc<T, LAYOUT_SWZ>(P, c.bw, sW);
     }
     __syncthreads();
-    tile_body<T, STAGE, ORD>(P, c, (long long)blockIdx.x, sW, sF, sRow);
+    tile_body<T, STAGE, ORD>(P, c, (long long)blockIdx.x, sW, sF, sRows);
 }
 
 // One RK stage, persistent blocks (three per SM in single precision, one
@@ -1577,9 +1657,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
     __shared__ __align__(8) unsigned long long s_bar;
     T* sW = reinterpret_cast<T*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     T* sF = sW + 7 * NCROSS;
-    int* sRow = reinterpret_cast<int*>(sF + NFLUX);
+    int2* sRows = reinterpret_cast<int2*>(sF + NFLUX);
     const bool tma = P.bc != OFM_BC_PERIODIC;
-    fill_rows(sRow);
+    fill_rows<LAYOUT_DENSE>(sRows);   // the layout the tensor copies land
     if (tma && threadIdx.x == 0) mbar_init(&s_bar, 1);
     __syncthreads();   // the barrier is initialised before any thread waits on it
     const long long stride = gridDim.x;
@@ -1590,7 +1670,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
         tile_ctx(P, t, parity, c);
         done = P.s.done[c.bw.slot];
         if (!tma)
-            tile_issue<T, STAGE>(P, c, sW);
+            tile_issue<T, STAGE, LAYOUT_DENSE>(P, c, sW);
         else if (threadIdx.x < 7)
             tile_issue_tma(c, parity, sW, &s_bar, (int)threadIdx.x);
     }
@@ -1615,14 +1695,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
             }
             if (!done) {
                 __syncthreads();
-                tile_convert(P.eos, sW);
+                tile_convert<T, LAYOUT_DENSE>(P.eos, sW);
                 if (P.bc == OFM_BC_CHARACTERISTIC) {
                     __syncthreads();
-                    tile_char_bc(P, c.bw, sW);
+                    tile_char_bc<T, LAYOUT_DENSE>(P, c.bw, sW);
                 }
                 __syncthreads();
-                tile_faces<T, ORD>(P, c, sW, sF, sRow, R);
-                tile_cell_pa(sW, pc, ac);
+                tile_faces<T, ORD>(P, c, sW, sF, sRows, R);
+                tile_cell_pa(sW, sRows, pc, ac);
             }
         }
         __syncthreads();   // every read of sW is done
@@ -1635,7 +1715,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
             tile_ctx(P, tn, parity, cn);
             done_n = P.s.done[cn.bw.slot];
             if (!tma) {
-                tile_issue<T, STAGE>(P, cn, sW);
+                tile_issue<T, STAGE, LAYOUT_DENSE>(P, cn, sW);
             } else if (threadIdx.x < 7) {
                 // the block's generic-proxy accesses of sW come before the copies' writes
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
