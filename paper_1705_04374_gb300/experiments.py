@@ -9,6 +9,8 @@ uneven3   three levels 32^3 / 64^3 / 128^3 with 1024 / 128 / 16 pairs of 50-bubb
           clouds (FP32 stencil, FP64 reductions) in one uneven batch; device time,
           cell-updates/s, pair costs, the OF-MLMC estimator; and the same solves
           as one batch per group, for comparison.
+unevensmall the same comparison at 8^3 / 16^3 / 32^3 with 256 / 64 / 16 pairs,
+          where no group fills the GPU alone.
 surrogate the MLP surrogate trained on the solver's own samples and used as the
           estimator's extra control variate: (a) on the level-0 term, geometry
           only, expectation from 65,536 extra clouds; (b) on the top term,
@@ -232,6 +234,36 @@ def cmd_uneven3(quick):
                 autotuned=dict(seconds=secs_tuned, variant=tune.get("chosen"),
                                two_step_ms_per_variant=tune.get("tune_ms")),
                 estimator={k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in est.items()})
+
+
+def cmd_unevensmall(quick):
+    """The coarse end of a hierarchy, where no level fills the GPU alone: 8^3 /
+    16^3 / 32^3 with 256 / 64 / 16 pairs of 50-bubble clouds (groups of 64 to
+    1,024 tiles against 456 resident stage-kernel blocks), one uneven batch
+    against one batch per group, identical results required."""
+    w = W.cfg3()
+    levels = (8, 16, 32)
+    counts = (64, 16, 4) if quick else (256, 64, 16)
+    solver = api.Solver(w.solver, "fp32")
+    r = run_levels(solver, w.cloud, levels, counts)
+    rs = run_levels(solver, w.cloud, levels, counts, separate=True)
+    spec = []
+    for l, (N, M) in enumerate(zip(levels, counts)):
+        spec.append((N, level_ids(l, 0, M)))
+        if l > 0:
+            spec.append((levels[l - 1], level_ids(l, 0, M)))
+    tune = {}
+    _, secs_tuned, _ = solve_groups(solver, w.cloud, spec, variant=-1, tune=tune)
+    return dict(experiment="unevensmall", levels=list(levels), counts=list(counts), precision="fp32",
+                bubbles=w.cloud.n_bubbles, groups=[(N, len(ids)) for N, ids in spec],
+                tiles_per_group=[len(ids) * (N // 8) ** 3 for N, ids in spec],
+                device_seconds=r["secs"], cell_steps=r["cells"], cell_updates_per_s=r["cells"] / r["secs"],
+                separate_batches_seconds=rs["secs"], separate_cell_updates_per_s=rs["cells"] / rs["secs"],
+                speedup_one_batch=rs["secs"] / r["secs"],
+                identical_to_separate=bool(all(np.array_equal(a, b) for a, b in zip(r["pairs"], rs["pairs"]))),
+                autotuned=dict(seconds=secs_tuned, variant=tune.get("chosen"),
+                               two_step_ms_per_variant=tune.get("tune_ms")),
+                failed=r["failed"])
 
 
 # ------------------------------------------------------------------------------ surrogate
@@ -719,13 +751,13 @@ def cmd_mlptime(quick):
 def main():
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["uneven3", "surrogate", "rmse", "cfg5", "epsval", "paper500", "orders",
-                                     "fitwarm", "boundaries", "surloop", "cfg5tol", "mlptime"])
+    ap.add_argument("what", choices=["uneven3", "unevensmall", "surrogate", "rmse", "cfg5", "epsval", "paper500",
+                                     "orders", "fitwarm", "boundaries", "surloop", "cfg5tol", "mlptime"])
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--min-samples", type=int, default=16, help="epsval: pairs every level starts with")
     a = ap.parse_args()
     torch.cuda.set_device(0)
-    fn = {"uneven3": cmd_uneven3, "surrogate": cmd_surrogate, "rmse": cmd_rmse, "cfg5": cmd_cfg5,
+    fn = {"uneven3": cmd_uneven3, "unevensmall": cmd_unevensmall, "surrogate": cmd_surrogate, "rmse": cmd_rmse, "cfg5": cmd_cfg5,
           "epsval": cmd_epsval, "paper500": cmd_paper500, "orders": cmd_orders, "fitwarm": cmd_fitwarm,
           "boundaries": cmd_boundaries, "surloop": cmd_surloop, "cfg5tol": cmd_cfg5tol,
           "mlptime": cmd_mlptime}[a.what]
