@@ -221,8 +221,10 @@ int ofm_batch_set_profiling(ofm_batch* batch, int on);
 int ofm_batch_stage_time(ofm_batch* batch, double* total_ms, int64_t* n_launches);
 /* Stage-kernel variant: 0 (default) = one block per 8^3 tile; 1 = persistent
  * blocks (three per SM in FP32, one in FP64) with one staging buffer each,
- * issuing the next tile's halo copies before the current tile's update and
- * skipping finished samples without launching; -1 = autotune: the first
+ * issuing the next tile's halo copies (tensor copies; per-row copies with a
+ * periodic boundary) before the current tile's update, staging but not
+ * computing finished samples' tiles (a copy wait that runs out marks the
+ * sample OFM_ST_TIMEOUT); -1 = autotune: the first
  * ofm_batch_run of at least 4 steps times two steps of each variant and keeps
  * the faster.  In FP64 both variants give identical bits; in FP32 they agree
  * to round-off (the compiler may fuse multiply-adds differently in the two
