@@ -504,8 +504,20 @@ __global__ void reset_kernel(const __grid_constant__ Params<T> P) {
 // distance from the domain centre) p_l = p_cloud for r <= ramp_r0 and
 // p_liq + (p_cloud - p_liq) ramp_r0 / r beyond; u = 0; E = Gamma p + Pi.
 // Evaluated in FP64, stored in T.
+//
+// The minimum over bubbles runs over the tile's candidates only: with B the
+// box of the tile's cell centres, a bubble whose surface distance to B from
+// below (its distance to B minus r_b) exceeds U, the smallest distance bound
+// from above (the farthest corner of B minus r_b), by more than a rounding
+// margin is never the nearest for any cell of the tile, and fmin over the rest
+// gives the same bits (fmin is exact and order-free on finite values).
+constexpr int IC_MAX_CAND = 2048;   // larger clouds take the plain loop over every bubble
+
 template <typename T>
 __global__ void __launch_bounds__(NT) ic_kernel(const __grid_constant__ Params<T> P) {
+    __shared__ int s_cand[IC_MAX_CAND];
+    __shared__ int s_ncand;
+    __shared__ double s_umin[NT / 32];
     BlockWork<T> bw;
     decode_block(P, blockIdx.x, bw);
     const GroupDev& G = *bw.G;
@@ -517,11 +529,48 @@ __global__ void __launch_bounds__(NT) ic_kernel(const __grid_constant__ Params<T
     const double gi1 = 1.0 / ((double)P.eos.g1 - 1.0), gi2 = 1.0 / ((double)P.eos.g2 - 1.0);
     const double pi1 = (double)P.eos.g1 * (double)P.eos.pc1 * gi1;
     const double pi2 = (double)P.eos.g2 * (double)P.eos.pc2 * gi2;
+    const bool cull = P.nb <= IC_MAX_CAND;
+    if (cull) {
+        const double lo[3] = {(bw.x0 + 0.5) * h, (bw.y0 + 0.5) * h, (bw.z0 + 0.5) * h};
+        const double hi[3] = {(bw.x0 + TS - 0.5) * h, (bw.y0 + TS - 0.5) * h, (bw.z0 + TS - 0.5) * h};
+        // U: the smallest upper bound of a bubble's surface distance over the box
+        double u = INFINITY;
+        for (int b = threadIdx.x; b < P.nb; b += NT) {
+            double f2 = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double d = fmax(fabs(bub[4 * b + k] - lo[k]), fabs(bub[4 * b + k] - hi[k]));
+                f2 += d * d;
+            }
+            u = fmin(u, sqrt(f2) - bub[4 * b + 3]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) u = fmin(u, __shfl_xor_sync(0xffffffffu, u, off));
+        if ((threadIdx.x & 31) == 0) s_umin[threadIdx.x >> 5] = u;
+        if (threadIdx.x == 0) s_ncand = 0;
+        __syncthreads();
+        double U = s_umin[0];
+        for (int w = 1; w < NT / 32; ++w) U = fmin(U, s_umin[w]);
+        const double margin = 1e-9;   // far above the rounding of any distance in the unit domain
+        for (int b = threadIdx.x; b < P.nb; b += NT) {
+            double n2 = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double c = bub[4 * b + k];
+                const double d = c < lo[k] ? lo[k] - c : (c > hi[k] ? c - hi[k] : 0.0);
+                n2 += d * d;
+            }
+            if (sqrt(n2) - bub[4 * b + 3] <= U + margin) s_cand[atomicAdd(&s_ncand, 1)] = b;
+        }
+        __syncthreads();
+    }
+    const int n_try = cull ? s_ncand : P.nb;
     for (int c = threadIdx.x; c < NCELL; c += NT) {
         const int x = bw.x0 + (c & 7), y = bw.y0 + ((c >> 3) & 7), z = bw.z0 + (c >> 6);
         const double xc = (x + 0.5) * h, yc = (y + 0.5) * h, zc = (z + 0.5) * h;
         double m = INFINITY;
-        for (int b = 0; b < P.nb; ++b) {
+        for (int i = 0; i < n_try; ++i) {
+            const int b = cull ? s_cand[i] : i;
             const double dx = xc - bub[4 * b], dy = yc - bub[4 * b + 1], dz = zc - bub[4 * b + 2];
             m = fmin(m, sqrt(dx * dx + dy * dy + dz * dz) - bub[4 * b + 3]);
         }
