@@ -438,16 +438,30 @@ __device__ __forceinline__ void red_cell(const Eos<T>& e, const T* q, long long 
     }
 }
 
+template <typename T>
+__device__ __forceinline__ void red_merge(RedT<T>& a, T smax, T cmax, T pmax, long long idx, int st) {
+    a.smax = fmax(a.smax, smax);
+    a.cmax = fmax(a.cmax, cmax);
+    if (pmax > a.pmax || (pmax == a.pmax && idx < a.idx)) {
+        a.pmax = pmax;
+        a.idx = idx;
+    }
+    a.status |= st;
+}
+
 // Combine a block's per-thread records in a fixed order (warp shuffles, then
-// warps in index order) and write one Partial.
-__device__ void block_reduce_write(Red r, Partial* out) {
-    __shared__ Red sred[NT / 32];
+// warps in index order) in the stencil precision and write one Partial
+// (widened at the end: the same bits as a reduction in double, since the
+// conversion is exact and monotone, without single-lane FP64 compares).
+template <typename T>
+__device__ void block_reduce_write(RedT<T> r, Partial* out) {
+    __shared__ RedT<T> sred[NT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        const double sm = __shfl_down_sync(0xffffffffu, r.smax, off);
-        const double cm = __shfl_down_sync(0xffffffffu, r.cmax, off);
-        const double pm = __shfl_down_sync(0xffffffffu, r.pmax, off);
+        const T sm = __shfl_down_sync(0xffffffffu, r.smax, off);
+        const T cm = __shfl_down_sync(0xffffffffu, r.cmax, off);
+        const T pm = __shfl_down_sync(0xffffffffu, r.pmax, off);
         const long long ix = __shfl_down_sync(0xffffffffu, r.idx, off);
         const int st = __shfl_down_sync(0xffffffffu, r.status, off);
         red_merge(r, sm, cm, pm, ix, st);
@@ -455,14 +469,15 @@ __device__ void block_reduce_write(Red r, Partial* out) {
     if (lane == 0) sred[warp] = r;
     __syncthreads();
     if (threadIdx.x == 0) {
-        Red a = sred[0];
+        RedT<T> a = sred[0];
         for (int w = 1; w < NT / 32; ++w)
             red_merge(a, sred[w].smax, sred[w].cmax, sred[w].pmax, sred[w].idx, sred[w].status);
-        out->smax = a.smax;
-        out->cmax = a.cmax;
-        out->pmax = a.pmax;
-        out->idx = a.idx;
-        out->status = a.status;
+        const Red o = red_widen(a);
+        out->smax = o.smax;
+        out->cmax = o.cmax;
+        out->pmax = o.pmax;
+        out->idx = o.idx;
+        out->status = o.status;
         out->pad = 0;
     }
 }
@@ -615,7 +630,7 @@ __global__ void __launch_bounds__(NT) reduce_kernel(const __grid_constant__ Para
         red_cell(P.eos, q, (long long)gi, r);
     }
     const long long tile = blockIdx.x - G.block0 - (long long)bw.s_local * G.tps;
-    block_reduce_write(red_widen(r), G.part + (size_t)bw.s_local * G.tps + tile);
+    block_reduce_write(r, G.part + (size_t)bw.s_local * G.tps + tile);
 }
 
 // Both WENO5 face states of the face between the cells holding c0 and p1,
@@ -1607,7 +1622,7 @@ __device__ __forceinline__ void tile_update(const Params<T>& P, const TileCtx<T>
             red_cell(e, q0, (long long)gi, red);
             red_cell(e, q1, (long long)gi + 1, red);
             const long long tile = tile_index - G.block0 - (long long)bw.s_local * G.tps;
-            block_reduce_write(red_widen(red), G.part + (size_t)bw.s_local * G.tps + tile);
+            block_reduce_write(red, G.part + (size_t)bw.s_local * G.tps + tile);
         }
     } else {
 #pragma unroll
@@ -1641,7 +1656,7 @@ __device__ __forceinline__ void tile_update(const Params<T>& P, const TileCtx<T>
         }
         if (STAGE == 2) {
             const long long tile = tile_index - G.block0 - (long long)bw.s_local * G.tps;
-            block_reduce_write(red_widen(red), G.part + (size_t)bw.s_local * G.tps + tile);
+            block_reduce_write(red, G.part + (size_t)bw.s_local * G.tps + tile);
         }
     }
 }
