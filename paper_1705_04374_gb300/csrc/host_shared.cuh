@@ -77,6 +77,8 @@ inline void params_constants(const ofm_solver* s, int nb, Params<T>& P) {
     for (int k = 0; k < 3; ++k) {
         P.rkA[k] = RK_A[k];
         P.rkB[k] = RK_B[k];
+        P.rkA_t[k] = (T)RK_A[k];
+        P.rkB_t[k] = (T)RK_B[k];
     }
     P.bc = c.bc;
     P.bc_penalty = c.bc_penalty;

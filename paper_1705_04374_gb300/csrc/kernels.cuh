@@ -1542,7 +1542,8 @@ __device__ __forceinline__ void tile_faces_staged(const Eos<T>& e, T invh, const
 template <typename T, int ORD>
 __device__ __forceinline__ void tile_faces(const Params<T>& P, const TileCtx<T>& c, const T* __restrict__ sW,
                                            T* __restrict__ sF, const int2* __restrict__ sRows, TileRhs<T>& R) {
-    const T invh = T(1) / (T)c.bw.G->h;  // 1/h, formed as the FP64 reference forms it
+    // 1/h, formed as the FP64 reference forms it (single precision: from the host's float h)
+    const T invh = T(1) / (std::is_same<T, float>::value ? (T)c.bw.G->h32 : (T)c.bw.G->h);
     if constexpr (std::is_same<T, float>::value && ORD == 5)
         tile_faces_direct(P.eos, invh, sW, sF, sRows, R);
     else
@@ -1583,7 +1584,7 @@ __device__ __forceinline__ void tile_update(const Params<T>& P, const TileCtx<T>
     const Eos<T> e = P.eos;
     T (&rhs)[CELLS_PER_THREAD][7] = R.rhs;
     T (&divu)[CELLS_PER_THREAD] = R.divu;
-    const T A = (T)P.rkA[STAGE], B = (T)P.rkB[STAGE];
+    const T A = P.rkA_t[STAGE], B = P.rkB_t[STAGE];
     RedT<T> red;
     red_init(red);
     if constexpr (kPairCells<T>) {

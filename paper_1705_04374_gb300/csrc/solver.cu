@@ -137,6 +137,7 @@ void fill_params(ofm_batch* b, Params<T>& P) {
         G.sens_cells = (const int*)(b->ws + gh.off_sens);
         for (int k = 0; k <= OFM_MAX_SENSORS; ++k) G.sens_off[k] = k <= c.n_sensors ? gh.sens_off[k] : 0;
         G.h = 1.0 / gh.N;
+        G.h32 = (float)G.h;
         blk += (long long)G.tps * gh.M;
         slot += gh.M;
     }

@@ -123,6 +123,7 @@ void static_params(const ofm_solver* s, int N, int M, int nb, unsigned char* ws,
     G.sens_cells = (const int*)(ws + L.sens);
     for (int k = 0; k <= c.n_sensors; ++k) G.sens_off[k] = sens_off[k];
     G.h = 1.0 / N;
+    G.h32 = (float)G.h;
     P.total_blocks = (long long)G.tps * M;
     P.total_slots = M;
     P.s.t = (double*)(ws + L.t);

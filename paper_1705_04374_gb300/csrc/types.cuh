@@ -83,6 +83,7 @@ struct GroupDev {
     const int* sens_cells;
     int sens_off[OFM_MAX_SENSORS + 1];
     double h;
+    float h32;            // (float)h, converted once on the host (the same rounding as on the device)
 };
 
 struct SampleDev {
@@ -110,6 +111,7 @@ struct Params {
     SampleDev s;
     Eos<T> eos;
     double rkA[3], rkB[3];
+    T rkA_t[3], rkB_t[3];      // the coefficients in the stencil precision (converted on the host)
     int bc, nb, n_sens, n_out, max_steps, total_slots;
     double t_end, cfl, p_gas, p_liq, rho1, rho2;
     double p_cloud, ramp_r0;   // cloud pressure ramp of the initial condition (ramp_r0 = 0: off)
