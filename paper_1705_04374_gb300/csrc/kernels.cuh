@@ -1572,7 +1572,7 @@ __device__ __forceinline__ void tile_cell_pa(const T* __restrict__ sW, const int
 template <typename T, int STAGE>
 __device__ __forceinline__ void tile_update(const Params<T>& P, const TileCtx<T>& c, long long tile_index,
                                             TileRhs<T>& R, const T (&pc)[CELLS_PER_THREAD],
-                                            const T (&ac)[CELLS_PER_THREAD]) {
+                                            const T (&ac)[CELLS_PER_THREAD], T dt) {
     const BlockWork<T>& bw = c.bw;
     const GroupDev& G = *bw.G;
     const int N = G.N;
@@ -1580,7 +1580,6 @@ __device__ __forceinline__ void tile_update(const Params<T>& P, const TileCtx<T>
     const T* __restrict__ Qin = c.Qin;
     T* __restrict__ Qout = c.Qout;
     T* __restrict__ dQ = c.dQ;
-    const T dt = (T)P.s.dt[bw.slot];
     const Eos<T> e = P.eos;
     T (&rhs)[CELLS_PER_THREAD][7] = R.rhs;
     T (&divu)[CELLS_PER_THREAD] = R.divu;
@@ -1667,12 +1666,12 @@ __device__ __forceinline__ void tile_update(const Params<T>& P, const TileCtx<T>
 template <typename T, int STAGE, int ORD>
 __device__ __forceinline__ void tile_body(const Params<T>& P, const TileCtx<T>& c, long long tile_index,
                                           const T* __restrict__ sW, T* __restrict__ sF,
-                                          const int2* __restrict__ sRows) {
+                                          const int2* __restrict__ sRows, T dt) {
     TileRhs<T> R;
     tile_faces<T, ORD>(P, c, sW, sF, sRows, R);
     T pc[CELLS_PER_THREAD], ac[CELLS_PER_THREAD];
     tile_cell_pa(sW, sRows, pc, ac);
-    tile_update<T, STAGE>(P, c, tile_index, R, pc, ac);
+    tile_update<T, STAGE>(P, c, tile_index, R, pc, ac, dt);
 }
 
 // One RK stage, one block per tile (ORD: WENO order, 5 or 3).
@@ -1692,6 +1691,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
     // launch keeps three tiles per SM in flight either way, and the per-row
     // copies need no barrier set-up; the persistent variant uses them.)
     const int done = P.s.done[c.bw.slot];
+    __shared__ T s_dt;   // the sample's time step, converted once per block
+    if (threadIdx.x == 0) s_dt = (T)P.s.dt[c.bw.slot];
     tile_issue<T, STAGE, LAYOUT_SWZ>(P, c, sW);
     fill_rows<LAYOUT_SWZ>(sRows);
     cp_async_wait_all();
@@ -1703,7 +1704,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
         tile_char_bc<T, LAYOUT_SWZ>(P, c.bw, sW);
     }
     __syncthreads();
-    tile_body<T, STAGE, ORD>(P, c, (long long)blockIdx.x, sW, sF, sRows);
+    tile_body<T, STAGE, ORD>(P, c, (long long)blockIdx.x, sW, sF, sRows, s_dt);
 }
 
 // One RK stage, persistent blocks (three per SM in single precision, one
@@ -1790,7 +1791,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
         if (!done) {
             TileCtx<T> c;
             tile_ctx(P, t, parity, c);
-            tile_update<T, STAGE>(P, c, t, R, pc, ac);
+            tile_update<T, STAGE>(P, c, t, R, pc, ac, (T)P.s.dt[c.bw.slot]);
         }
         t = tn;
         done = done_n;
