@@ -993,11 +993,20 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
     return ok != 0;
 }
 
-// Bounded wait for phase `parity` of bar (each try_wait may itself suspend
-// the thread for a while): false if it did not complete within the limit.
+// Bounded wait for phase `parity` of bar: false if it did not complete
+// within about a second of the global timer (each try_wait may itself
+// suspend the thread for a while; the iteration cap is a second bound).
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
-    for (int it = 0; it < (1 << 22); ++it)
+    const unsigned long long t0 = global_ns();
+    for (int it = 0; it < (1 << 24); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > 1000000000ull) return false;
+    }
     return false;
 }
 
