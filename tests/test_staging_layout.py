@@ -1,10 +1,12 @@
-"""CPU checks of the stage kernels' shared-memory staging layouts (read from
-the kernel source): every staged cell of a tile and its halo has its own slot
-inside the staging buffer, 16-byte chunks of four x-consecutive cells stay
-whole and aligned (the copies move chunks), the dense layout is the boxes the
-tensor copies land, and the bank-spread layout spreads the face runs' and far
-faces' stencil loads over the 32 banks as its search found (a lane-by-lane
-model of the kernel's access patterns)."""
+"""CPU checks of the kernels' index and culling logic (read from the kernel
+source): every staged cell of a tile and its halo has its own slot inside the
+staging buffer, 16-byte chunks of four x-consecutive cells stay whole and
+aligned (the copies move chunks), the dense layout is the boxes the tensor
+copies land, the bank-spread layout spreads the face runs' and far faces'
+stencil loads over the 32 banks as its search found (a lane-by-lane model of
+the kernel's access patterns), the per-cell accumulation array's slots are a
+conflict-free permutation, and the initial condition's per-tile bubble culling
+keeps every bubble that can be a cell's nearest."""
 import os
 import re
 
@@ -152,3 +154,64 @@ def test_bank_spread_layout_spreads_the_stencil_loads():
     assert len(loads) == 204
     assert dense == 864
     assert swz <= 327   # the x runs read one parity (two-way at best), the x far faces one x (four-way)
+
+
+def _rslot():
+    text = _source()
+    m = re.search(r"__device__ __forceinline__ int rslot\(int c\) \{ return (.*?); \}", text)
+    assert m, "rslot not found"
+    expr = m.group(1)
+    return lambda c: eval(expr, {"c": c})
+
+
+def test_accumulation_slots_are_a_permutation_without_bank_conflicts():
+    """The per-cell y + z flux-difference array: the y-run stores (lanes x, runs
+    y = 0, 2, 4, 6 and y + 1), the z-run updates (lanes x, runs z = 0, 2, 4, 6 and
+    z + 1) and the owners' paired reads (cells 2t, 2t + 1 of a warp) touch 32
+    distinct banks, and the owners' pairs stay adjacent and 8-byte aligned."""
+    rslot = _rslot()
+    assert sorted(rslot(c) for c in range(512)) == list(range(512))
+
+    def banks(slots):
+        return len({s % 32 for s in slots})
+    for b in range(8):
+        for off in (0, 8):
+            assert banks([rslot(a + 8 * 2 * g + 64 * b + off) for g in range(4) for a in range(8)]) == 32
+        for off in (0, 64):
+            assert banks([rslot(a + 8 * b + 64 * 2 * g + off) for g in range(4) for a in range(8)]) == 32
+    for w in range(8):
+        for half in range(2):
+            words = []
+            for lane in range(16 * half, 16 * half + 16):
+                s0 = rslot(64 * w + 2 * lane)
+                assert s0 % 2 == 0 and rslot(64 * w + 2 * lane + 1) == s0 + 1
+                words += [s0, s0 + 1]
+            assert banks(words) == 32
+
+
+def test_initial_condition_candidates_keep_every_nearest_bubble():
+    """The initial condition's per-tile culling (a bubble whose lower bound of the
+    surface distance over the tile's cell centres exceeds the smallest upper
+    bound, by the kernel's margin, is dropped): restated here in FP64 and checked
+    on seeded clouds of 4 to 500 bubbles on 8^3 to 64^3 that fmin over the kept
+    bubbles equals fmin over all of them, bit for bit, in every cell."""
+    import numpy as np
+    text = _source()
+    margin = float(re.search(r"const double margin = ([0-9.e-]+);", text).group(1))
+    rng = np.random.default_rng(7)
+    for N, nb in ((8, 4), (16, 20), (32, 50), (64, 500)):
+        h = 1.0 / N
+        bub = np.column_stack([0.5 + rng.uniform(-0.3, 0.3, (nb, 3)), rng.uniform(0.05, 0.1, nb) * 0.3])
+        tiles = [(x0, y0, z0) for x0 in range(0, N, 8) for y0 in range(0, N, 8) for z0 in range(0, N, 8)]
+        for x0, y0, z0 in tiles[:: max(1, len(tiles) // 24)]:
+            lo = np.array([(x0 + 0.5) * h, (y0 + 0.5) * h, (z0 + 0.5) * h])
+            hi = np.array([(x0 + 7.5) * h, (y0 + 7.5) * h, (z0 + 7.5) * h])
+            far = np.maximum(np.abs(bub[:, :3] - lo), np.abs(bub[:, :3] - hi))
+            U = np.min(np.sqrt((far ** 2).sum(1)) - bub[:, 3])
+            near = np.where(bub[:, :3] < lo, lo - bub[:, :3], np.where(bub[:, :3] > hi, bub[:, :3] - hi, 0.0))
+            keep = np.sqrt((near ** 2).sum(1)) - bub[:, 3] <= U + margin
+            assert keep.any()
+            g = np.arange(8) + 0.5
+            xs = np.stack(np.meshgrid((x0 + g) * h, (y0 + g) * h, (z0 + g) * h, indexing="ij"), -1).reshape(-1, 3)
+            d = np.sqrt(((xs[:, None, :] - bub[None, :, :3]) ** 2).sum(-1)) - bub[None, :, 3]
+            assert np.array_equal(d.min(1), d[:, keep].min(1))
