@@ -127,7 +127,7 @@ constexpr double RK_B[3] = {0.924574, 0.287713063186749, 0.626538109512740};
 // fluxes (near faces of one direction or, in single-precision WENO5, the
 // per-cell y + z flux differences; far faces of all three directions) and
 // the staging layout's per-row slot table
-// (FP32: 73.5 KB, three blocks per SM; FP64: 146 KB, one).
+// (FP32: 74.4 KB, three blocks per SM; FP64: 148 KB, one).
 // (+128 bytes: the kernels align the staging buffer to 128 bytes for the
 // tensor copies.)
 constexpr size_t smem_bytes(size_t elem) { return elem * (7 * NCROSS + NFLUX) + 2 * sizeof(int) * BX * BX + 128; }
