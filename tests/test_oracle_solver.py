@@ -47,14 +47,18 @@ def test_prim_cons_round_trip():
     assert rel(S.cons_to_prim(g, Q), Wp) < 1e-12
 
 
-def test_max_speed_uniform_state_is_textbook():
-    """Uniform pure-liquid state: max speed = max|u_d| + sqrt(g (p + pc)/rho)."""
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_max_speed_uniform_state_is_textbook(axis):
+    """Uniform pure-liquid state: max speed = max|u_d| + sqrt(g (p + pc)/rho),
+    with the largest velocity component along each axis in turn."""
     n = 4
     g = S.make_grid(n, gamma=GAM, pc_nd=PC)
     Wp = np.zeros((7, n ** 3))
     Wp[0] = 1.0
     Wp[1] = 0.0
-    Wp[2], Wp[3], Wp[4] = 0.1, -0.7, 0.2
+    vel = [0.1, 0.2, -0.15]
+    vel[axis] = -0.7
+    Wp[2], Wp[3], Wp[4] = vel
     Wp[5] = 1.0
     Q = S.prim_to_cons(g, Wp)
     c = math.sqrt(GAM[0] * (1.0 + PC[0]) / 1.0)
@@ -227,6 +231,74 @@ def test_hllc_mirror_symmetry():
         sign[3] = 1.0                      # normal momentum flux is even
         assert np.allclose(Fm, sign * F, rtol=1e-11, atol=1e-12)
         assert abs(ufm + uf) < 1e-12
+
+
+def test_hllc_face_between_a_state_and_its_mirror_image():
+    """Left and right states that are mirror images across the face (normal
+    velocity reversed), colliding and separating: by symmetry nothing crosses
+    the face but momentum, the face velocity is zero and the normal momentum
+    flux is the HLLC star pressure p* = p + rho u (u - s_L) with s* = 0 and
+    s_L = -|u| - c (Toro).  With s* = 0 the face velocity is the mean of the
+    two one-sided ones, which are exact opposites here, so it is exactly 0."""
+    g = S.make_grid(4, gamma=GAM, pc_nd=PC)
+    rng = np.random.default_rng(14)
+    for _ in range(20):
+        w = _random_state(rng)
+        for d in range(3):
+            for sgn in (1.0, -1.0):      # towards the face from both sides / away from it
+                wl = w.copy()
+                wl[2 + d] = sgn * (abs(w[2 + d]) + 0.05)
+                wr = wl.copy()
+                wr[2 + d] = -wl[2 + d]
+                F, uf = S.hllc(g, wl, wr, d)
+                assert uf == 0.0 and F[6] == 0.0
+                a2, rho, u, p = wl[6], wl[0] + wl[1], wl[2 + d], wl[5]
+                G = (1 - a2) / (GAM[0] - 1) + a2 / (GAM[1] - 1)
+                Pi = (1 - a2) * GAM[0] * PC[0] / (GAM[0] - 1) + a2 * GAM[1] * PC[1] / (GAM[1] - 1)
+                c = math.sqrt(((G + 1) * p + Pi) / (G * rho))
+                # the vanishing fluxes cancel terms of the size of the one-sided flux and
+                # of s_L times the conserved state: bound them by rounding on that scale
+                qv = S.prim_to_cons(g, wl.reshape(7, 1)).ravel()
+                size = np.abs(_flux_text(wl, d, GAM, PC)) + (abs(u) + c) * np.abs(qv)
+                others = [v for v in range(6) if v != 2 + d]
+                assert np.all(np.abs(F[others]) <= 1e-14 * size[others]), (F, d, sgn)
+                p_star = p + rho * u * (u + abs(u) + c)
+                assert abs(F[2 + d] - p_star) <= 1e-13 * (abs(p) + rho * abs(u) * (2 * abs(u) + c))
+                assert (F[2 + d] > p) == (sgn > 0)    # compression when colliding
+
+
+@pytest.mark.parametrize("order", [5, 3])
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_rhs_commutes_with_reflections_and_axis_swaps(order, bc):
+    """The right-hand side of a random smooth state is equivariant under the
+    symmetries of the grid: reflecting the state along an axis (with that
+    velocity component reversed) reflects its right-hand side the same way,
+    and swapping two axes (with their velocity components) swaps it.  A
+    stencil taken in the wrong orientation, a face state from the wrong side,
+    or a direction index mixed up breaks one of these."""
+    n = 8
+    g = S.make_grid(n, gamma=GAM, pc_nd=PC, bc=bc, weno_order=order, bc_penalty=0.7, p_inf=1.1)
+    Wp = W.smooth_periodic_primitives(n, seed=21, amp=0.3)
+    Q = S.prim_to_cons(g, Wp.reshape(7, -1)).reshape(7, n, n, n)
+    R = S.rhs(g, Q).reshape(7, n, n, n)
+    scale = np.max(np.abs(R), axis=(1, 2, 3), keepdims=True)
+    assert np.all(scale > 1e-3)
+    for ax in range(3):                  # grid axis ax is array axis 3 - ax (x fastest)
+        sl = [slice(None)] * 4
+        sl[3 - ax] = slice(None, None, -1)
+        M = Q[tuple(sl)].copy()
+        M[2 + ax] *= -1
+        want = R[tuple(sl)].copy()
+        want[2 + ax] *= -1
+        got = S.rhs(g, M).reshape(7, n, n, n)
+        assert np.all(np.abs(got - want) <= 1e-12 * scale), (ax, np.max(np.abs(got - want) / scale))
+    for a, b in ((0, 1), (1, 2), (0, 2)):
+        T = np.swapaxes(Q, 3 - a, 3 - b).copy()
+        T[[2 + a, 2 + b]] = T[[2 + b, 2 + a]]
+        want = np.swapaxes(R, 3 - a, 3 - b).copy()
+        want[[2 + a, 2 + b]] = want[[2 + b, 2 + a]]
+        got = S.rhs(g, T).reshape(7, n, n, n)
+        assert np.all(np.abs(got - want) <= 1e-12 * scale), ((a, b), np.max(np.abs(got - want) / scale))
 
 
 # ---------------------------------------------------------------- positivity fallback (reading of Sec. 2.2)
@@ -712,17 +784,20 @@ def test_characteristic_boundary_keeps_the_far_field_at_rest():
     assert np.array_equal(Q1, Q)
 
 
-def test_characteristic_boundary_admits_the_far_field_wave_of_linear_acoustics():
+@pytest.mark.parametrize("rho", [1.0, 2.0])
+def test_characteristic_boundary_admits_the_far_field_wave_of_linear_acoustics(rho):
     """Liquid at rest at p0 = p_inf - d: each face admits the wave of the
     acoustic Riemann problem against the far field, p0 + d/2 moving inwards
-    at d/(2 Z), and the incoming characteristic at the face carries p_inf.
-    At t = L/(4c) the face centres are still reached by their own face's
-    wave only."""
+    at d/(2 Z) with the impedance Z = rho c, and the incoming characteristic
+    at the face carries p_inf.  At t = L/(4c) the face centres are still
+    reached by their own face's wave only.  (At rho = 2 the impedance differs
+    from the sound speed, so a boundary that used c for Z would admit a
+    wave of the wrong amplitude.)"""
     n, d = 32, 0.01
     p0 = 1.0 - d
-    g, Q, _ = _liquid(n, p0, 2)
-    c = math.sqrt(GAM[0] * (p0 + PC[0]))
-    Z = c
+    g, Q, _ = _liquid(n, p0, 2, rho=rho)
+    c = math.sqrt(GAM[0] * (p0 + PC[0]) / rho)
+    Z = rho * c
     Qt, _ = S.advance(g, Q, 0.25 / c)
     Wn = _prim(g, Qt)
     p, u = Wn[5][16, 16, :], Wn[2][16, 16, :]
@@ -771,17 +846,16 @@ def test_characteristic_boundary_lets_an_acoustic_pulse_leave():
     assert left[2] < 0.5 * left[0]
 
 
-def test_sensor_histories_are_the_step_values_interpolated_onto_the_output_times():
-    """The QoI bookkeeping of a solve against a time loop written here (CFL
-    steps of the oracle's RK3, the last one clipped to t_end): sensor means
-    taken with numpy over the cells whose centre lies within max(r, h), their
-    histories by numpy's linear interpolation onto t_k = k t_end/(K - 1), the
-    peak pressure with its first (x-fastest) cell and first time, the sensor
-    peaks, and the gas-fraction minima with their first times."""
-    sp = W.SolverParams(sensors=(W.centre_sensor()[0], (0.03, 0.05, 0.06, 0.012)), n_out_times=17)
-    n = 16
-    b = cloud.sample_cloud(W.cloud_uniform(4), W.BASE_SEED, 2)
-    q, hist, _ = S.solve(sp, n, b)
+def _qoi_bookkeeping(sp, n, b, Q0=None):
+    """Solve with the oracle and check its QoI bookkeeping against a time loop
+    written here (CFL steps of the oracle's RK3, the last one clipped to
+    t_end): sensor means taken with numpy over the cells whose centre lies
+    within max(r, h), their histories by numpy's linear interpolation onto
+    t_k = k t_end/(K - 1), the peak pressure with its first (x-fastest) cell
+    and first time, the maximum sound speed from the textbook closure, the
+    sensor peaks, and the gas-fraction minima with their first times.
+    Returns the QoIs and the loop's step values."""
+    q, hist, _ = S.solve(sp, n, b, Q0=Q0)
     g = S.grid_from_params(sp, n)
     u = S.Units(sp.domain_L, sp.p_liq)
     t_end = sp.t_end / u.t_ref
@@ -792,15 +866,21 @@ def test_sensor_histories_are_the_step_values_interpolated_onto_the_output_times
         R = max(r / sp.domain_L, 1.0 / n)
         d2 = (X - sx / sp.domain_L) ** 2 + (Y - sy / sp.domain_L) ** 2 + (Z - sz / sp.domain_L) ** 2
         masks.append(d2 <= R * R)
+    gam = sp.gamma
+    pc = (sp.pc[0] / u.p_ref, sp.pc[1] / u.p_ref)
 
     def sensors(Q):
         Wp = S.cons_to_prim(g, Q.reshape(7, -1)).reshape(7, n, n, n)
-        return [Wp[5][m].mean() for m in masks], [Wp[6][m].mean() for m in masks], Wp[5].ravel()
+        a2 = np.clip(Wp[6], 0.0, 1.0)
+        G = (1 - a2) / (gam[0] - 1) + a2 / (gam[1] - 1)
+        Pi = (1 - a2) * gam[0] * pc[0] / (gam[0] - 1) + a2 * gam[1] * pc[1] / (gam[1] - 1)
+        c = np.sqrt(((G + 1) * Wp[5] + Pi) / (G * (Wp[0] + Wp[1])))
+        return [Wp[5][m].mean() for m in masks], [Wp[6][m].mean() for m in masks], Wp[5].ravel(), c.max()
 
-    Q = S.init_cloud(sp, n, b)
+    Q = S.init_cloud(sp, n, b) if Q0 is None else Q0
     t, times = 0.0, [0.0]
-    p0, a0, pf = sensors(Q)
-    ps, als = [p0], [a0]
+    p0, a0, pf, cm = sensors(Q)
+    ps, als, cms = [p0], [a0], [cm]
     peak, peak_i, peak_t = pf.max(), int(np.argmax(pf)), 0.0     # first maximum, x fastest
     while t < t_end:
         dt = sp.cfl * g.h / S.max_speed(g, Q)
@@ -810,23 +890,89 @@ def test_sensor_histories_are_the_step_values_interpolated_onto_the_output_times
         Q = S.rk3_step(g, Q, dt)
         t = t_end if last else t + dt
         times.append(t)
-        p, a, pf = sensors(Q)
+        p, a, pf, cm = sensors(Q)
         ps.append(p)
         als.append(a)
+        cms.append(cm)
         if pf.max() > peak:                                        # a later equal value keeps the first
             peak, peak_i, peak_t = pf.max(), int(np.argmax(pf)), t
     assert len(times) - 1 == q["n_steps"]
     assert abs(q["p_peak"] - peak * sp.p_liq) <= 1e-12 * q["p_peak"]
     assert q["peak_index"] == peak_i and abs(q["p_peak_t"] - peak_t * u.t_ref) <= 1e-12 * u.t_ref
+    assert abs(q["c_max"] - max(cms) * u.u_ref) <= 1e-12 * q["c_max"]
     ps_a, als_a = np.array(ps), np.array(als)
     assert np.allclose(q["sensor_peak"], ps_a.max(axis=0) * sp.p_liq, rtol=1e-12, atol=0)
     assert np.allclose(q["sensor_alpha_min"], als_a.min(axis=0), rtol=1e-12, atol=0)
-    first_min = [times[int(np.argmin(als_a[:, s]))] * u.t_ref for s in range(2)]
+    first_min = [times[int(np.argmin(als_a[:, s]))] * u.t_ref for s in range(len(sp.sensors))]
     assert np.allclose(q["sensor_alpha_min_t"], first_min, rtol=1e-12, atol=0)
     tk = np.arange(sp.n_out_times) * t_end / (sp.n_out_times - 1)
-    ps, als = np.array(ps), np.array(als)
-    for s in range(2):
-        want_p = np.interp(tk, times, ps[:, s]) * sp.p_liq
-        want_a = np.interp(tk, times, als[:, s])
+    for s in range(len(sp.sensors)):
+        want_p = np.interp(tk, times, ps_a[:, s]) * sp.p_liq
+        want_a = np.interp(tk, times, als_a[:, s])
         assert np.allclose(hist[s], want_p, rtol=1e-12, atol=0)
         assert np.allclose(q["alpha_hist"][s], want_a, rtol=1e-12, atol=0)
+    return q, np.array(times) * u.t_ref, ps_a, np.array(cms)
+
+
+def test_sensor_histories_are_the_step_values_interpolated_onto_the_output_times():
+    """The QoI bookkeeping of a cloud solve (4 bubbles on 16^3, two sensors)."""
+    sp = W.SolverParams(sensors=(W.centre_sensor()[0], (0.03, 0.05, 0.06, 0.012)), n_out_times=17)
+    b = cloud.sample_cloud(W.cloud_uniform(4), W.BASE_SEED, 2)
+    _qoi_bookkeeping(sp, 16, b)
+
+
+def test_qoi_maxima_reached_after_the_initial_state_are_recorded():
+    """A converging flow of liquid at uniform pressure: the compression raises
+    the pressure, the sound speed and the centre sensor's reading after t = 0,
+    so the peak pressure, its time, the maximum sound speed and the sensor
+    peak all come from later steps, and are checked against the time loop."""
+    sp = W.SolverParams(sensors=W.centre_sensor(), n_out_times=9)
+    n = 16
+    g = S.grid_from_params(sp, n)
+    x = (np.arange(n) + 0.5) / n - 0.5
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    env = 0.05 * np.exp(-(X ** 2 + Y ** 2 + Z ** 2) / 0.04)
+    a2 = 1e-6
+    Wp = np.zeros((7, n, n, n))
+    Wp[0] = (1 - a2) * 1.0
+    Wp[1] = a2 * sp.rho0[1] / 1000.0
+    Wp[2], Wp[3], Wp[4] = -X * env / 0.2, -Y * env / 0.2, -Z * env / 0.2
+    Wp[5] = 1.0
+    Wp[6] = a2
+    Q0 = S.prim_to_cons(g, Wp.reshape(7, -1)).reshape(7, n, n, n)
+    q, times, ps, cms = _qoi_bookkeeping(sp, n, np.zeros((0, 4)), Q0=Q0)
+    assert q["status"] == 0
+    assert q["p_peak"] > 1.05 * sp.p_liq and q["p_peak_t"] > 0.0
+    assert q["c_max"] > cms[0] * 1.0001 * S.Units(sp.domain_L, sp.p_liq).u_ref
+    assert q["sensor_peak"][0] > 1.05 * ps[0, 0] * sp.p_liq
+
+
+def test_uniform_state_keeps_the_first_cell_and_the_first_time_of_its_peak():
+    """Every cell of a uniform liquid at rest ties for the maximum pressure at
+    every step: the peak is the first cell in x-fastest order at t = 0."""
+    sp = W.SolverParams(sensors=W.centre_sensor())
+    n = 8
+    g = S.grid_from_params(sp, n)
+    Wp = np.zeros((7, n ** 3))
+    Wp[0], Wp[1], Wp[5], Wp[6] = 1.0 - 1e-6, 1e-6 * sp.rho0[1] / 1000.0, 1.0, 1e-6
+    Q0 = S.prim_to_cons(g, Wp).reshape(7, n, n, n)
+    q, _, Qt = S.solve(sp, n, np.zeros((0, 4)), Q0=Q0)
+    assert np.array_equal(Qt, Q0)
+    assert q["peak_index"] == 0 and q["p_peak_t"] == 0.0
+    assert abs(q["p_peak"] / sp.p_liq - 1.0) < 1e-12   # the primitive -> conserved round trip
+
+
+def test_sensor_ball_holds_the_cells_within_and_on_its_radius():
+    """A sensor centred on a cell centre of a 16^3 grid (h = 1/16, so the
+    offsets and radii below are exact binary fractions) holds the cells whose
+    integer offset (i, j, k) has i^2 + j^2 + k^2 <= (R/h)^2, R = max(r, h),
+    the boundary included: counted here by brute force."""
+    n = 16
+    g = S.make_grid(n)
+    h = 1.0 / n
+    for r_over_h, R_over_h in ((0.5, 1), (1.0, 1), (1.5, 1.5), (2.0, 2), (3.0, 3)):
+        s = np.array([8.5 * h, 8.5 * h, 5.5 * h, r_over_h * h])
+        m = int(math.floor(R_over_h))
+        want = sum(1 for i in range(-m, m + 1) for j in range(-m, m + 1) for k in range(-m, m + 1)
+                   if i * i + j * j + k * k <= R_over_h * R_over_h)
+        assert S._lib().orc_sensor_cell_count(g, S._p(s)) == want, r_over_h
