@@ -174,7 +174,12 @@ int ofm_solver_create(ofm_solver** out, const ofm_solver_config* config);
 void ofm_solver_destroy(ofm_solver* solver);
 
 /* Device bytes a batch of these groups needs (states Q, Q', dQ per sample in
- * the configured precision, per-tile partial reductions, per-sample records). */
+ * the configured precision, per-tile partial reductions, per-sample records).
+ * Errors: OFM_EINVAL for a bad group table or more than 2^31 - 1 tiles;
+ * OFM_ENOMEM when the samples times their bubbles, or times their
+ * n_sensors x n_out_times history values, exceed 2^40 (so that no byte count
+ * can wrap around; such a batch would not fit any device anyway).  The same
+ * checks apply to ofm_batch_create and the calls built on it. */
 int ofm_batch_workspace_bytes(const ofm_solver* solver, const ofm_cloud_params* cloud,
                               const ofm_group* groups, int n_groups, size_t* bytes);
 
@@ -260,7 +265,9 @@ int ofm_solve_level(ofm_solver* solver, const ofm_cloud_params* cloud, int N, in
  * clouds from `cloud`) and outputs (`out`, `sensor_hist`, as in
  * ofm_solve_level) are host arrays owned by the caller.
  *   - Sizes whose scratch would exceed the array are rejected with
- *     OFM_ENOMEM and a message giving the bytes needed.  Each sample takes
+ *     OFM_ENOMEM and a message giving the bytes needed (the sample count is
+ *     checked against the array by division first, so no byte count can wrap
+ *     around and pass the check).  Each sample takes
  *     three state buffers of 7 N^3 values: up to 12 FP32 or 6 FP64 samples on
  *     32^3 fit, one FP32 sample on 64^3, no FP64 sample on 64^3.
  *   - The first call on a device, with that device current, looks up the

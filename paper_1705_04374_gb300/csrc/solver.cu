@@ -278,6 +278,15 @@ static int check_groups(const ofm_solver* s, const ofm_cloud_params* cloud, cons
         blocks += (long long)(N / TS) * (N / TS) * (N / TS) * groups[g].n_samples;
     }
     if (blocks > 0x7fffffffLL) return fail(OFM_EINVAL, "too many tiles in one batch");
+    // every sample has at least one tile, so at most 2^31 samples; bounding the
+    // per-sample bubble and history counts keeps every workspace size below
+    // 2^50 bytes, so no byte count can wrap around
+    long long samples = 0;
+    for (int g = 0; g < n_groups; ++g) samples += groups[g].n_samples;
+    const long long hist_per = (long long)s->cfg.n_sensors * s->cfg.n_out_times;
+    if ((long long)cloud->n_bubbles * samples > (1LL << 40) || hist_per * samples > (1LL << 40))
+        return fail(OFM_ENOMEM, "batch too large: %lld samples with %d bubbles and %lld history values each", samples,
+                    cloud->n_bubbles, hist_per);
     return OFM_OK;
 }
 

@@ -192,6 +192,15 @@ extern "C" int ofm_solve_level_static(const ofm_solver* s, const ofm_cloud_param
     int sens_off[OFM_MAX_SENSORS + 1];
     sensor_cell_list(s, N, cells, sens_off);
 
+    // the three state buffers alone bound the sample count; checked by division
+    // first, so that the layout's byte counts below cannot wrap around
+    const size_t es = c.precision == OFM_FP64 ? 8 : 4;
+    const size_t state_bytes = 3 * 7 * (size_t)N * N * N * es;
+    if ((size_t)n > OFM_STATIC_SCRATCH_BYTES / state_bytes)
+        return fail(OFM_ENOMEM,
+                    "ofm_solve_level_static: %d samples on %d^3 need %.4g bytes for their states alone, the static "
+                    "array holds %zu (use ofm_solve_level, or fewer / smaller samples)",
+                    n, N, (double)n * (double)state_bytes, (size_t)OFM_STATIC_SCRATCH_BYTES);
     const StaticLayout L = static_layout(s, N, n, nb, cells.size());
     if (L.total > OFM_STATIC_SCRATCH_BYTES)
         return fail(OFM_ENOMEM,

@@ -365,6 +365,90 @@ def test_static_entry_point_capacity(precision, N, fits):
         assert (rc == nv.OFM_ENOMEM) == rejected, (n, rc, nv.lib().ofm_last_error())
 
 
+@pytest.mark.parametrize("precision,N,n", [("fp64", 512, 2**31 - 1), ("fp64", 512, 2**30), ("fp32", 504, 10**9),
+                                            ("fp32", 8, 2**31 - 1), ("fp32", 8, 781)])
+def test_static_entry_point_rejects_huge_sample_counts(precision, N, n):
+    """Sample counts whose byte count would not fit a 64-bit size (n times
+    three state buffers of 7 N^3 values reaches 2^64 on the finest grids) are
+    rejected with OFM_ENOMEM before any byte count is formed, so no wrapped
+    size can pass the 32 MiB check.  The ids array is never read on this path."""
+    import ctypes as C
+    sp = W.SolverParams(sensors=W.centre_sensor())
+    s = api.Solver(sp, precision)
+    cp = api.cloud_params(W.cloud_uniform(4))
+    ids = (C.c_uint64 * 1)(0)
+    out = (nv.ofm_qoi * 1)()
+    rc = nv.lib().ofm_solve_level_static(s.h, C.byref(cp), N, n, ids, W.BASE_SEED, out, None, None)
+    assert rc == nv.OFM_ENOMEM, (rc, nv.lib().ofm_last_error())
+    assert b"need" in nv.lib().ofm_last_error()
+
+
+def test_static_entry_point_rejects_oversized_histories():
+    """One sample on 8^3 with eight sensors and 2^31 - 1 output times needs
+    ~1.4e11 bytes of history: rejected with OFM_ENOMEM on the host."""
+    import ctypes as C
+    sp = W.SolverParams(sensors=W.eight_sensors(0.02), n_out_times=2**31 - 1)
+    s = api.Solver(sp, "fp32")
+    cp = api.cloud_params(W.cloud_uniform(4))
+    ids = (C.c_uint64 * 1)(0)
+    out = (nv.ofm_qoi * 1)()
+    rc = nv.lib().ofm_solve_level_static(s.h, C.byref(cp), 8, 1, ids, W.BASE_SEED, out, None, None)
+    assert rc == nv.OFM_ENOMEM, (rc, nv.lib().ofm_last_error())
+
+
+def test_static_entry_point_rejects_a_request_whose_byte_count_wraps():
+    """2^30 FP64 samples on 512^3, one sensor, no bubbles and 1,475,084,226
+    output times: every per-sample byte count is then a multiple of 256 and
+    their sum a multiple of 2^34, so the unchecked total is 2 x 2^64 + 1280
+    bytes and wraps to 1280, under the 32 MiB of the array.  The sample
+    count is rejected (OFM_ENOMEM) before any byte count is formed."""
+    import ctypes as C
+    sp = W.SolverParams(sensors=W.centre_sensor(), n_out_times=1475084226)
+    s = api.Solver(sp, "fp64")
+    cp = api.cloud_params(W.cloud_uniform(0))
+    ids = (C.c_uint64 * 1)(0)
+    out = (nv.ofm_qoi * 1)()
+    rc = nv.lib().ofm_solve_level_static(s.h, C.byref(cp), 512, 2**30, ids, W.BASE_SEED, out, None, None)
+    assert rc == nv.OFM_ENOMEM, (rc, nv.lib().ofm_last_error())
+
+
+@pytest.mark.parametrize("n_bubbles,n_out,n_samples", [(0, 2**30, 2**28), (2**31 - 1, 65, 2**28 + 1),
+                                                       (4, 65, 2**31 - 1)])
+def test_batch_workspace_size_never_wraps(n_bubbles, n_out, n_samples):
+    """ofm_batch_workspace_bytes returns an error instead of a wrapped byte
+    count: 2^28 samples with 8 sensors x 2^30 output times make a history of
+    exactly 2^64 bytes (a wrapped count of 0); 2^28 + 1 samples of 2^31 - 1
+    bubbles make a cloud table of just over 2^64 bytes; 2^31 - 1 samples of
+    8^3 (within the tile limit) carry more than 2^40 history values.  The
+    benchmark's size (512 samples on 64^3) is still computed.  Only the group
+    table is read on this path."""
+    import ctypes as C
+    sp = W.SolverParams(sensors=W.eight_sensors(0.02), n_out_times=n_out)
+    s = api.Solver(sp, "fp32")
+    cloud = W.cloud_uniform(4)
+    cp = api.cloud_params(cloud)
+    cp.n_bubbles = n_bubbles
+    ids = (C.c_uint64 * 1)(0)
+    g = nv.ofm_group()
+    g.N = 8
+    g.n_samples = n_samples
+    g.sample_ids = ids
+    nbytes = C.c_size_t(0)
+    rc = nv.lib().ofm_batch_workspace_bytes(s.h, C.byref(cp), C.byref(g), 1, C.byref(nbytes))
+    assert rc in (nv.OFM_ENOMEM, nv.OFM_EINVAL), (rc, nbytes.value)
+    # the benchmark's size is still computed, and it is at least its three state buffers
+    sp = W.SolverParams(sensors=W.eight_sensors(0.02))
+    s = api.Solver(sp, "fp32")
+    cp = api.cloud_params(W.cloud_uniform(20))
+    ids = (C.c_uint64 * 512)(*range(512))
+    g = nv.ofm_group()
+    g.N = 64
+    g.n_samples = 512
+    g.sample_ids = ids
+    assert nv.lib().ofm_batch_workspace_bytes(s.h, C.byref(cp), C.byref(g), 1, C.byref(nbytes)) == nv.OFM_OK
+    assert nbytes.value >= 3 * 512 * 7 * 64**3 * 4
+
+
 def test_surrogate_estimator_matches_oracle():
     """ofm_estimate_surrogate against the oracle on a toy hierarchy with a
     nonlinear surrogate: optimal and fixed beta."""
