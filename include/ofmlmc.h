@@ -547,6 +547,9 @@ int ofm_level_kde(int L, const int64_t* M, const double* const* q, const double*
 #define OFM_MLP_MAX_LAYERS 8
 #define OFM_MLP_MAX_STEPS 200000
 typedef struct ofm_mlp ofm_mlp;
+/* Errors: OFM_EINVAL for a size < 1 or more than OFM_MLP_MAX_LAYERS layers;
+ * OFM_ENOMEM for a weight matrix or a max_rows x width activation array of
+ * more than 2^40 values (no byte count can wrap around). */
 int ofm_mlp_workspace_bytes(int d_in, int hidden, int n_hidden, int d_out, int max_rows, size_t* bytes);
 int ofm_mlp_create(ofm_mlp** out, int d_in, int hidden, int n_hidden, int d_out, int max_rows, void* workspace,
                    size_t workspace_bytes);

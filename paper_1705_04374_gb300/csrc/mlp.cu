@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -435,6 +436,13 @@ extern "C" int ofm_mlp_workspace_bytes(int d_in, int hidden, int n_hidden, int d
     if (d_in < 1 || hidden < 1 || n_hidden < 1 || n_hidden + 1 > OFM_MLP_MAX_LAYERS || d_out < 1 || max_rows < 1 ||
         !bytes)
         return fail(OFM_EINVAL, "ofm_mlp_workspace_bytes: bad sizes");
+    // a weight matrix or an activation array of more than 2^40 values would not
+    // fit any device; bounding them keeps every byte count below 2^50 (no wrap)
+    const long long wmax = std::max<long long>({(long long)d_in, (long long)hidden, (long long)d_out});
+    if ((long long)d_in * hidden > (1LL << 40) || (long long)hidden * hidden > (1LL << 40) ||
+        (long long)hidden * d_out > (1LL << 40) || (long long)max_rows * wmax > (1LL << 40))
+        return fail(OFM_ENOMEM, "ofm_mlp_workspace_bytes: network too large (%d inputs, %d wide, %d outputs, %d rows)",
+                    d_in, hidden, d_out, max_rows);
     ofm_mlp p;
     std::memset(&p, 0, sizeof(p));
     p.d_in = d_in;

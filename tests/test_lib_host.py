@@ -449,6 +449,21 @@ def test_batch_workspace_size_never_wraps(n_bubbles, n_out, n_samples):
     assert nbytes.value >= 3 * 512 * 7 * 64**3 * 4
 
 
+@pytest.mark.parametrize("d_in,hidden,d_out,rows", [(2**31 - 1, 2**31 - 1, 1, 1), (2000, 2**31 - 1, 1, 1),
+                                                    (201, 1024, 1, 2**31 - 1)])
+def test_mlp_workspace_size_never_wraps(d_in, hidden, d_out, rows):
+    """Four parameter-sized buffers of (2^31 - 1)^2 floats sum past 2^64
+    bytes: ofm_mlp_workspace_bytes returns OFM_ENOMEM for that and the other
+    oversized networks instead of a wrapped count, and still sizes the
+    surrogate's own shapes (2001 inputs, 3 x 256, 65,536 rows)."""
+    import ctypes as C
+    nbytes = C.c_size_t(0)
+    rc = nv.lib().ofm_mlp_workspace_bytes(d_in, hidden, 3, d_out, rows, C.byref(nbytes))
+    assert rc == nv.OFM_ENOMEM, (rc, nbytes.value)
+    assert nv.lib().ofm_mlp_workspace_bytes(2001, 256, 3, 1, 65536, C.byref(nbytes)) == nv.OFM_OK
+    assert nbytes.value >= 4 * 4 * (2001 * 256 + 2 * 256 * 256 + 256)
+
+
 def test_surrogate_estimator_matches_oracle():
     """ofm_estimate_surrogate against the oracle on a toy hierarchy with a
     nonlinear surrogate: optimal and fixed beta."""
