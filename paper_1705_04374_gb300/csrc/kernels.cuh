@@ -1043,8 +1043,7 @@ __device__ __forceinline__ void tile_ctx(const Params<T>& P, long long b, int pa
 // flight at once, in segments of four cells of one row: 16-byte copies (two
 // in double precision) wherever the four cells lie in the domain, else one
 // copy per halo cell through the boundary map (x halos of tiles on the
-// domain's x faces; rows of y and z halos are mapped as a whole).  For stages
-// that read dQ, an L2 prefetch of the tile's own dQ rows.
+// domain's x faces; rows of y and z halos are mapped as a whole).
 constexpr int NSEG_INT = TS * TS * 4;                 // full-width rows: 4 segments each
 constexpr int NSEG = NSEG_INT + 4 * HALO * TS * 2;     // + y and z halo rows: 2 each (448)
 
@@ -1109,7 +1108,6 @@ __device__ __forceinline__ void tile_issue(const Params<T>& P, const TileCtx<T>&
             }
         }
     }
-    if (STAGE > 0) tile_prefetch_dq(c);
 }
 
 // The tile's halo'd box by tensor copies: per variable the tile's rows with
@@ -1699,10 +1697,15 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
     // in flight.  (Staging by tensor copies measured 0.6-1 % slower here: one
     // launch keeps three tiles per SM in flight either way, and the per-row
     // copies need no barrier set-up; the persistent variant uses them.)
+    // The update reads dQ straight from global memory: an L2 prefetch of the
+    // tile's dQ rows issued with the copies made the single-precision kernel
+    // 4 % slower (12.60 against 12.11 ms per launch on 512 x 64^3, same bits);
+    // the double-precision kernel, bound by its FP64 pipe, keeps it.
     const int done = P.s.done[c.bw.slot];
     __shared__ T s_dt;   // the sample's time step, converted once per block
     if (threadIdx.x == 0) s_dt = (T)P.s.dt[c.bw.slot];
     tile_issue<T, STAGE, LAYOUT_SWZ>(P, c, sW);
+    if (sizeof(T) == 8 && STAGE > 0) tile_prefetch_dq(c);
     fill_rows<LAYOUT_SWZ>(sRows);
     cp_async_wait_all();
     if (done) return;
@@ -1744,9 +1747,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
         TileCtx<T> c;
         tile_ctx(P, t, parity, c);
         done = P.s.done[c.bw.slot];
-        if (!tma)
+        if (!tma) {
             tile_issue<T, STAGE, LAYOUT_DENSE>(P, c, sW);
-        else if (threadIdx.x < 7)
+            if (STAGE > 0) tile_prefetch_dq(c);
+        } else if (threadIdx.x < 7)
             tile_issue_tma(c, parity, sW, &s_bar, (int)threadIdx.x);
     }
     unsigned phase = 0;
@@ -1791,6 +1795,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? BLOCKS_FP32 : 1)
             done_n = P.s.done[cn.bw.slot];
             if (!tma) {
                 tile_issue<T, STAGE, LAYOUT_DENSE>(P, cn, sW);
+                if (STAGE > 0) tile_prefetch_dq(cn);
             } else if (threadIdx.x < 7) {
                 // the block's generic-proxy accesses of sW come before the copies' writes
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
